@@ -1,0 +1,429 @@
+#!/usr/bin/env python3
+"""Benchmark of the bricked multi-resolution raycaster on GB300.
+
+Default workload (one step = one frame of the whole hot path):
+  1024^3 uint16 fractal value noise (5 octaves) + 200 spheres (r 4..60), 64^3 bricks with apron,
+  5 LOD levels built on the GPU, footprint LOD, 1920x1080 orbit view at a seeded angle, 45 deg FOV,
+  step 0.5 voxel, 256-entry RGBA TF with 3 seeded opacity peaks, early termination at 0.99.
+The metric is composited ray samples per second (and ms per frame).  The primary line renders
+from uint16 bricks; the binary16 store of the same volume and a float32 store ("plain FP32 path")
+are timed beside it, and the differentiable workload (forward + adjoint) adds a fwd+bwd figure.
+
+--impl reference times the FP64 CPU oracle on a bounded seeded pixel sample of the same frame.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ------------------------------------------------------------------ workloads
+
+def c2_workload(seed=2):
+    D = (1024, 1024, 1024)
+    return {
+        "name": "reduced-precision single view, 1024^3 u16 noise+spheres, 64^3 bricks, 5 levels, 1920x1080",
+        "D": D, "brick": 64, "levels": 5,
+        "make": lambda: synth.noise_spheres(D, seed, octaves=5, period0=128.0, nspheres=200,
+                                            radius=(4.0, 60.0), value=(0.3, 1.0)),
+        "src": "u16",
+        "cams": [synth.seeded_orbit(D, 1920, 1080, seed)],
+        "tf": synth.tf_peaks(seed),
+        "params": {"step": 0.5, "et": 0.99, "lod_mode": 1, "lod_bias": 0},
+    }
+
+
+def c4_workload(seed=4):
+    D = (256, 256, 256)
+    return {
+        "name": "differentiable, 256^3 f32 blobs, 16 views 512x512, fwd+adjoint",
+        "D": D, "brick": 32, "levels": 1,
+        "make": lambda: synth.blobs(D, seed, dtype="f32", nblobs=8, sigma=(12.0, 40.0), amp=(0.2, 1.0),
+                                    noise=0.02, vmax=1.0),
+        "src": "f32",
+        "cams": [synth.seeded_orbit(D, 512, 512, seed, view=v) for v in range(16)],
+        "tf": synth.tf_ramp(alpha_start=0.05, alpha_max=0.1),
+        "params": {"step": 0.5, "et": 0.99, "lod_mode": 0},
+    }
+
+
+# ------------------------------------------------------------------ helpers
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1])); mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def render_kernel_digest():
+    h = hashlib.sha256()
+    for f in ("kernels_render.cu", "internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2509_26213_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    path = os.path.join(ROOT, "profiles", f"raycast_fwd_{workload_key}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_src = re.search(r"kernel source digest:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram bytes per launch \(scaled to the bench frame\):\s*([0-9.eE+]+)", text)
+    if m_src and m_b and m_src.group(1) == render_kernel_digest():
+        return float(m_b.group(1))
+    return None
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist, rank, ws, local
+    return None, rank, ws, local
+
+
+def barrier(dist):
+    if dist:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x):
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+
+def run_reference(args, dist, rank, ws):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = c2_workload()
+    t0 = time.time()
+    raw = wl["make"]()
+    ovol = oracle.Volume(oracle.pyramid(raw, wl["levels"], "u16"), "u16", wl["brick"])
+    prep = time.time() - t0
+    cam, tf, params = wl["cams"][0], wl["tf"], wl["params"]
+    npix = args.ref_pixels
+    threads = oracle.threads()
+    for i in range(args.warmup):
+        oracle.render(ovol, cam, tf, params, pixels=synth.pixel_subset(cam["w"], cam["h"], 64, 1000 + i))
+    times, samples = [], 0
+    for i in range(args.steps):
+        pix = synth.pixel_subset(cam["w"], cam["h"], npix, 2000 + i)
+        t = time.perf_counter()
+        out = oracle.render(ovol, cam, tf, params, pixels=pix)
+        times.append(time.perf_counter() - t)
+        samples += int(out["n"].sum())
+    total = sum(times)
+    value = samples / total
+    line = {
+        "impl": "reference", "metric": "ray samples/s", "value": value, "unit": "samples/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl["name"], "store": "u16",
+                                         "sample": f"{npix} seeded pixels of the frame per step"},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{npix} seeded pixels per step x {args.steps} steps"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "prep_s": prep,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def build_volume(P, wl, store, raw):
+    Dx, Dy, Dz = wl["D"]
+    vol = P.Volume(wl["D"], store, wl["brick"], wl["levels"])
+    vol.upload_level(0, raw, wl["src"])
+    if wl["levels"] > 1:
+        vol.build_lod(0)
+    return vol
+
+
+def time_frames(torch, vol, cams, tf, params, steps, warmup, flush, grad=False, drgba=None, dtf=None, dvox=None):
+    """Per-step CUDA-event times (ms) of one frame; L2 flushed before every step (not timed)."""
+    for _ in range(warmup):
+        vol.render(cams, tf, params, grad=grad)
+        if grad:
+            vol.render_backward(drgba, dtf, dvox)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        vol.render(cams, tf, params, grad=grad)
+        if grad:
+            vol.render_backward(drgba, dtf, dvox)
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_ours(args, dist, rank, ws, local):
+    import torch
+    import paper_2509_26213_gb300 as pkg
+    pkg.build()
+    from paper_2509_26213_gb300.volume import Volume
+    import paper_2509_26213_gb300.volume as P
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = c2_workload()
+    raw = wl["make"]()
+    # weak scaling: every rank renders its own frame (view rotated per rank); no collective
+    cams = [synth.seeded_orbit(wl["D"], 1920, 1080, 2, view=rank)] if ws > 1 else wl["cams"]
+    tf = torch.from_numpy(wl["tf"]).to(dev)
+    params = wl["params"]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    vol = build_volume(P, wl, "u16", raw)
+    out, ns = vol.render(cams, tf, params, nsamples=True)
+    torch.cuda.synchronize()
+    samples = int(ns.sum().item())
+    st = vol.stats()
+    touched = st["touched"]
+
+    barrier(dist)
+    with Clocks(local) as clk:
+        wall0 = time.perf_counter()
+        ms = time_frames(torch, vol, cams, tf, params, args.steps, args.warmup, flush)
+        wall = time.perf_counter() - wall0
+    clocks = clk.summary()
+    t_step = max_over_ranks(dist, statistics.mean(ms))
+    total_samples = sum_over_ranks(dist, samples)
+    value = total_samples / (t_step * 1e-3)
+
+    # end to end through the public API with host buffers: TF up, image down, every step
+    npx = sum(c["w"] * c["h"] for c in cams)
+    tf_host = torch.from_numpy(wl["tf"]).pin_memory()
+    img_host = torch.empty((npx, 4), dtype=torch.float32).pin_memory()
+    tf_dev = torch.empty_like(tf)
+    out_dev = torch.empty((npx, 4), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        tf_dev.copy_(tf_host, non_blocking=True)
+        vol.render(cams, tf_dev, params, out=out_dev)
+        img_host.copy_(out_dev, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(dist)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        tf_dev.copy_(tf_host, non_blocking=True)
+        vol.render(cams, tf_dev, params, out=out_dev)
+        img_host.copy_(out_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
+    e2e_step = max_over_ranks(dist, statistics.mean(e2e_ms))
+    e2e_value = total_samples / (e2e_step * 1e-3)
+
+    # roofline of the render kernel: algorithmic bytes = bricks touched + image + TF + page-table words
+    lay = vol.layout
+    brick_payload = (wl["brick"] + 1) ** 3 * 2
+    b_unique = touched * brick_payload + npx * 16 + 4096 + touched * 4
+    b_sample = samples * (8 * 2 + 4)
+    peak, peak_kind = measured_peaks()
+    achieved = b_unique / (statistics.mean(ms) * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic("c2"), "peak_kind": f"{peak_kind} hbm_gbs",
+                "bytes_accounting": "unique bricks touched x (B+1)^3 x 2 B + image + TF + page-table words",
+                "per_sample_gather_GBps": b_sample / (statistics.mean(ms) * 1e-3) / 1e9}
+
+    variants = {}
+    if not args.quick:
+        for store in ("f16", "f32"):
+            v2 = build_volume(P, wl, store, raw)
+            _, ns2 = v2.render(cams, tf, params, nsamples=True)
+            torch.cuda.synchronize()
+            s2 = int(ns2.sum().item())
+            ms2 = time_frames(torch, v2, cams, tf, params, max(3, args.steps // 2), args.warmup, flush)
+            variants[store] = {"samples_per_s": s2 / (statistics.mean(ms2) * 1e-3), "ms_per_frame": statistics.mean(ms2),
+                               "samples_per_frame": s2}
+            v2.close()
+            torch.cuda.empty_cache()
+        # differentiable workload: forward in gradient mode + adjoint
+        w4 = c4_workload()
+        raw4 = w4["make"]()
+        v4 = build_volume(P, w4, "f32", raw4)
+        tf4 = torch.from_numpy(w4["tf"]).to(dev)
+        o4, ns4 = v4.render(w4["cams"], tf4, w4["params"], nsamples=True, grad=True)
+        torch.cuda.synchronize()
+        s4 = int(ns4.sum().item())
+        drgba = torch.randn_like(o4) * 0.01
+        dtf = torch.zeros((256, 4), dtype=torch.float32, device=dev)
+        dvox = torch.zeros((256, 256, 256), dtype=torch.float32, device=dev)
+        ms_f = time_frames(torch, v4, w4["cams"], tf4, w4["params"], max(3, args.steps // 2), args.warmup, flush)
+        ms_fb = time_frames(torch, v4, w4["cams"], tf4, w4["params"], max(3, args.steps // 2), args.warmup, flush,
+                            grad=True, drgba=drgba, dtf=dtf, dvox=dvox)
+        variants["fwd_bwd"] = {"workload": w4["name"], "samples_per_frame": s4,
+                               "fwd_ms": statistics.mean(ms_f), "fwd_bwd_ms": statistics.mean(ms_fb),
+                               "fwd_samples_per_s": s4 / (statistics.mean(ms_f) * 1e-3),
+                               "fwd_bwd_samples_per_s": s4 / (statistics.mean(ms_fb) * 1e-3)}
+        v4.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wl, raw, args.cpu_pixels)
+
+    if rank == 0:
+        line = {
+            "metric": "ray samples/s", "value": value, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "store": "u16", "brick": wl["brick"], "levels": wl["levels"],
+                       "image": "1920x1080", "lod": "footprint", "step": 0.5, "et": 0.99,
+                       "samples_per_frame": samples, "bricks_touched": touched,
+                       "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
+                       "parallelism": f"replicas x{ws}"},
+            "ms_per_frame": statistics.mean(ms),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": 4096,
+                    "d2h_bytes_per_step": npx * 16, "ms_per_step": e2e_step},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "wall_s_timed": wall,
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    vol.close()
+
+
+def cpu_baseline(wl, raw, npix):
+    import oracle
+    oracle.build()
+    ovol = oracle.Volume(oracle.pyramid(raw, wl["levels"], "u16"), "u16", wl["brick"])
+    cam = wl["cams"][0]
+    pix = synth.pixel_subset(cam["w"], cam["h"], npix, 77)
+    t = time.perf_counter()
+    out = oracle.render(ovol, cam, wl["tf"], wl["params"], pixels=pix)
+    dt = time.perf_counter() - t
+    return {"value": int(out["n"].sum()) / dt, "unit": "samples/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{npix} seeded pixels of the 1920x1080 frame ({int(out['n'].sum())} samples, {dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="primary line only (no storage variants, no fwd+bwd)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-pixels", type=int, default=32768)
+    ap.add_argument("--ref-pixels", type=int, default=8192)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    dist, rank, ws, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, dist, rank, ws)
+    else:
+        run_ours(args, dist, rank, ws, local)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * vol.h -- C ABI of the GB300 bricked multi-resolution volume raycaster.
+ *
+ * The library renders a volume that is split into bricks (Drees & Risse,
+ * "Palace", arXiv 2509.26213, Sec. III-A: h = floor(g / C), l = g mod C),
+ * kept as a level-of-detail pyramid (Sec. III-D) whose resident bricks sit in
+ * one device "atlas" and are found through one page table per level
+ * (Sec. III-E).  Rendering is direct volume rendering (Sec. IV-A) with a 1D
+ * RGBA transfer function (Fig. 1), footprint-based LOD selection (Sec. V-C),
+ * early ray termination, and a brick-request queue for bricks that are not
+ * resident (Sec. III-H).  An adjoint pass gives gradients with respect to the
+ * transfer function and the level-0 voxels (not in the paper).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: VOL_OK (0) or a negative VOL_ERR_* code.  The message of
+ *     the last failure on a volume is available from vol_last_error().
+ *   - Coordinates: level-0 voxel units; the volume occupies [0, D) per axis
+ *     and voxel i has its centre at i + 0.5.  Level l has D_l = ceil(D_{l-1}/2)
+ *     voxels per axis and spacing D_0 / D_l (uniform physical size).
+ *   - Dense voxel arrays are x fastest: index = x + Dx * (y + Dy * z).
+ *   - Images are packed per view, row-major, y down: float RGBA [h][w][4].
+ *   - Ownership: the caller owns every pointer it passes; the library never
+ *     frees them and keeps none after the call returns, except that
+ *     vol_render_backward() and vol_render_resume() use the buffers of the
+ *     preceding vol_render() on the same volume.
+ *   - Streams: all device work of a volume is ordered on the CUDA stream given
+ *     to vol_create() / vol_set_stream() (NULL = the legacy default stream).
+ *     Calls return once the work is enqueued, except where noted.
+ *   - One volume is used by one host thread at a time.
+ */
+#ifndef VOLRC_VOL_H
+#define VOLRC_VOL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VOL_OK 0
+#define VOL_ERR_INVALID_ARG (-1)      /* bad size, pointer, level, brick or parameter */
+#define VOL_ERR_OOM (-2)              /* a device or pinned host allocation failed */
+#define VOL_ERR_INCOMPLETE (-3)       /* rays are still waiting for non-resident bricks */
+#define VOL_ERR_PROVIDER (-4)         /* the brick provider callback returned non-zero */
+#define VOL_ERR_CUDA (-5)             /* a CUDA runtime call failed */
+#define VOL_ERR_NO_FORWARD_STATE (-6) /* backward/resume without a matching render */
+#define VOL_ERR_UNSUPPORTED (-7)      /* valid request outside what this build supports */
+#define VOL_ERR_DEVICE (-8)           /* a device-side check failed (recorded, not trapped) */
+#define VOL_ERR_CACHE_FULL (-9)       /* no brick slot could be freed */
+
+#define VOL_MAX_LEVELS 16
+#define VOL_MAX_VIEWS 1024
+
+/* Storage type of the voxels in the atlas; values are normalised to [0, 1]
+ * as u8 / 255, u16 / 65535, and floats as stored (clamped to [0, 1] before
+ * the transfer function). */
+typedef enum { VOL_U8 = 0, VOL_U16 = 1, VOL_F16 = 2, VOL_F32 = 3 } vol_dtype;
+
+typedef struct vol_s *vol_t;
+
+/* Pinhole camera.  For pixel (px, py) of a w x h image:
+ *   u = ((px + 0.5) / w) * 2 - 1,  v = 1 - ((py + 0.5) / h) * 2,
+ *   d = normalise(fwd + (u * tan_half_fov * aspect) * right + (v * tan_half_fov) * up)
+ * in binary32 without contraction; the ray starts at eye (Fig. 1's
+ * CameraState / entry_exit_points). */
+typedef struct {
+    float eye[3], right[3], up[3], fwd[3];
+    float tan_half_fov; /* tan(vertical field of view / 2) */
+    float aspect;       /* w / h */
+    int32_t w, h;
+} vol_camera;
+
+#define VOL_RENDER_GRAD 1u /* keep transmittance checkpoints for vol_render_backward */
+
+typedef struct {
+    float step;          /* sample spacing in level-0 voxels (> 0) */
+    float et_threshold;  /* stop a ray after the sample where 1 - T >= et_threshold */
+    float bg[4];         /* background RGBA composited behind the volume */
+    int32_t lod_mode;    /* 0: all samples on level 0; 1: footprint LOD (Sec. V-C) */
+    int32_t lod_bias;    /* added to the footprint level before clamping to [0, L-1] */
+    int32_t tile_w;      /* ray tile (work item) width in pixels; 0 = default 8 */
+    int32_t tile_h;      /* ray tile height; tile_w * tile_h must be a multiple of 32; 0 = 8 */
+    int32_t max_passes;  /* miss/refill passes per render when a provider is set; 0 = 64 */
+    uint32_t flags;      /* VOL_RENDER_* bits */
+    int32_t refill;      /* a warp fetches new rays once fewer lanes than this are busy
+                            (1..32; 0 = default 24); performance only, never the image */
+    int32_t ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
+} vol_params;
+
+/* Brick-and-level layout that vol_create() would use (pure host computation). */
+typedef struct {
+    int64_t dims[3];
+    int32_t dtype, brick, levels;
+    int32_t bytes_per_voxel;
+    int64_t level_dims[VOL_MAX_LEVELS][3];
+    int64_t level_bricks[VOL_MAX_LEVELS][3];  /* ceil(D_l / B) per axis */
+    int64_t level_pt_offset[VOL_MAX_LEVELS];  /* first page-table entry of each level */
+    int64_t total_bricks;                     /* page-table entries over all levels */
+    int64_t slot_bytes;   /* one atlas slot: (B+1)^3 voxels, padded to 256 bytes */
+    int64_t nslots;       /* atlas capacity in bricks */
+    int64_t atlas_bytes;
+} vol_layout;
+
+/* Per-render counters (vol_get_stats). */
+typedef struct {
+    int64_t passes;          /* kernel passes of the last render (1 when nothing missed) */
+    int64_t rays;            /* rays of the last render */
+    int64_t suspended;       /* rays suspended at a missing brick, summed over passes */
+    int64_t requests;        /* distinct brick requests, summed over passes */
+    int64_t request_overflow;/* requests dropped because the table's probe bound was hit */
+    int64_t bricks_loaded;   /* bricks the provider filled during the last render */
+    int64_t bytes_loaded;    /* host-to-device brick bytes during the last render */
+    int64_t evicted;         /* slots evicted during the last render */
+    int64_t resident;        /* resident bricks after the last render */
+    int64_t frame;           /* frame counter (one per vol_render) */
+    int64_t device_error;    /* device-side check failures (0 expected) */
+    int64_t touched;         /* distinct bricks the last render sampled (usage stamps) */
+} vol_stats;
+
+/* Provider of bricks that are not resident (procedural or out-of-core source).
+ * Fills dst (host memory owned by the library, (B+1)^3 voxels of type
+ * src_dtype as declared by vol_set_provider) with the voxels of brick
+ * (bx, by, bz) of `level` INCLUDING the one-voxel apron on its +x/+y/+z sides:
+ * voxel (i, j, k) of dst, i, j, k in [0, B], is the level voxel
+ * (min(bx*B + i, D_l - 1), min(by*B + j, D_l - 1), min(bz*B + k, D_l - 1)).
+ * Returns 0 on success. Called from the host thread that called vol_render(). */
+typedef int (*vol_provider_fn)(void *user, int level, const int32_t brick[3], void *dst);
+
+/* Debug record of one sample's decisions (vol_trace). */
+typedef struct {
+    int32_t k;          /* sample index */
+    uint32_t t_bits;    /* binary32 bits of t_k */
+    int32_t level;      /* LOD level */
+    int32_t i0[3];      /* clamped lower-corner voxel on the level grid */
+    int32_t local[3];   /* position inside the brick: i0 mod B */
+    int32_t pad;
+    int64_t brick_id;   /* bx + nbx * (by + nby * bz) on the level */
+    uint32_t slot;      /* atlas slot from the page table (0xFFFFFFFF = not resident) */
+    uint32_t pad2;
+} vol_trace_rec;
+
+/* ---- layout and lifetime ------------------------------------------------ */
+
+/* Computes the layout for dims / dtype / brick (power of two, 4..128) /
+ * levels (1..16) / cache_bytes (0 = room for every brick of every level).
+ * Pure host code; needs no GPU. */
+int vol_plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes,
+             vol_layout *out);
+
+/* Creates a volume on the current CUDA device: allocates the atlas (the
+ * cache of brick slots), the page tables (all entries non-resident) and the
+ * slot usage stamps.  `stream` is a cudaStream_t or NULL. */
+int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes,
+               void *stream, vol_t *out);
+
+/* Frees everything the volume allocated.  NULL is ignored. */
+void vol_destroy(vol_t v);
+
+/* Message of the last failure on v (or of the last vol_create failure when
+ * v is NULL).  Valid until the next call on v. */
+const char *vol_last_error(vol_t v);
+
+int vol_set_stream(vol_t v, void *stream);
+int vol_get_layout(vol_t v, vol_layout *out);
+int vol_get_stats(vol_t v, vol_stats *out); /* synchronises the stream */
+
+/* ---- bricks -------------------------------------------------------------- */
+
+/* Makes every brick of `level` resident from a dense level array `src`
+ * (D_l voxels per axis, x fastest) of type src_dtype, in host memory
+ * (src_on_device = 0) or device memory (1).  Each brick is written into its
+ * atlas slot with its +side apron (edge voxels replicated at the volume
+ * boundary).  Conversions: equal types are copied; u16 -> f16 stores the
+ * binary16 of the binary32 quotient u / 65535; u8 -> f32 and u16 -> f32
+ * store u / 255 and u / 65535 in binary32; others are VOL_ERR_UNSUPPORTED.
+ * Host sources are copied synchronously. */
+int vol_upload_level(vol_t v, int level, const void *src, int src_dtype, int src_on_device);
+
+/* Makes one brick resident from (B+1)^3 voxels (apron included, layout as
+ * for vol_provider_fn) of type src_dtype in host or device memory.  Evicts
+ * the least recently used brick when the atlas is full. */
+int vol_upload_brick(vol_t v, int level, const int32_t brick[3], const void *src, int src_dtype,
+                     int src_on_device);
+
+/* Builds levels from_level+1 .. L-1 from resident level from_level by the
+ * 2x2x2 box filter of Sec. III-D: coarse voxel i averages fine voxels 2i and
+ * 2i+1 per axis (the last fine voxel replaces an index past the edge);
+ * integer types: (sum + 4) >> 3; float types: binary32 sum in (dz, dy, dx)
+ * order times 0.125 (binary16 rounded to nearest even).  Every brick of each
+ * source level must be resident; all bricks of the built levels become
+ * resident.  VOL_ERR_CACHE_FULL when the atlas cannot hold them. */
+int vol_build_lod(vol_t v, int from_level);
+
+/* Copies the (B+1)^3 stored voxels of a resident brick (apron included) to
+ * host memory dst; synchronous.  VOL_ERR_INVALID_ARG when not resident. */
+int vol_download_brick(vol_t v, int level, const int32_t brick[3], void *dst);
+
+/* Drops every brick (page tables back to non-resident). */
+int vol_evict_all(vol_t v);
+
+/* Installs (or with fn = NULL removes) the provider used by vol_render() to
+ * load missing bricks; src_dtype is the type the provider writes. */
+int vol_set_provider(vol_t v, vol_provider_fn fn, void *user, int src_dtype);
+
+/* ---- rendering ----------------------------------------------------------- */
+
+/* Renders nviews views (cams: host array) in one persistent launch that
+ * takes ray tiles of all views from one work counter.  tf_dev: device
+ * float [256][4] RGBA transfer function (entry j at value j / 255, linearly
+ * interpolated).  rgba_dev: device output, the views' images packed in
+ * order.  nsamples_dev: optional device int32 per pixel, the number of
+ * samples composited (NULL to skip).
+ * Sample k of a ray is at t_k = t0 + k * step while t_k < t1 (entry/exit of
+ * the box); C += T a rgb, T *= 1 - a; the ray stops after the sample where
+ * 1 - T >= et_threshold; output rgb = C + T bg_rgb, a = (1 - T) + T bg_a.
+ * When every brick is resident the call only enqueues work.  Otherwise it
+ * synchronises: rays that reach a missing brick are suspended (position and
+ * partial colour kept), the bricks are requested through a deduplicating
+ * hash table, and -- if a provider is set -- loaded and the suspended rays
+ * resumed, up to max_passes passes; without a provider, or when passes run
+ * out, it returns VOL_ERR_INCOMPLETE and the requests can be read with
+ * vol_poll_requests().  The finished image does not depend on how many
+ * passes it took. */
+int vol_render(vol_t v, const vol_camera *cams, int nviews, const float *tf_dev,
+               const vol_params *params, float *rgba_dev, int32_t *nsamples_dev);
+
+/* Resumes the rays that the last vol_render() left suspended, after the
+ * caller uploaded the requested bricks (vol_upload_brick). Synchronises.
+ * VOL_OK when every ray finished, else VOL_ERR_INCOMPLETE. */
+int vol_render_resume(vol_t v);
+
+/* Copies up to cap outstanding brick requests of the last pass as
+ * [level, bx, by, bz] int32 quadruples to host memory; *n receives their
+ * total count (which may exceed cap). Synchronises. */
+int vol_poll_requests(vol_t v, int32_t *out, int cap, int *n);
+
+/* Adjoint of the last vol_render() made with VOL_RENDER_GRAD (lod_mode 0,
+ * every brick resident, no suspended rays).  drgba_dev: dL/dRGBA in the
+ * layout of rgba_dev.  Accumulates (+=) dL/dtf into dtf_dev (device float
+ * [256][4]) and dL/dvoxel into dvoxel_dev (device float, dense level 0, x
+ * fastest; gradient with respect to the normalised voxel value).  Either
+ * output may be NULL.  Transmittance is recomputed forward from checkpoints
+ * stored every 32 samples, never by dividing by (1 - a). */
+int vol_render_backward(vol_t v, const float *drgba_dev, float *dtf_dev, float *dvoxel_dev);
+
+/* Debug: the decision-layer record of up to max_samples samples of each of
+ * npix pixels (pixels_host: int32 [npix][2] = px, py of view `cam`), without
+ * early termination.  out_host: [npix][max_samples] records; counts_host:
+ * int32 [npix] total samples per ray.  Synchronises. */
+int vol_trace(vol_t v, const vol_camera *cam, const vol_params *params, const int32_t *pixels_host,
+              int npix, int max_samples, vol_trace_rec *out_host, int32_t *counts_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VOLRC_VOL_H */

@@ -1,0 +1,147 @@
+// internal.cuh -- device-side structures shared by the runtime and the kernels.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vol.h"
+
+namespace volrc {
+
+constexpr uint32_t kInvalidSlot = 0xFFFFFFFFu;
+constexpr int kMaxLevels = VOL_MAX_LEVELS;
+constexpr int kCkptEvery = 32;      // transmittance checkpoint spacing (samples)
+constexpr int kRenderThreads = 128; // threads per CTA of the render kernels
+constexpr int kMaxProbe = 64;       // bounded linear probing of the request table
+
+// Counter words of one render (device memory, reset before each pass).
+enum Counter : int {
+    kWork = 0,       // next work item (tile or suspended-ray chunk)
+    kReqCount = 1,   // entries appended to the request list
+    kSuspCount = 2,  // rays suspended in this pass
+    kReqOverflow = 3,
+    kDevError = 4,
+    kNumCounters = 8
+};
+
+struct LevelDev {
+    int D[3];        // voxels per axis
+    int nb[3];       // bricks per axis
+    float r[3];      // D_l / D_0 per axis, binary32
+    uint32_t pt_off; // first page-table entry
+};
+
+struct ViewDev {
+    float eye[3], right[3], up[3], fwd[3];
+    float tan;        // tan_half_fov
+    float tan_aspect; // tan_half_fov * aspect (binary32)
+    float lodscale;   // (2 * tan_half_fov) / h (binary32)
+    int w, h;
+    int tiles_x;
+    int tile_off;     // first work item of this view
+    long long ray_off;// first ray (pixel) of this view in the packed image
+};
+
+struct SuspRec {       // a ray waiting for a brick
+    long long ray;     // packed pixel index
+    int k;             // next sample
+    int pad;
+    float C[3], T;     // partial colour and transmittance
+};
+
+struct VolDev {
+    const void* atlas;
+    unsigned long long slot_elems; // elements per slot (padded)
+    int bshift, bmask, B1;         // log2 B, B - 1, B + 1
+    int nlevels;
+    const uint32_t* pt;
+    LevelDev lv[kMaxLevels];
+    float D0f[3];
+};
+
+struct RenderDev {
+    VolDev vol;
+    const ViewDev* views;
+    int nviews;
+    int nwork;          // tiles (fresh pass) or 32-ray chunks (resume pass)
+    int resume;         // 0: fresh pass over tiles; 1: resume suspended rays
+    int tile_w, tile_h;
+    int refill_thresh;  // refill lanes when fewer than this many are active
+    const float4* tf;
+    float step, et;
+    float4 bg;
+    int lod_mode, lod_bias;
+    float4* out;
+    int* nsamp;
+    unsigned* counters;
+    // misses
+    const SuspRec* susp_in;
+    int nsusp_in;
+    SuspRec* susp_out;
+    unsigned* req_table;
+    unsigned req_cap_mask;
+    unsigned* req_list;
+    unsigned req_list_cap;
+    unsigned* last_used;
+    unsigned frame;
+    // gradient checkpoints
+    float* ckpt;
+    long long nrays;
+    int ckpt_segs;
+    int* ray_n;
+};
+
+struct BackwardDev {
+    VolDev vol;
+    const ViewDev* views;
+    int nviews;
+    int nwork;
+    int tile_w, tile_h;
+    const float4* tf;
+    float step;
+    float4 bg;
+    const float4* drgba;
+    float* dtf;
+    float* dvox;
+    int D0[3];
+    unsigned* counters;
+    const float* ckpt;
+    long long nrays;
+    const int* ray_n;
+};
+
+struct TraceDev {
+    VolDev vol;
+    ViewDev view;
+    float step;
+    int lod_mode, lod_bias;
+    const int* pixels;
+    int npix;
+    int max_samples;
+    vol_trace_rec* out;
+    int* counts;
+};
+
+// ---- launchers (kernels_render.cu) ----
+cudaError_t launch_render(int dtype, bool grad, const RenderDev& p, int grid, cudaStream_t s);
+cudaError_t launch_backward(int dtype, const BackwardDev& p, int grid, cudaStream_t s);
+cudaError_t launch_trace(const TraceDev& p, cudaStream_t s);
+int render_blocks_per_sm(int dtype, bool grad);
+int backward_blocks_per_sm(int dtype);
+
+// ---- launchers (kernels_volume.cu) ----
+// Write every brick of a dense level (src of src_dtype) into atlas slots.
+cudaError_t launch_upload_level(int dst_dtype, int src_dtype, const void* src, const VolDev& vol,
+                                int level, const uint32_t* slots_of_bricks, long long nbricks,
+                                cudaStream_t s);
+// Write n packed (B+1)^3 bricks (src of src_dtype, device) into slots[i] (device array).
+cudaError_t launch_upload_bricks(int dst_dtype, int src_dtype, const void* src, const VolDev& vol,
+                                 const uint32_t* slots, long long n, cudaStream_t s);
+// Build level `level` (all bricks; slots_of_bricks indexed by brick id) from level-1.
+cudaError_t launch_downsample(int dtype, const VolDev& vol, int level, const uint32_t* slots_of_bricks,
+                              long long nbricks, unsigned* err, cudaStream_t s);
+// pt[idx[i]] = val[i] for i < n (atomic exchange; Sec. III-E parallel insert/remove).
+cudaError_t launch_pt_update(uint32_t* pt, const uint32_t* idx, const uint32_t* val, int n,
+                             cudaStream_t s);
+
+}  // namespace volrc

@@ -1,0 +1,626 @@
+// kernels_render.cu -- raycast forward (persistent, batched), adjoint, and decision trace.
+//
+// The forward kernel is the data-parallel hot path of the bricked multi-resolution
+// raycaster (Drees & Risse, "Palace", Sec. III-E, III-H, IV-A, V-C): per pixel it builds
+// the camera ray, intersects the volume box, and for each sample picks the LOD level from
+// the pixel footprint, resolves the brick through the level's page table into the atlas,
+// interpolates trilinearly inside the brick (the +side apron makes every corner local),
+// maps the value through the RGBA transfer function, and composites front to back with
+// early termination.
+//
+// Work distribution: one persistent grid; each warp takes ray tiles (or, on a resume
+// pass, chunks of 32 suspended rays) from a global counter and refills lanes whose ray
+// ended as soon as fewer than `refill_thresh` lanes are busy, so early-terminated rays do
+// not leave lanes idle.
+//
+// Decision arithmetic (ray setup, sample positions, LOD level, voxel index, brick id) is
+// binary32 with explicit round-to-nearest intrinsics, so it never contracts into FMAs and
+// is bit-identical to any correct IEEE binary32 evaluation of the same expressions.
+#include "internal.cuh"
+
+namespace volrc {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+template <int DT>
+struct Voxel;
+template <>
+struct Voxel<VOL_U8> {
+    using T = uint8_t;
+    static __device__ __forceinline__ float ld(const T* p) { return (float)__ldg(p); }
+};
+template <>
+struct Voxel<VOL_U16> {
+    using T = uint16_t;
+    static __device__ __forceinline__ float ld(const T* p) { return (float)__ldg(p); }
+};
+template <>
+struct Voxel<VOL_F16> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)); }
+};
+template <>
+struct Voxel<VOL_F32> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const T* p) { return __ldg(p); }
+};
+
+// Transfer-function coordinate x = 255 * clamp(v_normalised, 0, 1) from an interpolated
+// stored value (u8: stored = 255 v; u16: stored = 65535 v; floats: v).
+template <int DT>
+__device__ __forceinline__ float tf_coord(float v) {
+    if (DT == VOL_U8) return v;
+    if (DT == VOL_U16) return v * (255.0f / 65535.0f);
+    return fminf(fmaxf(v, 0.0f), 1.0f) * 255.0f;
+}
+template <int DT>
+__device__ __forceinline__ bool tf_inside(float v) {
+    if (DT == VOL_U8 || DT == VOL_U16) return true;
+    return v >= 0.0f && v <= 1.0f;
+}
+
+struct Ray {
+    float o[3], d[3], t0, t1;
+    bool hit;
+};
+
+// Pixel -> ray and slab entry/exit against [0, D0) (Fig. 1 entry_exit_points).
+__device__ __forceinline__ void make_ray(const ViewDev& V, const float D0f[3], int px, int py, Ray& r) {
+    const float u = __fsub_rn(__fmul_rn(__fdiv_rn(__fadd_rn((float)px, 0.5f), (float)V.w), 2.0f), 1.0f);
+    const float v = __fsub_rn(1.0f, __fmul_rn(__fdiv_rn(__fadd_rn((float)py, 0.5f), (float)V.h), 2.0f));
+    const float cx = __fmul_rn(u, V.tan_aspect);
+    const float cy = __fmul_rn(v, V.tan);
+    float dd[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        dd[a] = __fadd_rn(__fadd_rn(V.fwd[a], __fmul_rn(cx, V.right[a])), __fmul_rn(cy, V.up[a]));
+    const float len2 = __fadd_rn(__fadd_rn(__fmul_rn(dd[0], dd[0]), __fmul_rn(dd[1], dd[1])), __fmul_rn(dd[2], dd[2]));
+    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(len2));
+    float t0 = 0.0f, t1 = __int_as_float(0x7f800000);
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        r.d[a] = __fmul_rn(dd[a], inv);
+        r.o[a] = V.eye[a];
+        if (r.d[a] == 0.0f) {
+            if (r.o[a] < 0.0f || r.o[a] >= D0f[a]) hit = false;
+            continue;
+        }
+        const float ta = __fdiv_rn(__fsub_rn(0.0f, r.o[a]), r.d[a]);
+        const float tb = __fdiv_rn(__fsub_rn(D0f[a], r.o[a]), r.d[a]);
+        const float tn = ta < tb ? ta : tb;
+        const float tf = ta < tb ? tb : ta;
+        if (tn > t0) t0 = tn;
+        if (tf < t1) t1 = tf;
+    }
+    r.t0 = t0;
+    r.t1 = t1;
+    r.hit = hit && (t0 < t1);
+}
+
+// Footprint LOD (Sec. V-C): l = clamp(ilogb(t * lodscale) + bias, 0, L-1); l = 0 when the
+// footprint has no normal exponent.
+__device__ __forceinline__ int lod_level(float t, float lodscale, int bias, int nlevels) {
+    const float q = __fmul_rn(t, lodscale);
+    const int e = (q >= 1.17549435e-38f) ? (int)((__float_as_uint(q) >> 23) & 0xFF) - 127 : -127;
+    return min(max(e + bias, 0), nlevels - 1);
+}
+
+struct Resolved {
+    int i0[3];
+    float w[3];
+    uint32_t pti;   // page-table index (level offset + brick id)
+    uint32_t local; // element offset inside the slot
+};
+
+// Grid position on a level, clamp to edge, chunk addressing (Sec. III-A).
+__device__ __forceinline__ void resolve(const LevelDev& L, int bshift, int bmask, int B1, const float p[3],
+                                        Resolved& R) {
+    int h[3], l[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float x = __fsub_rn(__fmul_rn(p[a], L.r[a]), 0.5f);
+        const float fx = floorf(x);
+        const int i = (int)fx;
+        if (i < 0) {
+            R.i0[a] = 0;
+            R.w[a] = 0.0f;
+        } else if (i >= L.D[a] - 1) {
+            R.i0[a] = L.D[a] - 1;
+            R.w[a] = 0.0f;
+        } else {
+            R.i0[a] = i;
+            R.w[a] = __fsub_rn(x, fx);
+        }
+        h[a] = R.i0[a] >> bshift;
+        l[a] = R.i0[a] & bmask;
+    }
+    R.pti = L.pt_off + (uint32_t)(h[0] + L.nb[0] * (h[1] + L.nb[1] * h[2]));
+    R.local = (uint32_t)((l[2] * B1 + l[1]) * B1 + l[0]);
+}
+
+// Trilinear interpolation of the 8 corners at atlas element `base` (+x, +y, +z neighbours
+// at +1, +B1, +B1^2 thanks to the apron).
+template <int DT>
+__device__ __forceinline__ float trilinear(const typename Voxel<DT>::T* a, unsigned long long base, int B1,
+                                           const float w[3]) {
+    const unsigned long long sy = (unsigned long long)B1, sz = (unsigned long long)B1 * B1;
+    const float v000 = Voxel<DT>::ld(a + base), v100 = Voxel<DT>::ld(a + base + 1);
+    const float v010 = Voxel<DT>::ld(a + base + sy), v110 = Voxel<DT>::ld(a + base + sy + 1);
+    const float v001 = Voxel<DT>::ld(a + base + sz), v101 = Voxel<DT>::ld(a + base + sz + 1);
+    const float v011 = Voxel<DT>::ld(a + base + sz + sy), v111 = Voxel<DT>::ld(a + base + sz + sy + 1);
+    const float c00 = fmaf(w[0], v100 - v000, v000);
+    const float c10 = fmaf(w[0], v110 - v010, v010);
+    const float c01 = fmaf(w[0], v101 - v001, v001);
+    const float c11 = fmaf(w[0], v111 - v011, v011);
+    const float c0 = fmaf(w[1], c10 - c00, c00);
+    const float c1 = fmaf(w[1], c11 - c01, c01);
+    return fmaf(w[2], c1 - c0, c0);
+}
+
+__device__ __forceinline__ int find_view_tile(const ViewDev* views, int nviews, int item) {
+    int lo = 0, hi = nviews - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].tile_off <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_view_ray(const ViewDev* views, int nviews, long long ray) {
+    int lo = 0, hi = nviews - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].ray_off <= ray) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t hash_key(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+// Records a brick request (Sec. III-H): insert key into the open-addressing table with
+// bounded linear probing; a newly inserted key is appended to the request list with one
+// atomic per group of inserting lanes.
+__device__ __forceinline__ void request_brick(const RenderDev& P, uint32_t key) {
+    uint32_t h = hash_key(key) & P.req_cap_mask;
+    int state = 2;  // 0 new, 1 present, 2 overflow
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        const uint32_t prev = atomicCAS(&P.req_table[h], 0u, key);
+        if (prev == 0u) { state = 0; break; }
+        if (prev == key) { state = 1; break; }
+        h = (h + 1) & P.req_cap_mask;
+    }
+    if (state == 2) atomicAdd(&P.counters[kReqOverflow], 1u);
+    const unsigned m = __activemask();
+    const unsigned mnew = __ballot_sync(m, state == 0);
+    if (state == 0) {
+        const int leader = __ffs(mnew) - 1;
+        const unsigned lane = threadIdx.x & 31;
+        unsigned base = 0;
+        if ((int)lane == leader) base = atomicAdd(&P.counters[kReqCount], (unsigned)__popc(mnew));
+        base = __shfl_sync(mnew, base, leader);
+        const unsigned pos = base + __popc(mnew & ((1u << lane) - 1));
+        if (pos < P.req_list_cap) P.req_list[pos] = key;
+        else atomicAdd(&P.counters[kReqOverflow], 1u);
+    }
+}
+
+__device__ __forceinline__ void suspend_ray(const RenderDev& P, long long ray, int k, float C0, float C1, float C2,
+                                            float T) {
+    const unsigned m = __activemask();
+    const int leader = __ffs(m) - 1;
+    const unsigned lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if ((int)lane == leader) base = atomicAdd(&P.counters[kSuspCount], (unsigned)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    const unsigned pos = base + __popc(m & ((1u << lane) - 1));
+    if ((long long)pos < P.nrays) {
+        SuspRec r;
+        r.ray = ray;
+        r.k = k;
+        r.pad = 0;
+        r.C[0] = C0;
+        r.C[1] = C1;
+        r.C[2] = C2;
+        r.T = T;
+        P.susp_out[pos] = r;
+    } else {
+        atomicAdd(&P.counters[kDevError], 1u);
+    }
+}
+
+template <int DT, bool LOD, bool GRAD>
+__global__ void __launch_bounds__(kRenderThreads) k_render(const __grid_constant__ RenderDev P) {
+    __shared__ float4 s_tf[256];
+    __shared__ LevelDev s_lv[kMaxLevels];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = P.tf[i];
+    if (threadIdx.x < P.vol.nlevels) s_lv[threadIdx.x] = P.vol.lv[threadIdx.x];
+    __syncthreads();
+
+    using VT = typename Voxel<DT>::T;
+    const VT* __restrict__ atlas = (const VT*)P.vol.atlas;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned ltmask = (1u << lane) - 1;
+    const int bshift = P.vol.bshift, bmask = P.vol.bmask, B1 = P.vol.B1;
+    const unsigned long long slot_elems = P.vol.slot_elems;
+    const float step = P.step, et = P.et;
+
+    // warp-uniform work pool
+    int pool_next = 0, pool_cnt = 0, pool_a = 0, pool_x0 = 0, pool_y0 = 0;
+    bool queue_done = false;
+
+    // lane state
+    bool active = false;
+    long long ray = 0;
+    float o0 = 0, o1 = 0, o2 = 0, d0 = 0, d1 = 0, d2 = 0, t0 = 0, t1 = 0, lodscale = 0;
+    int k = 0;
+    float C0 = 0, C1 = 0, C2 = 0, T = 1.0f;
+    uint32_t cur_pti = kInvalidSlot, cur_slot = kInvalidSlot;
+
+    for (;;) {
+        // ---- refill lanes whose ray ended
+        while (!queue_done) {
+            const unsigned need = __ballot_sync(kFull, !active);
+            if (!need) break;
+            if (pool_next >= pool_cnt) {
+                int item = 0;
+                if (lane == 0) item = (int)atomicAdd(&P.counters[kWork], 1u);
+                item = __shfl_sync(kFull, item, 0);
+                if (item >= P.nwork) {
+                    queue_done = true;
+                    break;
+                }
+                if (!P.resume) {
+                    const int v = find_view_tile(P.views, P.nviews, item);
+                    const int tl = item - P.views[v].tile_off;
+                    const int tx = P.views[v].tiles_x;
+                    pool_a = v;
+                    pool_x0 = (tl % tx) * P.tile_w;
+                    pool_y0 = (tl / tx) * P.tile_h;
+                    pool_cnt = P.tile_w * P.tile_h;
+                } else {
+                    pool_a = item * 32;
+                    pool_cnt = min(32, P.nsusp_in - item * 32);
+                }
+                pool_next = 0;
+            }
+            const int idx = pool_next + __popc(need & ltmask);
+            pool_next = min(pool_cnt, pool_next + __popc(need));
+            if (!active && idx < pool_cnt) {
+                int view, px, py, k0 = 0;
+                float c0 = 0.f, c1 = 0.f, c2 = 0.f, tt = 1.0f;
+                bool ok;
+                if (!P.resume) {
+                    view = pool_a;
+                    px = pool_x0 + idx % P.tile_w;
+                    py = pool_y0 + idx / P.tile_w;
+                    ok = px < P.views[view].w && py < P.views[view].h;
+                    ray = P.views[view].ray_off + (long long)py * P.views[view].w + px;
+                } else {
+                    const SuspRec r = P.susp_in[pool_a + idx];
+                    ray = r.ray;
+                    k0 = r.k;
+                    c0 = r.C[0];
+                    c1 = r.C[1];
+                    c2 = r.C[2];
+                    tt = r.T;
+                    view = find_view_ray(P.views, P.nviews, ray);
+                    const long long loc = ray - P.views[view].ray_off;
+                    px = (int)(loc % P.views[view].w);
+                    py = (int)(loc / P.views[view].w);
+                    ok = true;
+                }
+                if (ok) {
+                    Ray R;
+                    make_ray(P.views[view], P.vol.D0f, px, py, R);
+                    if (R.hit) {
+                        active = true;
+                        o0 = R.o[0]; o1 = R.o[1]; o2 = R.o[2];
+                        d0 = R.d[0]; d1 = R.d[1]; d2 = R.d[2];
+                        t0 = R.t0; t1 = R.t1;
+                        lodscale = P.views[view].lodscale;
+                        k = k0; C0 = c0; C1 = c1; C2 = c2; T = tt;
+                        cur_pti = kInvalidSlot;
+                        cur_slot = kInvalidSlot;
+                    } else {
+                        P.out[ray] = P.bg;
+                        if (P.nsamp) P.nsamp[ray] = 0;
+                        if (GRAD) P.ray_n[ray] = 0;
+                    }
+                }
+            }
+        }
+        unsigned act = __ballot_sync(kFull, active);
+        if (!act) break;
+
+        // ---- march
+        const int thresh = queue_done ? 1 : P.refill_thresh;
+        do {
+            if (active) {
+                bool fin = false;
+                const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
+                if (!(t < t1)) {
+                    fin = true;
+                } else {
+                    if (GRAD && k > 0 && (k & (kCkptEvery - 1)) == 0)
+                        P.ckpt[(long long)(k / kCkptEvery - 1) * P.nrays + ray] = T;
+                    const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
+                                        __fadd_rn(o2, __fmul_rn(t, d2))};
+                    const int l = LOD ? lod_level(t, lodscale, P.lod_bias, P.vol.nlevels) : 0;
+                    Resolved R;
+                    resolve(s_lv[l], bshift, bmask, B1, p, R);
+                    if (R.pti != cur_pti) {
+                        cur_pti = R.pti;
+                        cur_slot = __ldg(P.vol.pt + R.pti);
+                        if (cur_slot != kInvalidSlot && P.last_used) P.last_used[cur_slot] = P.frame;
+                    }
+                    if (cur_slot == kInvalidSlot) {
+                        if (P.req_table) {
+                            request_brick(P, R.pti + 1u);
+                            suspend_ray(P, ray, k, C0, C1, C2, T);
+                        } else {
+                            atomicAdd(&P.counters[kDevError], 1u);
+                        }
+                        active = false;
+                    } else {
+                        const unsigned long long base = (unsigned long long)cur_slot * slot_elems + R.local;
+                        const float v = trilinear<DT>(atlas, base, B1, R.w);
+                        const float x = tf_coord<DT>(v);
+                        const int i = min((int)x, 254);
+                        const float wt = x - (float)i;
+                        const float4 a = s_tf[i], b = s_tf[i + 1];
+                        const float al = fmaf(wt, b.w - a.w, a.w);
+                        const float Ta = T * al;
+                        C0 = fmaf(Ta, fmaf(wt, b.x - a.x, a.x), C0);
+                        C1 = fmaf(Ta, fmaf(wt, b.y - a.y, a.y), C1);
+                        C2 = fmaf(Ta, fmaf(wt, b.z - a.z, a.z), C2);
+                        T = T * (1.0f - al);
+                        ++k;
+                        if (__fsub_rn(1.0f, T) >= et) fin = true;
+                    }
+                }
+                if (fin) {
+                    const float4 bg = P.bg;
+                    P.out[ray] = make_float4(fmaf(T, bg.x, C0), fmaf(T, bg.y, C1), fmaf(T, bg.z, C2),
+                                             fmaf(T, bg.w, 1.0f - T));
+                    if (P.nsamp) P.nsamp[ray] = k;
+                    if (GRAD) P.ray_n[ray] = k;
+                    active = false;
+                }
+            }
+            act = __ballot_sync(kFull, active);
+        } while (__popc(act) >= thresh);
+    }
+}
+
+// ------------------------------------------------------------------ adjoint
+
+template <int DT>
+__global__ void __launch_bounds__(kRenderThreads) k_backward(const __grid_constant__ BackwardDev P) {
+    __shared__ float4 s_tf[256];
+    __shared__ float s_dtf[1024];
+    __shared__ float s_T[kCkptEvery][kRenderThreads];
+    __shared__ float s_V[kCkptEvery][kRenderThreads];
+    __shared__ LevelDev s_l0;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = P.tf[i];
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) s_dtf[i] = 0.0f;
+    if (threadIdx.x == 0) s_l0 = P.vol.lv[0];
+    __syncthreads();
+
+    using VT = typename Voxel<DT>::T;
+    const VT* __restrict__ atlas = (const VT*)P.vol.atlas;
+    const unsigned lane = threadIdx.x & 31;
+    const int tid = threadIdx.x;
+    const int bshift = P.vol.bshift, bmask = P.vol.bmask, B1 = P.vol.B1;
+    const unsigned long long slot_elems = P.vol.slot_elems;
+    const int Dx = P.D0[0], Dy = P.D0[1];
+    const float step = P.step;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(&P.counters[kWork], 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= P.nwork) break;
+        const int v = find_view_tile(P.views, P.nviews, item);
+        const ViewDev& V = P.views[v];
+        const int tl = item - V.tile_off;
+        const int x0 = (tl % V.tiles_x) * P.tile_w, y0 = (tl / V.tiles_x) * P.tile_h;
+        for (int idx = lane; idx < P.tile_w * P.tile_h; idx += 32) {
+            const int px = x0 + idx % P.tile_w, py = y0 + idx / P.tile_w;
+            if (px >= V.w || py >= V.h) continue;
+            const long long ray = V.ray_off + (long long)py * V.w + px;
+            const int n = P.ray_n[ray];
+            if (n <= 0) continue;
+            Ray R;
+            make_ray(V, P.vol.D0f, px, py, R);
+            const float4 g = P.drgba[ray];
+            float R0 = P.bg.x, R1 = P.bg.y, R2 = P.bg.z, R3 = P.bg.w;
+            const int nseg = (n + kCkptEvery - 1) / kCkptEvery;
+            for (int s = nseg - 1; s >= 0; --s) {
+                const int k0 = s * kCkptEvery, k1 = min(n, k0 + kCkptEvery);
+                float T = s == 0 ? 1.0f : P.ckpt[(long long)(s - 1) * P.nrays + ray];
+                // forward over the segment: transmittance before each sample, and its value
+                for (int k = k0; k < k1; ++k) {
+                    const float t = __fadd_rn(R.t0, __fmul_rn((float)k, step));
+                    const float p[3] = {__fadd_rn(R.o[0], __fmul_rn(t, R.d[0])), __fadd_rn(R.o[1], __fmul_rn(t, R.d[1])),
+                                        __fadd_rn(R.o[2], __fmul_rn(t, R.d[2]))};
+                    Resolved Q;
+                    resolve(s_l0, bshift, bmask, B1, p, Q);
+                    const uint32_t slot = __ldg(P.vol.pt + Q.pti);
+                    float val = 0.0f;
+                    if (slot != kInvalidSlot) {
+                        val = trilinear<DT>(atlas, (unsigned long long)slot * slot_elems + Q.local, B1, Q.w);
+                    } else {
+                        atomicAdd(&P.counters[kDevError], 1u);
+                    }
+                    const float x = tf_coord<DT>(val);
+                    const int i = min((int)x, 254);
+                    const float wt = x - (float)i;
+                    const float al = fmaf(wt, s_tf[i + 1].w - s_tf[i].w, s_tf[i].w);
+                    s_T[k - k0][tid] = T;
+                    s_V[k - k0][tid] = val;
+                    T = T * (1.0f - al);
+                }
+                // reverse over the segment
+                for (int k = k1 - 1; k >= k0; --k) {
+                    const float t = __fadd_rn(R.t0, __fmul_rn((float)k, step));
+                    const float p[3] = {__fadd_rn(R.o[0], __fmul_rn(t, R.d[0])), __fadd_rn(R.o[1], __fmul_rn(t, R.d[1])),
+                                        __fadd_rn(R.o[2], __fmul_rn(t, R.d[2]))};
+                    Resolved Q;
+                    resolve(s_l0, bshift, bmask, B1, p, Q);
+                    const float val = s_V[k - k0][tid];
+                    const float Tk = s_T[k - k0][tid];
+                    const float x = tf_coord<DT>(val);
+                    const int i = min((int)x, 254);
+                    const float wt = x - (float)i;
+                    const float4 a = s_tf[i], b = s_tf[i + 1];
+                    const float cr = fmaf(wt, b.x - a.x, a.x), cg = fmaf(wt, b.y - a.y, a.y);
+                    const float cb = fmaf(wt, b.z - a.z, a.z), al = fmaf(wt, b.w - a.w, a.w);
+                    const float dal = Tk * (g.x * (cr - R0) + g.y * (cg - R1) + g.z * (cb - R2) + g.w * (1.0f - R3));
+                    const float Ta = Tk * al;
+                    const float dr = g.x * Ta, dg = g.y * Ta, db = g.z * Ta;
+                    if (P.dtf) {
+                        const float w0 = 1.0f - wt;
+                        atomicAdd(&s_dtf[4 * i + 0], w0 * dr);
+                        atomicAdd(&s_dtf[4 * i + 1], w0 * dg);
+                        atomicAdd(&s_dtf[4 * i + 2], w0 * db);
+                        atomicAdd(&s_dtf[4 * i + 3], w0 * dal);
+                        atomicAdd(&s_dtf[4 * i + 4], wt * dr);
+                        atomicAdd(&s_dtf[4 * i + 5], wt * dg);
+                        atomicAdd(&s_dtf[4 * i + 6], wt * db);
+                        atomicAdd(&s_dtf[4 * i + 7], wt * dal);
+                    }
+                    if (P.dvox && tf_inside<DT>(val)) {
+                        const float dv = 255.0f * (dr * (b.x - a.x) + dg * (b.y - a.y) + db * (b.z - a.z) + dal * (b.w - a.w));
+                        if (dv != 0.0f) {
+                            const long long b0 = (long long)Q.i0[0] + (long long)Dx * ((long long)Q.i0[1] + (long long)Dy * Q.i0[2]);
+                            const long long sy = Dx, sz = (long long)Dx * Dy;
+                            const float wx = Q.w[0], wy = Q.w[1], wz = Q.w[2];
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+                                const float wgt = (cx ? wx : 1.0f - wx) * (cy ? wy : 1.0f - wy) * (cz ? wz : 1.0f - wz);
+                                if (wgt != 0.0f) atomicAdd(&P.dvox[b0 + cx + cy * sy + cz * sz], wgt * dv);
+                            }
+                        }
+                    }
+                    R0 = fmaf(al, cr - R0, R0);
+                    R1 = fmaf(al, cg - R1, R1);
+                    R2 = fmaf(al, cb - R2, R2);
+                    R3 = fmaf(al, 1.0f - R3, R3);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (P.dtf)
+        for (int i = threadIdx.x; i < 1024; i += blockDim.x)
+            if (s_dtf[i] != 0.0f) atomicAdd(&P.dtf[i], s_dtf[i]);
+}
+
+// ------------------------------------------------------------------ trace
+
+__global__ void k_trace(const __grid_constant__ TraceDev P) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P.npix) return;
+    Ray R;
+    make_ray(P.view, P.vol.D0f, P.pixels[2 * q], P.pixels[2 * q + 1], R);
+    int k = 0;
+    if (R.hit) {
+        for (;; ++k) {
+            const float t = __fadd_rn(R.t0, __fmul_rn((float)k, P.step));
+            if (!(t < R.t1)) break;
+            if (k >= P.max_samples) continue;
+            const float p[3] = {__fadd_rn(R.o[0], __fmul_rn(t, R.d[0])), __fadd_rn(R.o[1], __fmul_rn(t, R.d[1])),
+                                __fadd_rn(R.o[2], __fmul_rn(t, R.d[2]))};
+            const int l = P.lod_mode ? lod_level(t, P.view.lodscale, P.lod_bias, P.vol.nlevels) : 0;
+            const LevelDev& L = P.vol.lv[l];
+            Resolved Q;
+            resolve(L, P.vol.bshift, P.vol.bmask, P.vol.B1, p, Q);
+            vol_trace_rec rec;
+            rec.k = k;
+            rec.t_bits = __float_as_uint(t);
+            rec.level = l;
+            for (int a = 0; a < 3; ++a) {
+                rec.i0[a] = Q.i0[a];
+                rec.local[a] = Q.i0[a] & P.vol.bmask;
+            }
+            rec.pad = 0;
+            rec.brick_id = (int64_t)(Q.pti - L.pt_off);
+            rec.slot = P.vol.pt[Q.pti];
+            rec.pad2 = 0;
+            P.out[(long long)q * P.max_samples + k] = rec;
+        }
+    }
+    P.counts[q] = k;
+}
+
+const void* pick_render(int dtype, bool lod, bool grad) {
+#define VOLRC_PICK(DT)                                                              \
+    if (dtype == DT) {                                                              \
+        if (grad) return (const void*)k_render<DT, false, true>;                    \
+        return lod ? (const void*)k_render<DT, true, false> : (const void*)k_render<DT, false, false>; \
+    }
+    VOLRC_PICK(VOL_U8)
+    VOLRC_PICK(VOL_U16)
+    VOLRC_PICK(VOL_F16)
+    VOLRC_PICK(VOL_F32)
+#undef VOLRC_PICK
+    return nullptr;
+}
+
+const void* pick_backward(int dtype) {
+    switch (dtype) {
+    case VOL_U8: return (const void*)k_backward<VOL_U8>;
+    case VOL_U16: return (const void*)k_backward<VOL_U16>;
+    case VOL_F16: return (const void*)k_backward<VOL_F16>;
+    case VOL_F32: return (const void*)k_backward<VOL_F32>;
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+cudaError_t launch_render(int dtype, bool grad, const RenderDev& p, int grid, cudaStream_t s) {
+    const void* fn = pick_render(dtype, p.lod_mode != 0, grad);
+    if (!fn) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&p};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kRenderThreads), args, 0, s);
+}
+
+cudaError_t launch_backward(int dtype, const BackwardDev& p, int grid, cudaStream_t s) {
+    const void* fn = pick_backward(dtype);
+    if (!fn) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&p};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kRenderThreads), args, 0, s);
+}
+
+cudaError_t launch_trace(const TraceDev& p, cudaStream_t s) {
+    const int threads = 64;
+    k_trace<<<(p.npix + threads - 1) / threads, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+int render_blocks_per_sm(int dtype, bool grad) {
+    int n = 0;
+    const void* fn = pick_render(dtype, false, grad);
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kRenderThreads, 0) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+int backward_blocks_per_sm(int dtype) {
+    int n = 0;
+    const void* fn = pick_backward(dtype);
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kRenderThreads, 0) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace volrc

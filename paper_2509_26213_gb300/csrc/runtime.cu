@@ -1,0 +1,907 @@
+// runtime.cu -- host runtime behind the C ABI (include/vol.h).
+//
+// Owns one volume: the brick atlas (a cache of fixed-size slots, Sec. III-C's VRAM store
+// specialised to equally sized bricks), one page table per LOD level laid end to end
+// (Sec. III-E), host mirrors of the page tables and of slot ownership, the least-recently-
+// used eviction policy driven by per-slot usage stamps written by the render kernel
+// (Sec. III-C/III-E: garbage collection frees down to a 10% target), the brick-request loop
+// (Sec. III-H), and the buffers of the last render needed by the adjoint.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace volrc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int bpv_of(int dtype) {
+    switch (dtype) {
+    case VOL_U8: return 1;
+    case VOL_U16: return 2;
+    case VOL_F16: return 2;
+    case VOL_F32: return 4;
+    }
+    return 0;
+}
+
+bool conversion_ok(int src, int dst) {
+    if (src == dst) return true;
+    return (src == VOL_U16 && dst == VOL_F16) || (src == VOL_U8 && dst == VOL_F32) || (src == VOL_U16 && dst == VOL_F32);
+}
+
+int plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes, vol_layout* o, std::string& err) {
+    if (!dims || !o) { err = "null argument"; return VOL_ERR_INVALID_ARG; }
+    memset(o, 0, sizeof(*o));
+    const int bpv = bpv_of(dtype);
+    if (!bpv) { err = "unknown dtype"; return VOL_ERR_INVALID_ARG; }
+    if (brick < 4 || brick > 128 || (brick & (brick - 1))) { err = "brick must be a power of two in 4..128"; return VOL_ERR_INVALID_ARG; }
+    if (levels < 1 || levels > VOL_MAX_LEVELS) { err = "levels must be 1..16"; return VOL_ERR_INVALID_ARG; }
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > (1 << 24)) { err = "dims must be 1..2^24"; return VOL_ERR_INVALID_ARG; }
+    o->dtype = dtype;
+    o->brick = brick;
+    o->levels = levels;
+    o->bytes_per_voxel = bpv;
+    int64_t off = 0;
+    for (int l = 0; l < levels; ++l) {
+        for (int a = 0; a < 3; ++a) {
+            o->dims[a] = dims[a];
+            o->level_dims[l][a] = l == 0 ? dims[a] : (o->level_dims[l - 1][a] + 1) / 2;
+            o->level_bricks[l][a] = (o->level_dims[l][a] + brick - 1) / brick;
+        }
+        o->level_pt_offset[l] = off;
+        off += o->level_bricks[l][0] * o->level_bricks[l][1] * o->level_bricks[l][2];
+    }
+    if (off >= (int64_t)0xFFFFFFF0ll) { err = "too many bricks for 32-bit page-table indices"; return VOL_ERR_UNSUPPORTED; }
+    o->total_bricks = off;
+    const int64_t B1 = brick + 1;
+    o->slot_bytes = ((B1 * B1 * B1 * bpv + 255) / 256) * 256;
+    int64_t ns = cache_bytes == 0 ? off : (int64_t)(cache_bytes / (uint64_t)o->slot_bytes);
+    if (ns > off) ns = off;
+    if (ns < 1) { err = "cache smaller than one brick"; return VOL_ERR_INVALID_ARG; }
+    if (ns >= (int64_t)0xFFFFFFF0ll) { err = "too many slots"; return VOL_ERR_UNSUPPORTED; }
+    o->nslots = ns;
+    o->atlas_bytes = ns * o->slot_bytes;
+    return VOL_OK;
+}
+
+}  // namespace
+
+struct vol_s {
+    int device = 0;
+    int nsm = 1;
+    cudaStream_t stream = nullptr;
+    vol_layout lay{};
+    int dtype = 0, B = 0, bshift = 0, L = 1;
+    std::string err;
+
+    void* atlas = nullptr;
+    uint32_t* pt = nullptr;
+    unsigned* last_used = nullptr;
+    unsigned* counters = nullptr;     // kNumCounters words
+    unsigned* aux = nullptr;          // [0] downsample error word
+
+    std::vector<uint32_t> pt_host;    // page tables (mirror)
+    std::vector<uint32_t> owner;      // slot -> page-table index or invalid
+    std::vector<uint32_t> protect;    // slot -> operation epoch that must not evict it
+    std::vector<uint32_t> free_slots; // stack
+    uint32_t op_epoch = 1;
+    int64_t resident = 0;
+    std::vector<int64_t> level_resident;
+
+    // pending page-table updates
+    std::vector<uint32_t> upd_idx, upd_val;
+    uint32_t* upd_dev = nullptr;
+    size_t upd_cap = 0;
+
+    // render state
+    ViewDev* views_dev = nullptr;
+    int views_cap = 0;
+    std::vector<ViewDev> views_host;
+    int nviews = 0;
+    int ntiles = 0;
+    int64_t nrays = 0;
+    vol_params params{};
+    const float* tf = nullptr;
+    float* out = nullptr;
+    int32_t* nsamp = nullptr;
+    bool grad = false;
+    bool have_forward = false;
+    uint32_t frame = 0;
+
+    // misses
+    unsigned* req_table = nullptr;
+    uint32_t req_cap = 0;
+    unsigned* req_list = nullptr;
+    uint32_t req_list_cap = 0;
+    SuspRec* susp[2] = {nullptr, nullptr};
+    int64_t susp_cap = 0;
+    int susp_cur = 0;          // buffer holding the rays still suspended
+    int64_t nsusp = 0;         // rays still suspended
+    std::vector<uint32_t> last_requests;
+
+    // gradient state
+    float* ckpt = nullptr;
+    size_t ckpt_cap = 0;
+    int* ray_n = nullptr;
+    size_t ray_n_cap = 0;
+
+    // provider
+    vol_provider_fn prov = nullptr;
+    void* prov_user = nullptr;
+    int prov_dtype = 0;
+    void* stage_host = nullptr;
+    void* stage_dev = nullptr;
+    uint32_t* stage_slots_dev = nullptr;
+    int stage_bricks = 0;
+
+    vol_stats stats{};
+    int occ_cache[4][2] = {{0}};
+};
+
+namespace {
+
+int fail(vol_t v, int code, const std::string& msg) {
+    if (v) v->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(vol_t v, cudaError_t e, const char* what) {
+    return fail(v, e == cudaErrorMemoryAllocation ? VOL_ERR_OOM : VOL_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(v, call)                                                   \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail((v), e_, #call);      \
+    } while (0)
+
+VolDev vol_dev(const vol_t v) {
+    VolDev d{};
+    d.atlas = v->atlas;
+    d.slot_elems = (unsigned long long)(v->lay.slot_bytes / v->lay.bytes_per_voxel);
+    d.bshift = v->bshift;
+    d.bmask = v->B - 1;
+    d.B1 = v->B + 1;
+    d.nlevels = v->L;
+    d.pt = v->pt;
+    for (int l = 0; l < v->L; ++l) {
+        for (int a = 0; a < 3; ++a) {
+            d.lv[l].D[a] = (int)v->lay.level_dims[l][a];
+            d.lv[l].nb[a] = (int)v->lay.level_bricks[l][a];
+            d.lv[l].r[a] = (float)v->lay.level_dims[l][a] / (float)v->lay.level_dims[0][a];
+        }
+        d.lv[l].pt_off = (uint32_t)v->lay.level_pt_offset[l];
+    }
+    for (int a = 0; a < 3; ++a) d.D0f[a] = (float)v->lay.dims[a];
+    return d;
+}
+
+int64_t level_nbricks(const vol_t v, int l) {
+    return v->lay.level_bricks[l][0] * v->lay.level_bricks[l][1] * v->lay.level_bricks[l][2];
+}
+
+int level_of_pti(const vol_t v, uint32_t pti) {
+    int l = 0;
+    while (l + 1 < v->L && (int64_t)pti >= v->lay.level_pt_offset[l + 1]) ++l;
+    return l;
+}
+
+template <class T>
+int ensure(vol_t v, T*& ptr, size_t& cap, size_t n, const char* what) {
+    if (n <= cap && ptr) return VOL_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc((void**)&ptr, sizeof(T) * std::max<size_t>(n, 1));
+    if (e != cudaSuccess) return cuda_fail(v, e, what);
+    cap = std::max<size_t>(n, 1);
+    return VOL_OK;
+}
+
+int flush_pt_updates(vol_t v) {
+    const size_t n = v->upd_idx.size();
+    if (!n) return VOL_OK;
+    if (int rc = ensure(v, v->upd_dev, v->upd_cap, 2 * n, "page-table update buffer")) return rc;
+    std::vector<uint32_t> packed(2 * n);
+    std::copy(v->upd_idx.begin(), v->upd_idx.end(), packed.begin());
+    std::copy(v->upd_val.begin(), v->upd_val.end(), packed.begin() + n);
+    CK(v, cudaMemcpyAsync(v->upd_dev, packed.data(), sizeof(uint32_t) * 2 * n, cudaMemcpyHostToDevice, v->stream));
+    CK(v, launch_pt_update(v->pt, v->upd_dev, v->upd_dev + n, (int)n, v->stream));
+    v->upd_idx.clear();
+    v->upd_val.clear();
+    return VOL_OK;
+}
+
+void set_entry(vol_t v, uint32_t pti, uint32_t slot) {
+    const uint32_t old = v->pt_host[pti];
+    const int l = level_of_pti(v, pti);
+    if (old == kInvalidSlot && slot != kInvalidSlot) { ++v->resident; ++v->level_resident[l]; }
+    if (old != kInvalidSlot && slot == kInvalidSlot) { --v->resident; --v->level_resident[l]; }
+    v->pt_host[pti] = slot;
+    v->upd_idx.push_back(pti);
+    v->upd_val.push_back(slot);
+}
+
+// Least-recently-used eviction (usage stamps written by the render kernel).  Frees slots
+// until `need` are free and at least 10% of the atlas is free (the collection target),
+// never a slot protected by the current operation; slots used in the current frame only
+// when nothing older is left.
+int evict_lru(vol_t v, size_t need) {
+    const int64_t ns = v->lay.nslots;
+    std::vector<uint32_t> stamp(ns);
+    CK(v, cudaMemcpyAsync(stamp.data(), v->last_used, sizeof(uint32_t) * ns, cudaMemcpyDeviceToHost, v->stream));
+    CK(v, cudaStreamSynchronize(v->stream));
+    std::vector<uint32_t> cand;
+    cand.reserve(ns);
+    for (int64_t s = 0; s < ns; ++s)
+        if (v->owner[s] != kInvalidSlot && v->protect[s] != v->op_epoch) cand.push_back((uint32_t)s);
+    // age order: older frames first; the current frame last
+    std::stable_sort(cand.begin(), cand.end(), [&](uint32_t a, uint32_t b) {
+        const uint32_t fa = stamp[a] == v->frame ? 0xFFFFFFFFu : stamp[a];
+        const uint32_t fb = stamp[b] == v->frame ? 0xFFFFFFFFu : stamp[b];
+        return fa < fb;
+    });
+    const size_t target = std::max<size_t>(need, (size_t)(ns / 10));
+    size_t i = 0;
+    while (v->free_slots.size() < target && i < cand.size()) {
+        const uint32_t s = cand[i++];
+        set_entry(v, v->owner[s], kInvalidSlot);
+        v->owner[s] = kInvalidSlot;
+        v->free_slots.push_back(s);
+        v->stats.evicted++;
+    }
+    if (v->free_slots.size() < need) return fail(v, VOL_ERR_CACHE_FULL, "brick cache full: nothing evictable");
+    return flush_pt_updates(v);
+}
+
+// Slot for page-table entry pti (existing one if resident), protected for this operation.
+int slot_for(vol_t v, uint32_t pti, uint32_t* out) {
+    uint32_t s = v->pt_host[pti];
+    if (s == kInvalidSlot) {
+        if (v->free_slots.empty())
+            if (int rc = evict_lru(v, 1)) return rc;
+        s = v->free_slots.back();
+        v->free_slots.pop_back();
+        v->owner[s] = pti;
+        set_entry(v, pti, s);
+    }
+    v->protect[s] = v->op_epoch;
+    *out = s;
+    return VOL_OK;
+}
+
+int brick_pti(const vol_t v, int level, const int32_t b[3], uint32_t* pti) {
+    if (level < 0 || level >= v->L || !b) return VOL_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (b[a] < 0 || b[a] >= v->lay.level_bricks[level][a]) return VOL_ERR_INVALID_ARG;
+    *pti = (uint32_t)(v->lay.level_pt_offset[level] + b[0] +
+                      v->lay.level_bricks[level][0] * (b[1] + v->lay.level_bricks[level][1] * (int64_t)b[2]));
+    return VOL_OK;
+}
+
+bool all_resident(const vol_t v, bool lod) {
+    const int n = lod ? v->L : 1;
+    for (int l = 0; l < n; ++l)
+        if (v->level_resident[l] != level_nbricks(v, l)) return false;
+    return true;
+}
+
+int grid_for(vol_t v, int dtype, bool grad, int ctas_per_sm) {
+    int& occ = v->occ_cache[dtype][grad ? 1 : 0];
+    if (!occ) occ = render_blocks_per_sm(dtype, grad);
+    int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+    return std::max(1, per * v->nsm);
+}
+
+int ensure_miss_buffers(vol_t v) {
+    if (!v->req_table) {
+        v->req_cap = 1u << 16;
+        v->req_list_cap = 1u << 16;
+        CK(v, cudaMalloc((void**)&v->req_table, sizeof(unsigned) * v->req_cap));
+        CK(v, cudaMalloc((void**)&v->req_list, sizeof(unsigned) * v->req_list_cap));
+    }
+    if (v->susp_cap < v->nrays) {
+        for (int i = 0; i < 2; ++i) {
+            if (v->susp[i]) cudaFree(v->susp[i]);
+            v->susp[i] = nullptr;
+        }
+        v->susp_cap = 0;
+        for (int i = 0; i < 2; ++i) CK(v, cudaMalloc((void**)&v->susp[i], sizeof(SuspRec) * (size_t)v->nrays));
+        v->susp_cap = v->nrays;
+    }
+    return VOL_OK;
+}
+
+RenderDev render_args(vol_t v) {
+    RenderDev p{};
+    p.vol = vol_dev(v);
+    p.views = v->views_dev;
+    p.nviews = v->nviews;
+    p.tile_w = v->params.tile_w;
+    p.tile_h = v->params.tile_h;
+    p.refill_thresh = v->params.refill;
+    p.tf = (const float4*)v->tf;
+    p.step = v->params.step;
+    p.et = v->params.et_threshold;
+    p.bg = make_float4(v->params.bg[0], v->params.bg[1], v->params.bg[2], v->params.bg[3]);
+    p.lod_mode = v->params.lod_mode;
+    p.lod_bias = v->params.lod_bias;
+    p.out = (float4*)v->out;
+    p.nsamp = v->nsamp;
+    p.counters = v->counters;
+    p.last_used = v->last_used;
+    p.frame = v->frame;
+    p.nrays = v->nrays;
+    if (v->grad) {
+        p.ckpt = v->ckpt;
+        p.ray_n = v->ray_n;
+    }
+    return p;
+}
+
+// One kernel pass.  resume = false: all tiles; true: the rays suspended in susp[susp_cur].
+int run_pass(vol_t v, bool resume, bool may_miss) {
+    RenderDev p = render_args(v);
+    if (may_miss) {
+        p.req_table = v->req_table;
+        p.req_cap_mask = v->req_cap - 1;
+        p.req_list = v->req_list;
+        p.req_list_cap = v->req_list_cap;
+        CK(v, cudaMemsetAsync(v->req_table, 0, sizeof(unsigned) * v->req_cap, v->stream));
+    }
+    if (resume) {
+        p.resume = 1;
+        p.susp_in = v->susp[v->susp_cur];
+        p.nsusp_in = (int)v->nsusp;
+        p.susp_out = v->susp[v->susp_cur ^ 1];
+        p.nwork = (int)((v->nsusp + 31) / 32);
+    } else {
+        p.resume = 0;
+        p.susp_out = v->susp[v->susp_cur];
+        p.nwork = v->ntiles;
+    }
+    CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
+    const int grid = grid_for(v, v->dtype, v->grad, v->params.ctas_per_sm);
+    CK(v, launch_render(v->dtype, v->grad, p, grid, v->stream));
+    v->stats.passes++;
+    return VOL_OK;
+}
+
+// After a pass that may have missed: read counters, keep the request list, and switch the
+// suspended-ray buffer.  Synchronises.
+int collect_pass(vol_t v, bool resumed) {
+    unsigned c[kNumCounters];
+    CK(v, cudaMemcpyAsync(c, v->counters, sizeof(c), cudaMemcpyDeviceToHost, v->stream));
+    CK(v, cudaStreamSynchronize(v->stream));
+    v->stats.device_error += c[kDevError];
+    v->stats.request_overflow += c[kReqOverflow];
+    const uint32_t nreq = std::min<uint32_t>(c[kReqCount], v->req_list_cap);
+    v->stats.requests += nreq;
+    v->stats.suspended += c[kSuspCount];
+    v->last_requests.resize(nreq);
+    if (nreq)
+        CK(v, cudaMemcpy(v->last_requests.data(), v->req_list, sizeof(uint32_t) * nreq, cudaMemcpyDeviceToHost));
+    v->nsusp = c[kSuspCount];
+    if (resumed) v->susp_cur ^= 1;
+    if (c[kDevError]) return fail(v, VOL_ERR_DEVICE, "device-side check failed during render");
+    return VOL_OK;
+}
+
+int ensure_stage(vol_t v) {
+    if (v->stage_host) return VOL_OK;
+    const int64_t B1 = v->B + 1;
+    const size_t brick_bytes = (size_t)(B1 * B1 * B1) * 4;  // room for the widest source type
+    v->stage_bricks = (int)std::max<int64_t>(1, std::min<int64_t>(256, (64ll << 20) / (int64_t)brick_bytes));
+    CK(v, cudaMallocHost(&v->stage_host, brick_bytes * v->stage_bricks));
+    CK(v, cudaMalloc(&v->stage_dev, brick_bytes * v->stage_bricks));
+    CK(v, cudaMalloc((void**)&v->stage_slots_dev, sizeof(uint32_t) * v->stage_bricks));
+    return VOL_OK;
+}
+
+// Loads the requested bricks through the provider in batches and publishes them.
+int load_requests(vol_t v) {
+    if (int rc = ensure_stage(v)) return rc;
+    const int64_t B1 = v->B + 1;
+    const size_t nvox = (size_t)(B1 * B1 * B1);
+    const size_t src_bytes = nvox * bpv_of(v->prov_dtype);
+    ++v->op_epoch;
+    const std::vector<uint32_t> reqs = v->last_requests;
+    std::vector<uint32_t> slots;
+    const int64_t loaded0 = v->stats.bricks_loaded;
+    bool full = false;
+    for (size_t i0 = 0; i0 < reqs.size() && !full; i0 += v->stage_bricks) {
+        size_t n = std::min<size_t>(v->stage_bricks, reqs.size() - i0);
+        slots.assign(n, kInvalidSlot);
+        for (size_t j = 0; j < n; ++j) {
+            const uint32_t pti = reqs[i0 + j] - 1u;
+            if (pti >= v->pt_host.size()) return fail(v, VOL_ERR_DEVICE, "corrupt brick request");
+            if (v->pt_host[pti] != kInvalidSlot) {  // already resident (e.g. a duplicate)
+                v->protect[v->pt_host[pti]] = v->op_epoch;
+                continue;
+            }
+            const int l = level_of_pti(v, pti);
+            const int64_t id = (int64_t)pti - v->lay.level_pt_offset[l];
+            const int64_t nbx = v->lay.level_bricks[l][0], nby = v->lay.level_bricks[l][1];
+            const int32_t b[3] = {(int32_t)(id % nbx), (int32_t)((id / nbx) % nby), (int32_t)(id / (nbx * nby))};
+            if (v->prov(v->prov_user, l, b, (char*)v->stage_host + j * src_bytes) != 0)
+                return fail(v, VOL_ERR_PROVIDER, "brick provider failed");
+            uint32_t s;
+            if (int rc = slot_for(v, pti, &s)) {
+                // the cache cannot take more bricks in this pass: load what fits, the rest is
+                // requested again by the rays that still wait for it
+                if (rc == VOL_ERR_CACHE_FULL && (v->stats.bricks_loaded > loaded0 || j > 0)) {
+                    full = true;
+                    break;
+                }
+                return rc;
+            }
+            slots[j] = s;
+            v->stats.bricks_loaded++;
+            v->stats.bytes_loaded += (int64_t)src_bytes;
+        }
+        if (full) {
+            size_t used = 0;
+            for (size_t j = 0; j < n; ++j)
+                if (slots[j] != kInvalidSlot) used = j + 1;
+            n = used;
+        }
+        CK(v, cudaMemcpyAsync(v->stage_dev, v->stage_host, src_bytes * n, cudaMemcpyHostToDevice, v->stream));
+        CK(v, cudaMemcpyAsync(v->stage_slots_dev, slots.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, v->stream));
+        CK(v, launch_upload_bricks(v->dtype, v->prov_dtype, v->stage_dev, vol_dev(v), v->stage_slots_dev, (long long)n,
+                                   v->stream));
+        if (int rc = flush_pt_updates(v)) return rc;
+        CK(v, cudaStreamSynchronize(v->stream));  // the pinned stage is reused by the next batch
+    }
+    return VOL_OK;
+}
+
+// Miss loop: load and resume until no ray is suspended or passes run out.
+int miss_loop(vol_t v, bool first_resumed) {
+    if (int rc = collect_pass(v, first_resumed)) return rc;
+    const int max_passes = v->params.max_passes > 0 ? v->params.max_passes : 64;
+    while (v->nsusp > 0) {
+        if (!v->prov) return fail(v, VOL_ERR_INCOMPLETE, "rays wait for non-resident bricks (no provider)");
+        if (v->stats.passes >= max_passes) return fail(v, VOL_ERR_INCOMPLETE, "max_passes reached");
+        if (int rc = load_requests(v)) return rc;
+        if (int rc = run_pass(v, true, true)) return rc;
+        if (int rc = collect_pass(v, true)) return rc;
+    }
+    return VOL_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+int vol_plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes, vol_layout* out) {
+    std::string err;
+    return plan(dims, dtype, brick, levels, cache_bytes, out, err);
+}
+
+int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes, void* stream,
+               vol_t* out) {
+    if (!out) return fail(nullptr, VOL_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    vol_layout lay;
+    std::string err;
+    if (int rc = plan(dims, dtype, brick, levels, cache_bytes, &lay, err)) return fail(nullptr, rc, err);
+    vol_t v = new vol_s();
+    v->lay = lay;
+    v->dtype = dtype;
+    v->B = brick;
+    v->bshift = 0;
+    while ((1 << v->bshift) < brick) ++v->bshift;
+    v->L = levels;
+    v->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&v->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v->nsm, cudaDevAttrMultiProcessorCount, v->device);
+    if (e == cudaSuccess) e = cudaMalloc(&v->atlas, (size_t)lay.atlas_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v->pt, sizeof(uint32_t) * (size_t)lay.total_bricks);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v->last_used, sizeof(unsigned) * (size_t)lay.nslots);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v->counters, sizeof(unsigned) * kNumCounters);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v->aux, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * (size_t)lay.total_bricks, v->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->last_used, 0, sizeof(unsigned) * (size_t)lay.nslots, v->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->aux, 0, sizeof(unsigned) * 4, v->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(v->stream);
+    if (e != cudaSuccess) {
+        const int code = e == cudaErrorMemoryAllocation ? VOL_ERR_OOM : VOL_ERR_CUDA;
+        std::string msg = std::string("vol_create: ") + cudaGetErrorString(e);
+        vol_destroy(v);
+        return fail(nullptr, code, msg);
+    }
+    v->pt_host.assign((size_t)lay.total_bricks, kInvalidSlot);
+    v->owner.assign((size_t)lay.nslots, kInvalidSlot);
+    v->protect.assign((size_t)lay.nslots, 0);
+    v->free_slots.resize((size_t)lay.nslots);
+    for (int64_t s = 0; s < lay.nslots; ++s) v->free_slots[(size_t)s] = (uint32_t)(lay.nslots - 1 - s);
+    v->level_resident.assign(levels, 0);
+    *out = v;
+    return VOL_OK;
+}
+
+void vol_destroy(vol_t v) {
+    if (!v) return;
+    if (v->stream) cudaStreamSynchronize(v->stream);
+    else cudaDeviceSynchronize();
+    void* bufs[] = {v->atlas, v->pt, v->last_used, v->counters, v->aux, v->upd_dev, v->views_dev, v->req_table,
+                    v->req_list, v->susp[0], v->susp[1], v->ckpt, v->ray_n, v->stage_dev, v->stage_slots_dev};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (v->stage_host) cudaFreeHost(v->stage_host);
+    delete v;
+}
+
+const char* vol_last_error(vol_t v) { return v ? v->err.c_str() : g_create_error.c_str(); }
+
+int vol_set_stream(vol_t v, void* stream) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    v->stream = (cudaStream_t)stream;
+    return VOL_OK;
+}
+
+int vol_get_layout(vol_t v, vol_layout* out) {
+    if (!v || !out) return VOL_ERR_INVALID_ARG;
+    *out = v->lay;
+    return VOL_OK;
+}
+
+int vol_get_stats(vol_t v, vol_stats* out) {
+    if (!v || !out) return VOL_ERR_INVALID_ARG;
+    unsigned c[kNumCounters], aux[4];
+    CK(v, cudaMemcpyAsync(c, v->counters, sizeof(c), cudaMemcpyDeviceToHost, v->stream));
+    CK(v, cudaMemcpyAsync(aux, v->aux, sizeof(aux), cudaMemcpyDeviceToHost, v->stream));
+    CK(v, cudaStreamSynchronize(v->stream));
+    std::vector<uint32_t> stamp((size_t)v->lay.nslots);
+    CK(v, cudaMemcpy(stamp.data(), v->last_used, sizeof(uint32_t) * stamp.size(), cudaMemcpyDeviceToHost));
+    *out = v->stats;
+    out->touched = 0;
+    for (size_t s = 0; s < stamp.size(); ++s)
+        if (v->owner[s] != kInvalidSlot && stamp[s] == v->frame && v->frame) out->touched++;
+    out->resident = v->resident;
+    out->frame = v->frame;
+    out->device_error = v->stats.device_error + c[kDevError] + aux[0];
+    return VOL_OK;
+}
+
+int vol_upload_level(vol_t v, int level, const void* src, int src_dtype, int src_on_device) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    if (level < 0 || level >= v->L || !src) return fail(v, VOL_ERR_INVALID_ARG, "bad level or src");
+    if (!bpv_of(src_dtype)) return fail(v, VOL_ERR_INVALID_ARG, "bad src dtype");
+    if (!conversion_ok(src_dtype, v->dtype)) return fail(v, VOL_ERR_UNSUPPORTED, "unsupported conversion");
+    const int64_t nb = level_nbricks(v, level);
+    if (nb > v->lay.nslots) return fail(v, VOL_ERR_CACHE_FULL, "level does not fit the brick cache");
+    ++v->op_epoch;
+    std::vector<uint32_t> slots((size_t)nb);
+    for (int64_t b = 0; b < nb; ++b)
+        if (int rc = slot_for(v, (uint32_t)(v->lay.level_pt_offset[level] + b), &slots[(size_t)b])) return rc;
+    const int64_t nvox = v->lay.level_dims[level][0] * v->lay.level_dims[level][1] * v->lay.level_dims[level][2];
+    const size_t sbytes = (size_t)nvox * bpv_of(src_dtype);
+    const void* dsrc = src;
+    void* tmp = nullptr;
+    uint32_t* dslots = nullptr;
+    CK(v, cudaMalloc((void**)&dslots, sizeof(uint32_t) * (size_t)nb));
+    if (!src_on_device) {
+        cudaError_t e = cudaMalloc(&tmp, sbytes);
+        if (e != cudaSuccess) { cudaFree(dslots); return cuda_fail(v, e, "upload staging"); }
+        e = cudaMemcpyAsync(tmp, src, sbytes, cudaMemcpyHostToDevice, v->stream);
+        if (e != cudaSuccess) { cudaFree(dslots); cudaFree(tmp); return cuda_fail(v, e, "upload copy"); }
+        dsrc = tmp;
+    }
+    cudaError_t e = cudaMemcpyAsync(dslots, slots.data(), sizeof(uint32_t) * (size_t)nb, cudaMemcpyHostToDevice, v->stream);
+    if (e == cudaSuccess) e = launch_upload_level(v->dtype, src_dtype, dsrc, vol_dev(v), level, dslots, nb, v->stream);
+    int rc = e == cudaSuccess ? flush_pt_updates(v) : cuda_fail(v, e, "upload_level kernel");
+    cudaError_t e2 = cudaStreamSynchronize(v->stream);
+    cudaFree(dslots);
+    if (tmp) cudaFree(tmp);
+    if (rc) return rc;
+    if (e2 != cudaSuccess) return cuda_fail(v, e2, "upload_level");
+    return VOL_OK;
+}
+
+int vol_upload_brick(vol_t v, int level, const int32_t brick[3], const void* src, int src_dtype, int src_on_device) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    uint32_t pti;
+    if (!src || brick_pti(v, level, brick, &pti)) return fail(v, VOL_ERR_INVALID_ARG, "bad level, brick or src");
+    if (!conversion_ok(src_dtype, v->dtype)) return fail(v, VOL_ERR_UNSUPPORTED, "unsupported conversion");
+    if (int rc = ensure_stage(v)) return rc;
+    ++v->op_epoch;
+    uint32_t s;
+    if (int rc = slot_for(v, pti, &s)) return rc;
+    const int64_t B1 = v->B + 1;
+    const size_t bytes = (size_t)(B1 * B1 * B1) * bpv_of(src_dtype);
+    const void* dsrc = src;
+    if (!src_on_device) {
+        CK(v, cudaMemcpyAsync(v->stage_dev, src, bytes, cudaMemcpyHostToDevice, v->stream));
+        dsrc = v->stage_dev;
+    }
+    CK(v, cudaMemcpyAsync(v->stage_slots_dev, &s, sizeof(uint32_t), cudaMemcpyHostToDevice, v->stream));
+    CK(v, launch_upload_bricks(v->dtype, src_dtype, dsrc, vol_dev(v), v->stage_slots_dev, 1, v->stream));
+    if (int rc = flush_pt_updates(v)) return rc;
+    CK(v, cudaStreamSynchronize(v->stream));
+    return VOL_OK;
+}
+
+int vol_build_lod(vol_t v, int from_level) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    if (from_level < 0 || from_level >= v->L) return fail(v, VOL_ERR_INVALID_ARG, "bad from_level");
+    for (int l = from_level + 1; l < v->L; ++l) {
+        if (v->level_resident[l - 1] != level_nbricks(v, l - 1))
+            return fail(v, VOL_ERR_INVALID_ARG, "source level not fully resident");
+        const int64_t nb = level_nbricks(v, l);
+        if (nb + level_nbricks(v, l - 1) > v->lay.nslots)
+            return fail(v, VOL_ERR_CACHE_FULL, "levels do not fit the brick cache");
+        ++v->op_epoch;
+        // keep the source level while allocating the coarse one
+        for (int64_t b = 0; b < level_nbricks(v, l - 1); ++b)
+            v->protect[v->pt_host[(size_t)(v->lay.level_pt_offset[l - 1] + b)]] = v->op_epoch;
+        std::vector<uint32_t> slots((size_t)nb);
+        for (int64_t b = 0; b < nb; ++b)
+            if (int rc = slot_for(v, (uint32_t)(v->lay.level_pt_offset[l] + b), &slots[(size_t)b])) return rc;
+        uint32_t* dslots = nullptr;
+        CK(v, cudaMalloc((void**)&dslots, sizeof(uint32_t) * (size_t)nb));
+        cudaError_t e = cudaMemcpyAsync(dslots, slots.data(), sizeof(uint32_t) * (size_t)nb, cudaMemcpyHostToDevice, v->stream);
+        int rc = VOL_OK;
+        if (e == cudaSuccess) rc = flush_pt_updates(v);  // the source level's entries must be live
+        if (e == cudaSuccess && !rc) e = launch_downsample(v->dtype, vol_dev(v), l, dslots, nb, v->aux, v->stream);
+        cudaError_t e2 = cudaStreamSynchronize(v->stream);
+        cudaFree(dslots);
+        if (rc) return rc;
+        if (e != cudaSuccess) return cuda_fail(v, e, "downsample");
+        if (e2 != cudaSuccess) return cuda_fail(v, e2, "downsample");
+    }
+    unsigned aux0 = 0;
+    CK(v, cudaMemcpy(&aux0, v->aux, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (aux0) return fail(v, VOL_ERR_DEVICE, "downsample met a non-resident brick");
+    return VOL_OK;
+}
+
+int vol_download_brick(vol_t v, int level, const int32_t brick[3], void* dst) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    uint32_t pti;
+    if (!dst || brick_pti(v, level, brick, &pti)) return fail(v, VOL_ERR_INVALID_ARG, "bad level, brick or dst");
+    const uint32_t s = v->pt_host[pti];
+    if (s == kInvalidSlot) return fail(v, VOL_ERR_INVALID_ARG, "brick not resident");
+    const int64_t B1 = v->B + 1;
+    const size_t bytes = (size_t)(B1 * B1 * B1) * v->lay.bytes_per_voxel;
+    CK(v, cudaMemcpyAsync(dst, (const char*)v->atlas + (size_t)s * v->lay.slot_bytes, bytes, cudaMemcpyDeviceToHost,
+                          v->stream));
+    CK(v, cudaStreamSynchronize(v->stream));
+    return VOL_OK;
+}
+
+int vol_evict_all(vol_t v) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    for (int64_t s = 0; s < v->lay.nslots; ++s)
+        if (v->owner[(size_t)s] != kInvalidSlot) {
+            v->owner[(size_t)s] = kInvalidSlot;
+            v->free_slots.push_back((uint32_t)s);
+        }
+    std::fill(v->pt_host.begin(), v->pt_host.end(), kInvalidSlot);
+    std::fill(v->level_resident.begin(), v->level_resident.end(), 0);
+    v->resident = 0;
+    v->upd_idx.clear();
+    v->upd_val.clear();
+    CK(v, cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * (size_t)v->lay.total_bricks, v->stream));
+    v->have_forward = false;
+    return VOL_OK;
+}
+
+int vol_set_provider(vol_t v, vol_provider_fn fn, void* user, int src_dtype) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    if (fn && !conversion_ok(src_dtype, v->dtype)) return fail(v, VOL_ERR_UNSUPPORTED, "unsupported provider dtype");
+    v->prov = fn;
+    v->prov_user = user;
+    v->prov_dtype = src_dtype;
+    return VOL_OK;
+}
+
+int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev, const vol_params* params,
+               float* rgba_dev, int32_t* nsamples_dev) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    if (!cams || !tf_dev || !params || !rgba_dev) return fail(v, VOL_ERR_INVALID_ARG, "null argument");
+    if (nviews < 1 || nviews > VOL_MAX_VIEWS) return fail(v, VOL_ERR_INVALID_ARG, "nviews out of range");
+    vol_params p = *params;
+    if (!(p.step > 0.0f) || !std::isfinite(p.step)) return fail(v, VOL_ERR_INVALID_ARG, "step must be > 0");
+    if (p.tile_w <= 0) p.tile_w = 8;
+    if (p.tile_h <= 0) p.tile_h = 8;
+    if ((p.tile_w * p.tile_h) % 32 != 0 || p.tile_w * p.tile_h > 4096)
+        return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be a multiple of 32, at most 4096");
+    if (p.refill <= 0 || p.refill > 32) p.refill = 24;
+    if (p.lod_mode != 0 && p.lod_mode != 1) return fail(v, VOL_ERR_INVALID_ARG, "lod_mode must be 0 or 1");
+    const bool grad = (p.flags & VOL_RENDER_GRAD) != 0;
+    if (grad && p.lod_mode != 0) return fail(v, VOL_ERR_UNSUPPORTED, "gradients need lod_mode 0");
+
+    // view table
+    v->views_host.resize(nviews);
+    int64_t rays = 0;
+    int64_t tiles = 0;
+    for (int i = 0; i < nviews; ++i) {
+        const vol_camera& c = cams[i];
+        if (c.w < 1 || c.h < 1 || c.w > 65536 || c.h > 65536) return fail(v, VOL_ERR_INVALID_ARG, "bad image size");
+        ViewDev& V = v->views_host[i];
+        for (int a = 0; a < 3; ++a) {
+            V.eye[a] = c.eye[a];
+            V.right[a] = c.right[a];
+            V.up[a] = c.up[a];
+            V.fwd[a] = c.fwd[a];
+        }
+        V.tan = c.tan_half_fov;
+        V.tan_aspect = c.tan_half_fov * c.aspect;
+        V.lodscale = (2.0f * c.tan_half_fov) / (float)c.h;
+        V.w = c.w;
+        V.h = c.h;
+        V.tiles_x = (c.w + p.tile_w - 1) / p.tile_w;
+        V.tile_off = (int)tiles;
+        V.ray_off = rays;
+        tiles += (int64_t)V.tiles_x * ((c.h + p.tile_h - 1) / p.tile_h);
+        rays += (int64_t)c.w * c.h;
+    }
+    if (tiles >= (1ll << 31)) return fail(v, VOL_ERR_INVALID_ARG, "too many tiles");
+    if (v->views_cap < nviews) {
+        if (v->views_dev) cudaFree(v->views_dev);
+        v->views_dev = nullptr;
+        v->views_cap = 0;
+        CK(v, cudaMalloc((void**)&v->views_dev, sizeof(ViewDev) * nviews));
+        v->views_cap = nviews;
+    }
+    CK(v, cudaMemcpyAsync(v->views_dev, v->views_host.data(), sizeof(ViewDev) * nviews, cudaMemcpyHostToDevice, v->stream));
+    v->nviews = nviews;
+    v->ntiles = (int)tiles;
+    v->nrays = rays;
+    v->params = p;
+    v->tf = tf_dev;
+    v->out = rgba_dev;
+    v->nsamp = nsamples_dev;
+    v->grad = grad;
+    v->have_forward = false;
+    v->nsusp = 0;
+    v->susp_cur = 0;
+    ++v->frame;
+    v->stats = vol_stats{};
+    v->stats.rays = rays;
+
+    if (grad) {
+        double diag = 0.0;
+        for (int a = 0; a < 3; ++a) diag += (double)v->lay.dims[a] * (double)v->lay.dims[a];
+        const int64_t max_n = (int64_t)std::ceil(std::sqrt(diag) / (double)p.step) + 2;
+        const int64_t segs = (max_n + kCkptEvery - 1) / kCkptEvery;
+        if (int rc = ensure(v, v->ckpt, v->ckpt_cap, (size_t)std::max<int64_t>(1, segs - 1) * (size_t)rays, "checkpoints")) return rc;
+        if (int rc = ensure(v, v->ray_n, v->ray_n_cap, (size_t)rays, "ray sample counts")) return rc;
+    }
+    const bool may_miss = !all_resident(v, p.lod_mode != 0);
+    if (may_miss)
+        if (int rc = ensure_miss_buffers(v)) return rc;
+    if (int rc = run_pass(v, false, may_miss)) return rc;
+    if (!may_miss) {
+        v->have_forward = true;
+        return VOL_OK;
+    }
+    int rc = miss_loop(v, false);
+    if (rc == VOL_OK) v->have_forward = true;
+    return rc;
+}
+
+int vol_render_resume(vol_t v) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    if (!v->out) return fail(v, VOL_ERR_NO_FORWARD_STATE, "no render to resume");
+    if (v->nsusp == 0) return VOL_OK;
+    if (int rc = run_pass(v, true, true)) return rc;
+    int rc = miss_loop(v, true);
+    if (rc == VOL_OK) v->have_forward = true;
+    return rc;
+}
+
+int vol_poll_requests(vol_t v, int32_t* out, int cap, int* n) {
+    if (!v || !n || (cap > 0 && !out)) return VOL_ERR_INVALID_ARG;
+    *n = (int)v->last_requests.size();
+    for (int i = 0; i < cap && i < *n; ++i) {
+        const uint32_t pti = v->last_requests[i] - 1u;
+        const int l = level_of_pti(v, pti);
+        const int64_t id = (int64_t)pti - v->lay.level_pt_offset[l];
+        const int64_t nbx = v->lay.level_bricks[l][0], nby = v->lay.level_bricks[l][1];
+        out[4 * i + 0] = l;
+        out[4 * i + 1] = (int32_t)(id % nbx);
+        out[4 * i + 2] = (int32_t)((id / nbx) % nby);
+        out[4 * i + 3] = (int32_t)(id / (nbx * nby));
+    }
+    return VOL_OK;
+}
+
+int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* dvoxel_dev) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    if (!drgba_dev) return fail(v, VOL_ERR_INVALID_ARG, "drgba is NULL");
+    if (!v->have_forward || !v->grad) return fail(v, VOL_ERR_NO_FORWARD_STATE, "no gradient-mode render to differentiate");
+    if (v->nsusp) return fail(v, VOL_ERR_NO_FORWARD_STATE, "last render is incomplete");
+    if (!all_resident(v, false)) return fail(v, VOL_ERR_NO_FORWARD_STATE, "level 0 changed since the render");
+    if (!dtf_dev && !dvoxel_dev) return VOL_OK;
+    BackwardDev b{};
+    b.vol = vol_dev(v);
+    b.views = v->views_dev;
+    b.nviews = v->nviews;
+    b.nwork = v->ntiles;
+    b.tile_w = v->params.tile_w;
+    b.tile_h = v->params.tile_h;
+    b.tf = (const float4*)v->tf;
+    b.step = v->params.step;
+    b.bg = make_float4(v->params.bg[0], v->params.bg[1], v->params.bg[2], v->params.bg[3]);
+    b.drgba = (const float4*)drgba_dev;
+    b.dtf = dtf_dev;
+    b.dvox = dvoxel_dev;
+    for (int a = 0; a < 3; ++a) b.D0[a] = (int)v->lay.dims[a];
+    b.counters = v->counters;
+    b.ckpt = v->ckpt;
+    b.nrays = v->nrays;
+    b.ray_n = v->ray_n;
+    CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
+    const int grid = backward_blocks_per_sm(v->dtype) * v->nsm;
+    CK(v, launch_backward(v->dtype, b, grid, v->stream));
+    return VOL_OK;
+}
+
+int vol_trace(vol_t v, const vol_camera* cam, const vol_params* params, const int32_t* pixels_host, int npix,
+              int max_samples, vol_trace_rec* out_host, int32_t* counts_host) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    if (!cam || !params || !pixels_host || !out_host || !counts_host || npix < 0 || max_samples < 0)
+        return fail(v, VOL_ERR_INVALID_ARG, "bad trace arguments");
+    if (npix == 0) return VOL_OK;
+    if (cam->w < 1 || cam->h < 1) return fail(v, VOL_ERR_INVALID_ARG, "bad image size");
+    for (int i = 0; i < npix; ++i)
+        if (pixels_host[2 * i] < 0 || pixels_host[2 * i] >= cam->w || pixels_host[2 * i + 1] < 0 ||
+            pixels_host[2 * i + 1] >= cam->h)
+            return fail(v, VOL_ERR_INVALID_ARG, "pixel outside the image");
+    TraceDev t{};
+    t.vol = vol_dev(v);
+    for (int a = 0; a < 3; ++a) {
+        t.view.eye[a] = cam->eye[a];
+        t.view.right[a] = cam->right[a];
+        t.view.up[a] = cam->up[a];
+        t.view.fwd[a] = cam->fwd[a];
+    }
+    t.view.tan = cam->tan_half_fov;
+    t.view.tan_aspect = cam->tan_half_fov * cam->aspect;
+    t.view.lodscale = (2.0f * cam->tan_half_fov) / (float)cam->h;
+    t.view.w = cam->w;
+    t.view.h = cam->h;
+    t.step = params->step;
+    t.lod_mode = params->lod_mode;
+    t.lod_bias = params->lod_bias;
+    t.npix = npix;
+    t.max_samples = max_samples;
+    int* dpix = nullptr;
+    int* dcnt = nullptr;
+    vol_trace_rec* drec = nullptr;
+    const size_t nrec = (size_t)npix * (size_t)std::max(1, max_samples);
+    cudaError_t e = cudaMalloc((void**)&dpix, sizeof(int) * 2 * npix);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dcnt, sizeof(int) * npix);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&drec, sizeof(vol_trace_rec) * nrec);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dpix, pixels_host, sizeof(int) * 2 * npix, cudaMemcpyHostToDevice, v->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(drec, 0, sizeof(vol_trace_rec) * nrec, v->stream);
+    if (e == cudaSuccess) {
+        t.pixels = dpix;
+        t.out = drec;
+        t.counts = dcnt;
+        e = launch_trace(t, v->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, drec, sizeof(vol_trace_rec) * (size_t)npix * max_samples, cudaMemcpyDeviceToHost, v->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts_host, dcnt, sizeof(int) * npix, cudaMemcpyDeviceToHost, v->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(v->stream);
+    cudaFree(dpix);
+    cudaFree(dcnt);
+    cudaFree(drec);
+    if (e != cudaSuccess) return cuda_fail(v, e, "trace");
+    return VOL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded inputs.
+
+Bit-exact: page-table resolve and LOD selection (trace records), LOD downsample and storage
+transcode (atlas bytes), batched vs single-view renders, renders after miss passes vs fully
+resident.  Tolerance: max-abs per channel 1e-4 (float32 arithmetic; storage decoded alike on
+both sides)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from _helpers import AMB, TOL_FP32, TOL_REDUCED, c1_inputs, compare, store_levels
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2509_26213_gb300 as pkg
+    pkg.build()
+    from paper_2509_26213_gb300 import volume
+    assert torch.cuda.is_available()
+    return volume
+
+
+def gpu_volume(P, raw0, src_dtype, store_dtype, brick, levels, cache_bytes=0):
+    Dz, Dy, Dx = raw0.shape
+    vol = P.Volume((Dx, Dy, Dz), store_dtype, brick, levels, cache_bytes)
+    vol.upload_level(0, raw0, src_dtype)
+    if levels > 1:
+        vol.build_lod(0)
+    return vol
+
+
+def tf_dev(tf):
+    return torch.from_numpy(np.ascontiguousarray(tf, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("lod", [0, 1])
+def test_c1_full_frame(P, orc, lod):
+    D, raw, cam, tf, params = c1_inputs()
+    params = dict(params, lod_mode=lod)
+    vol = gpu_volume(P, raw, "u8", "u8", 32, 2)
+    out, ns = vol.render(cam, tf_dev(tf), params, nsamples=True)
+    torch.cuda.synchronize()
+    gpu = out.cpu().numpy()
+    ovol = orc.Volume(store_levels(orc, raw, "u8", "u8", 2), "u8", 32)
+    ref = orc.render(ovol, cam, tf, params, amb=AMB)
+    err, bad, alt = compare(gpu, ref, TOL_FP32)
+    assert len(bad) == 0, f"{len(bad)} pixels above {TOL_FP32}, max err {err}"
+    n_gpu = ns.cpu().numpy()
+    agree = (n_gpu == ref["n"]) | (alt & (n_gpu == ref["alt_n"]))
+    assert agree.all()
+    assert vol.stats()["device_error"] == 0
+    print(f"C1 lod={lod}: max abs err {err:.3g}, alternate ET pixels {int(alt.sum())}, samples {int(n_gpu.sum())}")
+
+
+@pytest.mark.parametrize("lod", [0, 1])
+def test_trace_bit_exact(P, orc, lod):
+    D, raw, cam, tf, params = c1_inputs(seed=2)
+    cam = dict(cam, h=64, w=64, aspect=np.float32(1.0))
+    params = dict(params, lod_mode=lod, lod_bias=1 if lod else 0)
+    vol = gpu_volume(P, raw, "u8", "u8", 32, 2)
+    pix = synth.pixel_subset(64, 64, 300, 7)
+    recs, counts = vol.trace(cam, params, pix, 600)
+    ovol = orc.Volume(store_levels(orc, raw, "u8", "u8", 2), "u8", 32)
+    nrec = 0
+    for i, (px, py) in enumerate(pix):
+        want, n = orc.trace(ovol, cam, params, int(px), int(py), 600)
+        assert counts[i] == n
+        got = recs[i, :min(n, 600)]
+        for f in ("k", "t_bits", "level", "i0", "local", "brick_id"):
+            np.testing.assert_array_equal(got[f], want[f], err_msg=f"pixel {(px, py)} field {f}")
+        assert np.all(got["slot"] != 0xFFFFFFFF)
+        nrec += len(got)
+    assert nrec > 10000
+    if lod:
+        lv = np.concatenate([recs[i, :min(counts[i], 600)]["level"] for i in range(len(pix))])
+        assert (lv == 0).any() and (lv == 1).any()
+
+
+@pytest.mark.parametrize("store,src", [("u8", "u8"), ("u16", "u16"), ("f16", "u16"), ("f32", "f32"),
+                                       ("f32", "u8"), ("f16", "f16")])
+def test_upload_and_downsample_bit_exact(P, orc, store, src):
+    rng = np.random.default_rng(5)
+    shape = (33, 45, 70)  # ragged against 16^3 bricks on every axis
+    if src == "u8":
+        raw = rng.integers(0, 256, shape, dtype=np.uint8)
+    elif src == "u16":
+        raw = rng.integers(0, 65536, shape, dtype=np.uint16)
+    elif src == "f16":
+        raw = rng.random(shape).astype(np.float16).view(np.uint16)
+    else:
+        raw = rng.random(shape, dtype=np.float32)
+    L = 4
+    vol = gpu_volume(P, raw, src, store, 16, L)
+    levels = store_levels(orc, raw, src, store, L)
+    npdt = {"u8": np.uint8, "u16": np.uint16, "f16": np.uint16, "f32": np.float32}[store]
+    for l, arr in enumerate(levels):
+        Dz, Dy, Dx = arr.shape
+        nb = vol.level_bricks[l]
+        for bz in range(nb[2]):
+            for by in range(nb[1]):
+                for bx in range(nb[0]):
+                    got = vol.download_brick(l, (bx, by, bz)).view(npdt)
+                    zi = np.minimum(bz * 16 + np.arange(17), Dz - 1)
+                    yi = np.minimum(by * 16 + np.arange(17), Dy - 1)
+                    xi = np.minimum(bx * 16 + np.arange(17), Dx - 1)
+                    want = arr[np.ix_(zi, yi, xi)]
+                    np.testing.assert_array_equal(got, want, err_msg=f"level {l} brick {(bx, by, bz)}")
+
+
+def test_empty_volume_and_edge_images(P, orc):
+    D = (40, 24, 33)
+    raw = np.zeros((33, 24, 40), np.uint8)
+    vol = gpu_volume(P, raw, "u8", "u8", 16, 3)
+    tf = synth.tf_ramp()
+    bg = (0.25, 0.5, 0.125, 1.0)
+    for (w, h) in [(1, 1), (37, 29), (64, 3), (3, 70)]:
+        cam = synth.seeded_orbit(D, w, h, 3)
+        for tile in [(8, 8), (16, 16), (32, 4), (32, 1)]:
+            out = vol.render(cam, tf_dev(tf), {"bg": bg, "tile_w": tile[0], "tile_h": tile[1]}).cpu().numpy()
+            np.testing.assert_array_equal(out, np.tile(np.float32(bg), (w * h, 1)))
+    # a camera looking away from the box: every ray misses
+    cam = synth.look_at((-50.0, 12.0, 16.0), (-100.0, 12.0, 16.0), 9, 9)
+    out = vol.render(cam, tf_dev(tf), {"bg": bg}).cpu().numpy()
+    np.testing.assert_array_equal(out, np.tile(np.float32(bg), (81, 1)))
+
+
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f16", "f32"])
+def test_ragged_volume_inside_camera(P, orc, dtype):
+    """Odd dims, bricks of 8, a camera inside the volume, all storage types, LOD on."""
+    D = (37, 29, 23)
+    rng = np.random.default_rng(9)
+    raw = synth.blobs(D, 4, dtype="u8" if dtype == "u8" else "f32", nblobs=6, sigma=(3, 8),
+                      amp=(80, 220) if dtype == "u8" else (0.3, 0.9), noise=8 if dtype == "u8" else 0.05)
+    if dtype == "u16":
+        raw = (raw.astype(np.float64) * 65535).astype(np.uint16)
+    if dtype == "f16":
+        raw = raw.astype(np.float16).view(np.uint16)
+    vol = gpu_volume(P, raw, dtype, dtype, 8, 3)
+    ovol = orc.Volume(store_levels(orc, raw, dtype, dtype, 3), dtype, 8)
+    tf = synth.tf_peaks(3)
+    tf[:, 3] = np.clip(tf[:, 3] + 0.02, 0, 1)
+    cams = [synth.look_at((18.0, 14.0, 11.0), (30.0, 20.0, 15.0), 45, 33, fov_deg=70.0),
+            synth.seeded_orbit(D, 41, 31, 8)]
+    for cam in cams:
+        for lod in (0, 1):
+            params = {"lod_mode": lod, "lod_bias": 2 if lod else 0, "bg": (0.1, 0.0, 0.2, 0.5)}
+            gpu = vol.render(cam, tf_dev(tf), params).cpu().numpy()
+            ref = orc.render(ovol, cam, tf, params, amb=AMB)
+            err, bad, _ = compare(gpu, ref, TOL_FP32)
+            assert len(bad) == 0, (dtype, lod, err)
+
+
+def test_batched_views_equal_single_and_oracle(P, orc):
+    D, raw, _, tf, params = c1_inputs(seed=3)
+    vol = gpu_volume(P, raw, "u8", "u8", 32, 2)
+    cams = [synth.seeded_orbit(D, s, s, 3, view=i) for i, s in enumerate([17, 64, 40, 96, 33])]
+    params = dict(params, lod_mode=1)
+    batched = vol.render(cams, tf_dev(tf), params).cpu().numpy()
+    ovol = orc.Volume(store_levels(orc, raw, "u8", "u8", 2), "u8", 32)
+    off = 0
+    for cam in cams:
+        n = cam["w"] * cam["h"]
+        single = vol.render(cam, tf_dev(tf), params).cpu().numpy()
+        np.testing.assert_array_equal(batched[off:off + n], single)
+        ref = orc.render(ovol, cam, tf, params, amb=AMB)
+        err, bad, _ = compare(batched[off:off + n], ref, TOL_FP32)
+        assert len(bad) == 0, err
+        off += n
+
+
+@pytest.mark.parametrize("tile,refill", [((8, 8), 24), ((16, 16), 32), ((32, 4), 1), ((4, 8), 16)])
+def test_tile_shape_and_refill_do_not_change_image(P, tile, refill):
+    D, raw, cam, tf, params = c1_inputs(seed=4)
+    vol = gpu_volume(P, raw, "u8", "u8", 32, 2)
+    base = vol.render(cam, tf_dev(tf), params).cpu().numpy()
+    out = vol.render(cam, tf_dev(tf), dict(params, tile_w=tile[0], tile_h=tile[1], refill=refill,
+                                         ctas_per_sm=1)).cpu().numpy()
+    np.testing.assert_array_equal(out, base)
+
+
+def test_miss_path_with_provider_equals_resident(P, orc):
+    """A cache that holds a fraction of the bricks, bricks loaded on request through the
+    provider: the final image equals the fully resident render bit for bit."""
+    D, raw, cam, tf, params = c1_inputs(seed=5)
+    params = dict(params, lod_mode=1, lod_bias=0)
+    levels = store_levels(orc, raw, "u8", "u8", 2)
+    full = gpu_volume(P, raw, "u8", "u8", 16, 2)
+    want = full.render(cam, tf_dev(tf), params).cpu().numpy()
+    B = 16
+
+    def provider(level, b):
+        arr = levels[level]
+        Dz, Dy, Dx = arr.shape
+        zi = np.minimum(b[2] * B + np.arange(B + 1), Dz - 1)
+        yi = np.minimum(b[1] * B + np.arange(B + 1), Dy - 1)
+        xi = np.minimum(b[0] * B + np.arange(B + 1), Dx - 1)
+        return arr[np.ix_(zi, yi, xi)]
+
+    slot = P.plan(D, "u8", B, 2).slot_bytes
+    vol = P.Volume(D, "u8", B, 2, cache_bytes=300 * slot)   # 300 of 584 bricks
+    vol.set_provider(provider, "u8")
+    got = vol.render(cam, tf_dev(tf), dict(params, max_passes=200)).cpu().numpy()
+    st = vol.stats()
+    assert st["passes"] > 1 and st["bricks_loaded"] > 0 and st["device_error"] == 0
+    np.testing.assert_array_equal(got, want)
+    # a second frame from another angle reuses and evicts
+    cam2 = synth.seeded_orbit(D, 256, 256, 5, view=1)
+    want2 = full.render(cam2, tf_dev(tf), params).cpu().numpy()
+    got2 = vol.render(cam2, tf_dev(tf), dict(params, max_passes=200)).cpu().numpy()
+    np.testing.assert_array_equal(got2, want2)
+    assert vol.stats()["evicted"] > 0
+
+
+def test_requests_without_provider_then_resume(P, orc):
+    D, raw, cam, tf, params = c1_inputs(seed=6)
+    levels = store_levels(orc, raw, "u8", "u8", 1)
+    full = gpu_volume(P, raw, "u8", "u8", 32, 1)
+    want = full.render(cam, tf_dev(tf), params).cpu().numpy()
+    vol = P.Volume(D, "u8", 32, 1)
+    out = vol.render(cam, tf_dev(tf), params, check_incomplete=False)
+    assert vol.last_rc == -3  # VOL_ERR_INCOMPLETE
+    for _ in range(100):
+        req = vol.poll_requests()
+        assert len(req) > 0 and len(np.unique(req, axis=0)) == len(req)  # deduplicated
+        for l, bx, by, bz in req:
+            arr = levels[l]
+            zi = np.minimum(bz * 32 + np.arange(33), 127)
+            yi = np.minimum(by * 32 + np.arange(33), 127)
+            xi = np.minimum(bx * 32 + np.arange(33), 127)
+            vol.upload_brick(l, (bx, by, bz), arr[np.ix_(zi, yi, xi)], "u8")
+        if vol.resume() == 0:
+            break
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
