@@ -37,32 +37,15 @@ L2_FLUSH_BYTES = 256 << 20
 
 # ------------------------------------------------------------------ workloads
 
-def c2_workload(seed=2):
-    D = (1024, 1024, 1024)
-    return {
-        "name": "reduced-precision single view, 1024^3 u16 noise+spheres, 64^3 bricks, 5 levels, 1920x1080",
-        "D": D, "brick": 64, "levels": 5,
-        "make": lambda: synth.noise_spheres(D, seed, octaves=5, period0=128.0, nspheres=200,
-                                            radius=(4.0, 60.0), value=(0.3, 1.0)),
-        "src": "u16",
-        "cams": [synth.seeded_orbit(D, 1920, 1080, seed)],
-        "tf": synth.tf_peaks(seed),
-        "params": {"step": 0.5, "et": 0.99, "lod_mode": 1, "lod_bias": 0},
-    }
+from synth import workloads  # noqa: E402
 
 
-def c4_workload(seed=4):
-    D = (256, 256, 256)
-    return {
-        "name": "differentiable, 256^3 f32 blobs, 16 views 512x512, fwd+adjoint",
-        "D": D, "brick": 32, "levels": 1,
-        "make": lambda: synth.blobs(D, seed, dtype="f32", nblobs=8, sigma=(12.0, 40.0), amp=(0.2, 1.0),
-                                    noise=0.02, vmax=1.0),
-        "src": "f32",
-        "cams": [synth.seeded_orbit(D, 512, 512, seed, view=v) for v in range(16)],
-        "tf": synth.tf_ramp(alpha_start=0.05, alpha_max=0.1),
-        "params": {"step": 0.5, "et": 0.99, "lod_mode": 0},
-    }
+def c2_workload():
+    return workloads.c2()
+
+
+def c4_workload():
+    return workloads.c4()
 
 
 # ------------------------------------------------------------------ helpers

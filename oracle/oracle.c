@@ -128,7 +128,14 @@ uint16_t orc_float_to_half(float f)
  * round to nearest even). */
 void orc_u16_to_f16(int64_t n, const uint16_t *src, uint16_t *dst)
 {
-    for (int64_t i = 0; i < n; ++i) dst[i] = orc_float_to_half((float)src[i] / 65535.0f);
+    /* all 65536 inputs converted once, then looked up */
+    uint16_t *tab = malloc(sizeof(uint16_t) * 65536);
+    for (int u = 0; u < 65536; ++u) tab[u] = orc_float_to_half((float)u / 65535.0f);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < n; ++i) dst[i] = tab[src[i]];
+    free(tab);
 }
 
 /* u8 -> float32 normalised value (u / 255 as one float division). */
@@ -152,6 +159,17 @@ int orc_downsample(int dtype, const int64_t D[3], const void *src, void *dst)
 {
     int64_t Dn[3];
     for (int a = 0; a < 3; ++a) Dn[a] = (D[a] + 1) / 2;
+    if (dtype < ORC_U8 || dtype > ORC_F32) return -1;
+    /* binary16 decode table (every value through orc_half_to_double) */
+    float *half_tab = NULL;
+    if (dtype == ORC_F16) {
+        half_tab = malloc(sizeof(float) * 65536);
+        if (!half_tab) return -2;
+        for (int h = 0; h < 65536; ++h) half_tab[h] = (float)orc_half_to_double((uint16_t)h);
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
     for (int64_t z = 0; z < Dn[2]; ++z)
         for (int64_t y = 0; y < Dn[1]; ++y)
             for (int64_t x = 0; x < Dn[0]; ++x) {
@@ -168,9 +186,8 @@ int orc_downsample(int dtype, const int64_t D[3], const void *src, void *dst)
                             switch (dtype) {
                             case ORC_U8: isum += ((const uint8_t *)src)[ci]; break;
                             case ORC_U16: isum += ((const uint16_t *)src)[ci]; break;
-                            case ORC_F16: fsum = fsum + (float)orc_half_to_double(((const uint16_t *)src)[ci]); break;
+                            case ORC_F16: fsum = fsum + half_tab[((const uint16_t *)src)[ci]]; break;
                             case ORC_F32: fsum = fsum + ((const float *)src)[ci]; break;
-                            default: return -1;
                             }
                         }
                 int64_t o = x + Dn[0] * (y + Dn[1] * z);
@@ -181,6 +198,7 @@ int orc_downsample(int dtype, const int64_t D[3], const void *src, void *dst)
                 case ORC_F32: ((float *)dst)[o] = fsum * 0.125f; break;
                 }
             }
+    free(half_tab);
     return 0;
 }
 

@@ -59,7 +59,7 @@ def test_c1_full_frame(P, orc, lod):
 def test_trace_bit_exact(P, orc, lod):
     D, raw, cam, tf, params = c1_inputs(seed=2)
     cam = dict(cam, h=64, w=64, aspect=np.float32(1.0))
-    params = dict(params, lod_mode=lod, lod_bias=1 if lod else 0)
+    params = dict(params, lod_mode=lod, lod_bias=-1 if lod else 0)   # q spans 2.6..5.6: levels 0 and 1
     vol = gpu_volume(P, raw, "u8", "u8", 32, 2)
     pix = synth.pixel_subset(64, 64, 300, 7)
     recs, counts = vol.trace(cam, params, pix, 600)
