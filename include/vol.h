@@ -250,6 +250,39 @@ int vol_render_backward(vol_t v, const float *drgba_dev, float *dtf_dev, float *
 int vol_trace(vol_t v, const vol_camera *cam, const vol_params *params, const int32_t *pixels_host,
               int npix, int max_samples, vol_trace_rec *out_host, int32_t *counts_host);
 
+/* ---- rendering without any allocation ------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * must not allocate device memory once set-up is over: a host application that
+ * reserves its whole device-memory budget up front and refuses later
+ * allocations, or a render loop that must never stall inside the allocator.
+ * vol_render() may allocate on its first calls (its view table, and, for
+ * partly resident volumes or gradient mode, request tables, suspended-ray
+ * buffers and checkpoints); this variant never does.
+ *
+ * It renders like vol_render() (same kernel, same image) from a volume whose
+ * bricks are all resident for the levels the parameters use.  Its only scratch
+ * (the work counter and the view table) lives in one static device array of
+ * VOL_NOALLOC_SCRATCH_BYTES (8 KiB) inside the library, which every GPU that
+ * loads the library keeps until the process exits; hence at most
+ * VOL_NOALLOC_MAX_VIEWS views per call.  The caller passes inputs and outputs
+ * exactly as for vol_render().
+ *   - The first call on each device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array, and each call overwrites it: calls that
+ *     overlap on the GPU (different streams, or different volumes on streams
+ *     that are not ordered) race.  Calls on one stream are ordered and safe.
+ *   - It neither queues brick requests nor keeps state for
+ *     vol_render_backward(), and it does not update the LRU usage stamps.
+ * Errors: VOL_ERR_INVALID_ARG (null pointers, nviews outside
+ * 1..VOL_NOALLOC_MAX_VIEWS, bad image size or tile), VOL_ERR_UNSUPPORTED
+ * (VOL_RENDER_GRAD set, or a needed level not fully resident), VOL_ERR_CUDA. */
+#define VOL_NOALLOC_SCRATCH_BYTES 8192
+#define VOL_NOALLOC_MAX_VIEWS 64
+int vol_render_noalloc(vol_t v, const vol_camera *cams, int nviews, const float *tf_dev,
+                       const vol_params *params, float *rgba_dev, int32_t *nsamples_dev);
+
 #ifdef __cplusplus
 }
 #endif

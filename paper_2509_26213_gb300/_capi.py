@@ -32,7 +32,9 @@ VOL_RENDER_GRAD = 1
 EXPORTS = ["vol_plan", "vol_create", "vol_destroy", "vol_last_error", "vol_set_stream", "vol_get_layout",
            "vol_get_stats", "vol_upload_level", "vol_upload_brick", "vol_build_lod", "vol_download_brick",
            "vol_evict_all", "vol_set_provider", "vol_render", "vol_render_resume", "vol_poll_requests",
-           "vol_render_backward", "vol_trace"]
+           "vol_render_backward", "vol_trace", "vol_render_noalloc"]
+VOL_NOALLOC_SCRATCH_BYTES = 8192
+VOL_NOALLOC_MAX_VIEWS = 64
 
 
 class vol_camera(ctypes.Structure):
@@ -105,6 +107,7 @@ def load() -> ctypes.CDLL:
         "vol_render_backward": (i32, [vp, vp, vp, vp]),
         "vol_trace": (i32, [vp, ctypes.POINTER(vol_camera), ctypes.POINTER(vol_params), i32p, i32, i32,
                             ctypes.POINTER(vol_trace_rec), i32p]),
+        "vol_render_noalloc": (i32, [vp, ctypes.POINTER(vol_camera), i32, vp, ctypes.POINTER(vol_params), vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

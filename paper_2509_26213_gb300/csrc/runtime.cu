@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -905,3 +906,121 @@ int vol_trace(vol_t v, const vol_camera* cam, const vol_params* params, const in
 }
 
 }  // extern "C"
+
+// =====================================================================================
+// Rendering without allocation (vol_render_noalloc).
+//
+// For callers that must not allocate device memory after set-up (a host application that
+// hands out a fixed device-memory budget once, a render loop that must not stall in the
+// allocator).  The per-call scratch of the render kernel -- its work counters and the view
+// table -- lives in this file-scope device array instead of buffers the volume allocates on
+// demand.  Every GPU that loads the library holds the array until the process exits.
+// Host code must not use the array's name as an address (it names a host-side stand-in);
+// the device address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+
+constexpr size_t kNoallocCounterBytes = 256;  // kNumCounters words, padded
+static_assert(sizeof(unsigned) * kNumCounters <= kNoallocCounterBytes, "counter area");
+static_assert(kNoallocCounterBytes + sizeof(ViewDev) * VOL_NOALLOC_MAX_VIEWS <= VOL_NOALLOC_SCRATCH_BYTES,
+              "scratch array too small for VOL_NOALLOC_MAX_VIEWS views");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[VOL_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device (set up on first use).
+int noalloc_scratch(vol_t v, unsigned char** out) {
+    int dev = 0;
+    CK(v, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(v, VOL_ERR_UNSUPPORTED, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(v, e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (unsigned char*)g_noalloc_addr[dev];
+    return VOL_OK;
+}
+
+}  // namespace
+
+extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
+                                  const vol_params* params, float* rgba_dev, int32_t* nsamples_dev) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    if (!cams || !tf_dev || !params || !rgba_dev) return fail(v, VOL_ERR_INVALID_ARG, "null argument");
+    if (nviews < 1 || nviews > VOL_NOALLOC_MAX_VIEWS)
+        return fail(v, VOL_ERR_INVALID_ARG, "nviews must be 1..VOL_NOALLOC_MAX_VIEWS (64) for vol_render_noalloc");
+    vol_params p = *params;
+    if (!(p.step > 0.0f) || !std::isfinite(p.step)) return fail(v, VOL_ERR_INVALID_ARG, "step must be > 0");
+    if (p.tile_w <= 0) p.tile_w = 8;
+    if (p.tile_h <= 0) p.tile_h = 8;
+    if ((p.tile_w * p.tile_h) % 32 != 0 || p.tile_w * p.tile_h > 4096)
+        return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be a multiple of 32, at most 4096");
+    if (p.refill <= 0 || p.refill > 32) p.refill = 24;
+    if (p.lod_mode != 0 && p.lod_mode != 1) return fail(v, VOL_ERR_INVALID_ARG, "lod_mode must be 0 or 1");
+    if (p.flags & VOL_RENDER_GRAD)
+        return fail(v, VOL_ERR_UNSUPPORTED, "vol_render_noalloc keeps no gradient state; use vol_render");
+    if (!all_resident(v, p.lod_mode != 0))
+        return fail(v, VOL_ERR_UNSUPPORTED, "vol_render_noalloc needs every brick of the used levels resident");
+
+    ViewDev views[VOL_NOALLOC_MAX_VIEWS];
+    int64_t rays = 0, tiles = 0;
+    for (int i = 0; i < nviews; ++i) {
+        const vol_camera& c = cams[i];
+        if (c.w < 1 || c.h < 1 || c.w > 65536 || c.h > 65536) return fail(v, VOL_ERR_INVALID_ARG, "bad image size");
+        ViewDev& V = views[i];
+        V = ViewDev{};
+        for (int a = 0; a < 3; ++a) {
+            V.eye[a] = c.eye[a];
+            V.right[a] = c.right[a];
+            V.up[a] = c.up[a];
+            V.fwd[a] = c.fwd[a];
+        }
+        V.tan = c.tan_half_fov;
+        V.tan_aspect = c.tan_half_fov * c.aspect;
+        V.lodscale = (2.0f * c.tan_half_fov) / (float)c.h;
+        V.w = c.w;
+        V.h = c.h;
+        V.tiles_x = (c.w + p.tile_w - 1) / p.tile_w;
+        V.tile_off = (int)tiles;
+        V.ray_off = rays;
+        tiles += (int64_t)V.tiles_x * ((c.h + p.tile_h - 1) / p.tile_h);
+        rays += (int64_t)c.w * c.h;
+    }
+    if (tiles >= (1ll << 31)) return fail(v, VOL_ERR_INVALID_ARG, "too many tiles");
+
+    unsigned char* scratch = nullptr;
+    if (int rc = noalloc_scratch(v, &scratch)) return rc;
+    unsigned* counters = (unsigned*)scratch;
+    ViewDev* views_dev = (ViewDev*)(scratch + kNoallocCounterBytes);
+    // the array keeps the previous call's contents: the counters must start at zero
+    CK(v, cudaMemcpyAsync(views_dev, views, sizeof(ViewDev) * nviews, cudaMemcpyHostToDevice, v->stream));
+    CK(v, cudaMemsetAsync(counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
+
+    RenderDev r{};
+    r.vol = vol_dev(v);
+    r.views = views_dev;
+    r.nviews = nviews;
+    r.nwork = (int)tiles;
+    r.resume = 0;
+    r.tile_w = p.tile_w;
+    r.tile_h = p.tile_h;
+    r.refill_thresh = p.refill;
+    r.tf = (const float4*)tf_dev;
+    r.step = p.step;
+    r.et = p.et_threshold;
+    r.bg = make_float4(p.bg[0], p.bg[1], p.bg[2], p.bg[3]);
+    r.lod_mode = p.lod_mode;
+    r.lod_bias = p.lod_bias;
+    r.out = (float4*)rgba_dev;
+    r.nsamp = nsamples_dev;
+    r.counters = counters;
+    r.nrays = rays;  // no request table, no suspension buffers, no usage stamps, no checkpoints
+    const int grid = grid_for(v, v->dtype, false, p.ctas_per_sm);
+    CK(v, launch_render(v->dtype, false, r, grid, v->stream));
+    return VOL_OK;
+}
