@@ -40,14 +40,6 @@ L2_FLUSH_BYTES = 256 << 20
 from synth import workloads  # noqa: E402
 
 
-def c2_workload():
-    return workloads.c2()
-
-
-def c4_workload():
-    return workloads.c4()
-
-
 # ------------------------------------------------------------------ helpers
 
 class Clocks:
@@ -67,7 +59,7 @@ class Clocks:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -170,40 +162,71 @@ def sum_over_ranks(dist, x):
     return float(t.item())
 
 
+# ------------------------------------------------------------------ workload helpers
+
+def load_workload(key, rank=0, ws=1):
+    wl = getattr(workloads, key)()
+    if ws > 1:
+        # weak scaling: every rank renders its own frame (views rotated per rank); no collective
+        wl["cams"] = [synth.seeded_orbit(wl["D"], c["w"], c["h"], 11 + rank, view=i) for i, c in enumerate(wl["cams"])]
+    return wl
+
+
+def oracle_volume(wl, raw):
+    import oracle
+    oracle.build()
+    store = wl["store"]
+    if (wl["src"], store) == ("u16", "f16"):
+        raw = oracle.u16_to_f16(raw)
+    return oracle.Volume(oracle.pyramid(raw, wl["levels"], store), store, wl["brick"])
+
+
+def frame_pixels(wl, frac, seed):
+    """A seeded sample of every view's pixels: [(view, pixels[n,2])]."""
+    out = []
+    for v, cam in enumerate(wl["cams"]):
+        n = max(1, int(cam["w"] * cam["h"] * frac))
+        out.append((v, synth.pixel_subset(cam["w"], cam["h"], n, seed * 1000 + v)))
+    return out
+
+
+def oracle_samples(ovol, wl, parts):
+    import oracle
+    tot = 0
+    for v, pix in parts:
+        tot += int(oracle.render(ovol, wl["cams"][v], wl["tf"], wl["params"], pixels=pix)["n"].sum())
+    return tot
+
+
 # ------------------------------------------------------------------ reference arm (the oracle)
 
 def run_reference(args, dist, rank, ws):
     if rank != 0:
         return
     import oracle
-    oracle.build()
-    wl = c2_workload()
+    wl = load_workload(args.workload)
     t0 = time.time()
-    raw = wl["make"]()
-    ovol = oracle.Volume(oracle.pyramid(raw, wl["levels"], "u16"), "u16", wl["brick"])
+    ovol = oracle_volume(wl, wl["make"]())
     prep = time.time() - t0
-    cam, tf, params = wl["cams"][0], wl["tf"], wl["params"]
-    npix = args.ref_pixels
     threads = oracle.threads()
+    frac = args.ref_frac
     for i in range(args.warmup):
-        oracle.render(ovol, cam, tf, params, pixels=synth.pixel_subset(cam["w"], cam["h"], 64, 1000 + i))
+        oracle_samples(ovol, wl, frame_pixels(wl, frac / 16, 500 + i))
     times, samples = [], 0
     for i in range(args.steps):
-        pix = synth.pixel_subset(cam["w"], cam["h"], npix, 2000 + i)
+        parts = frame_pixels(wl, frac, 2000 + i)
         t = time.perf_counter()
-        out = oracle.render(ovol, cam, tf, params, pixels=pix)
+        samples += oracle_samples(ovol, wl, parts)
         times.append(time.perf_counter() - t)
-        samples += int(out["n"].sum())
     total = sum(times)
     value = samples / total
+    sample = f"{frac:g} of every view's pixels per step (seeded, new each step), {args.steps} steps"
     line = {
         "impl": "reference", "metric": "ray samples/s", "value": value, "unit": "samples/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": wl["name"], "store": "u16",
-                                         "sample": f"{npix} seeded pixels of the frame per step"},
-        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{npix} seeded pixels per step x {args.steps} steps"},
+        "data": "synthetic", "config": {"workload": wl["name"], "store": wl["store"], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "prep_s": prep,
     }
@@ -213,7 +236,6 @@ def run_reference(args, dist, rank, ws):
 # ------------------------------------------------------------------ our arm
 
 def build_volume(P, wl, store, raw):
-    Dx, Dy, Dz = wl["D"]
     vol = P.Volume(wl["D"], store, wl["brick"], wl["levels"])
     vol.upload_level(0, raw, wl["src"])
     if wl["levels"] > 1:
@@ -242,29 +264,32 @@ def time_frames(torch, vol, cams, tf, params, steps, warmup, flush, grad=False, 
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def bytes_per_voxel(store):
+    return {"u8": 1, "u16": 2, "f16": 2, "f32": 4}[store]
+
+
 def run_ours(args, dist, rank, ws, local):
     import torch
     import paper_2509_26213_gb300 as pkg
     pkg.build()
-    from paper_2509_26213_gb300.volume import Volume
     import paper_2509_26213_gb300.volume as P
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = c2_workload()
+    wl = load_workload(args.workload, rank, ws)
     raw = wl["make"]()
-    # weak scaling: every rank renders its own frame (view rotated per rank); no collective
-    cams = [synth.seeded_orbit(wl["D"], 1920, 1080, 2, view=rank)] if ws > 1 else wl["cams"]
+    cams, params = wl["cams"], dict(wl["params"])
     tf = torch.from_numpy(wl["tf"]).to(dev)
-    params = wl["params"]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    store = wl["store"]
+    bpv = bytes_per_voxel(store)
 
-    vol = build_volume(P, wl, "u16", raw)
+    vol = build_volume(P, wl, store, raw)
     out, ns = vol.render(cams, tf, params, nsamples=True)
     torch.cuda.synchronize()
     samples = int(ns.sum().item())
-    st = vol.stats()
-    touched = st["touched"]
+    touched = vol.stats()["touched"]
+    npx = sum(c["w"] * c["h"] for c in cams)
 
     barrier(dist)
     with Clocks(local) as clk:
@@ -272,12 +297,12 @@ def run_ours(args, dist, rank, ws, local):
         ms = time_frames(torch, vol, cams, tf, params, args.steps, args.warmup, flush)
         wall = time.perf_counter() - wall0
     clocks = clk.summary()
-    t_step = max_over_ranks(dist, statistics.mean(ms))
+    t_mean = statistics.mean(ms)
+    t_step = max_over_ranks(dist, t_mean)
     total_samples = sum_over_ranks(dist, samples)
     value = total_samples / (t_step * 1e-3)
 
     # end to end through the public API with host buffers: TF up, image down, every step
-    npx = sum(c["w"] * c["h"] for c in cams)
     tf_host = torch.from_numpy(wl["tf"]).pin_memory()
     img_host = torch.empty((npx, 4), dtype=torch.float32).pin_memory()
     tf_dev = torch.empty_like(tf)
@@ -302,32 +327,33 @@ def run_ours(args, dist, rank, ws, local):
     e2e_value = total_samples / (e2e_step * 1e-3)
 
     # roofline of the render kernel: algorithmic bytes = bricks touched + image + TF + page-table words
-    lay = vol.layout
-    brick_payload = (wl["brick"] + 1) ** 3 * 2
-    b_unique = touched * brick_payload + npx * 16 + 4096 + touched * 4
-    b_sample = samples * (8 * 2 + 4)
+    b_unique = touched * (wl["brick"] + 1) ** 3 * bpv + npx * 16 + 4096 + touched * 4
+    b_sample = samples * (8 * bpv + 4)
     peak, peak_kind = measured_peaks()
-    achieved = b_unique / (statistics.mean(ms) * 1e-3) / 1e9
+    achieved = b_unique / (t_mean * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic("c2"), "peak_kind": f"{peak_kind} hbm_gbs",
-                "bytes_accounting": "unique bricks touched x (B+1)^3 x 2 B + image + TF + page-table words",
-                "per_sample_gather_GBps": b_sample / (statistics.mean(ms) * 1e-3) / 1e9}
+                "traffic": recorded_traffic(wl["key"]), "peak_kind": f"{peak_kind} hbm_gbs (copy, burst)",
+                "kernel": "k_render",
+                "bytes_accounting": "bricks touched x (B+1)^3 x bytes/voxel + image 16 B/px + TF 4 KiB + 4 B/brick page-table word",
+                "bytes_per_frame": b_unique,
+                "per_sample_gather_GBps": b_sample / (t_mean * 1e-3) / 1e9}
 
     variants = {}
-    if not args.quick:
-        for store in ("f16", "f32"):
-            v2 = build_volume(P, wl, store, raw)
+    if not args.quick and args.workload == "c2":
+        for st2 in ("f16", "f32"):
+            v2 = build_volume(P, wl, st2, raw)
             _, ns2 = v2.render(cams, tf, params, nsamples=True)
             torch.cuda.synchronize()
             s2 = int(ns2.sum().item())
-            ms2 = time_frames(torch, v2, cams, tf, params, max(3, args.steps // 2), args.warmup, flush)
-            variants[store] = {"samples_per_s": s2 / (statistics.mean(ms2) * 1e-3), "ms_per_frame": statistics.mean(ms2),
-                               "samples_per_frame": s2}
+            ms2 = time_frames(torch, v2, cams, tf, params, max(5, args.steps // 4), args.warmup, flush)
+            variants[st2] = {"samples_per_s": s2 / (statistics.mean(ms2) * 1e-3),
+                             "ms_per_frame": statistics.mean(ms2), "samples_per_frame": s2}
             v2.close()
             torch.cuda.empty_cache()
+    if not args.quick and args.workload in ("c2", "c4"):
         # differentiable workload: forward in gradient mode + adjoint
-        w4 = c4_workload()
-        raw4 = w4["make"]()
+        w4 = workloads.c4()
+        raw4 = w4["make"]() if args.workload != "c4" else raw
         v4 = build_volume(P, w4, "f32", raw4)
         tf4 = torch.from_numpy(w4["tf"]).to(dev)
         o4, ns4 = v4.render(w4["cams"], tf4, w4["params"], nsamples=True, grad=True)
@@ -336,8 +362,9 @@ def run_ours(args, dist, rank, ws, local):
         drgba = torch.randn_like(o4) * 0.01
         dtf = torch.zeros((256, 4), dtype=torch.float32, device=dev)
         dvox = torch.zeros((256, 256, 256), dtype=torch.float32, device=dev)
-        ms_f = time_frames(torch, v4, w4["cams"], tf4, w4["params"], max(3, args.steps // 2), args.warmup, flush)
-        ms_fb = time_frames(torch, v4, w4["cams"], tf4, w4["params"], max(3, args.steps // 2), args.warmup, flush,
+        n4 = max(5, args.steps // 4)
+        ms_f = time_frames(torch, v4, w4["cams"], tf4, w4["params"], n4, args.warmup, flush)
+        ms_fb = time_frames(torch, v4, w4["cams"], tf4, w4["params"], n4, args.warmup, flush,
                             grad=True, drgba=drgba, dtf=dtf, dvox=dvox)
         variants["fwd_bwd"] = {"workload": w4["name"], "samples_per_frame": s4,
                                "fwd_ms": statistics.mean(ms_f), "fwd_bwd_ms": statistics.mean(ms_fb),
@@ -347,24 +374,26 @@ def run_ours(args, dist, rank, ws, local):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(wl, raw, args.cpu_pixels)
+        cpu = cpu_baseline(wl, raw, args.cpu_seconds)
 
     if rank == 0:
         line = {
             "metric": "ray samples/s", "value": value, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl["name"], "store": "u16", "brick": wl["brick"], "levels": wl["levels"],
-                       "image": "1920x1080", "lod": "footprint", "step": 0.5, "et": 0.99,
-                       "samples_per_frame": samples, "bricks_touched": touched,
+            "config": {"workload": wl["name"], "store": store, "brick": wl["brick"], "levels": wl["levels"],
+                       "views": len(cams), "pixels": npx, "lod": "footprint" if params.get("lod_mode") else "level 0",
+                       "step": params["step"], "et": params["et"], "samples_per_frame": samples,
+                       "bricks_touched": touched,
                        "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                        "parallelism": f"replicas x{ws}"},
-            "ms_per_frame": statistics.mean(ms),
+            "ms_per_frame": t_mean,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": 4096,
                     "d2h_bytes_per_step": npx * 16, "ms_per_step": e2e_step},
-            "gpu_launches": args.steps,
+            # per step: the render kernel and the heaviest-first scheduling kernel
+            "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "wall_s_timed": wall,
             "variants": variants,
@@ -373,29 +402,34 @@ def run_ours(args, dist, rank, ws, local):
     vol.close()
 
 
-def cpu_baseline(wl, raw, npix):
+def cpu_baseline(wl, raw, seconds):
+    """The oracle as it stands on the host cores: whole frames (every view) repeated until `seconds`."""
     import oracle
-    oracle.build()
-    ovol = oracle.Volume(oracle.pyramid(raw, wl["levels"], "u16"), "u16", wl["brick"])
-    cam = wl["cams"][0]
-    pix = synth.pixel_subset(cam["w"], cam["h"], npix, 77)
+    ovol = oracle_volume(wl, raw)
+    samples, frames = 0, 0
     t = time.perf_counter()
-    out = oracle.render(ovol, cam, wl["tf"], wl["params"], pixels=pix)
-    dt = time.perf_counter() - t
-    return {"value": int(out["n"].sum()) / dt, "unit": "samples/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{npix} seeded pixels of the 1920x1080 frame ({int(out['n'].sum())} samples, {dt:.1f} s)"}
+    while True:
+        for v, cam in enumerate(wl["cams"]):
+            samples += int(oracle.render(ovol, cam, wl["tf"], wl["params"])["n"].sum())
+        frames += 1
+        dt = time.perf_counter() - t
+        if dt >= seconds:
+            break
+    return {"value": samples / dt, "unit": "samples/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{frames} whole frame(s) of the workload, {samples} samples in {dt:.1f} s"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="primary line only (no storage variants, no fwd+bwd)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-pixels", type=int, default=32768)
-    ap.add_argument("--ref-pixels", type=int, default=8192)
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-frac", type=float, default=0.25, help="reference arm: fraction of pixels per step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -79,19 +79,31 @@ typedef struct {
     int32_t lod_mode;    /* 0: all samples on level 0; 1: footprint LOD (Sec. V-C) */
     int32_t lod_bias;    /* added to the footprint level before clamping to [0, L-1] */
     int32_t tile_w;      /* ray tile (work item) width in pixels; 0 = default 8 */
-    int32_t tile_h;      /* ray tile height; tile_w * tile_h must be a multiple of 32; 0 = 8 */
+    int32_t tile_h;      /* ray tile height (tile_w * tile_h <= 4096); 0 = 4 */
     int32_t max_passes;  /* miss/refill passes per render when a provider is set; 0 = 64 */
     uint32_t flags;      /* VOL_RENDER_* bits */
     int32_t refill;      /* a warp fetches new rays once fewer lanes than this are busy
-                            (1..32; 0 = default 24); performance only, never the image */
+                            (1..32; 0 = default 30); performance only, never the image */
     int32_t ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
 } vol_params;
+
+/* Atlas slot layouts (vol_plan / vol_create flags).
+ * Default, "quad": a slot holds B x B x (B+1) entries, entry (x, y, z) being the
+ * four voxels (x, y), (x+1, y), (x, y+1), (x+1, y+1) of slice z of the brick's
+ * apron-extended region, stored together (4, 8, 8 or 16 bytes for u8, u16,
+ * f16, f32), so the eight corners of a trilinear sample are two aligned loads.
+ * It takes about 4x the memory of the voxels.
+ * VOL_LAYOUT_COMPACT: a slot holds the (B+1)^3 voxels of the brick and its
+ * +x/+y/+z apron; a sample reads eight scalars.  Both give identical images. */
+#define VOL_LAYOUT_COMPACT 1u
 
 /* Brick-and-level layout that vol_create() would use (pure host computation). */
 typedef struct {
     int64_t dims[3];
     int32_t dtype, brick, levels;
     int32_t bytes_per_voxel;
+    int32_t layout;        /* 0 quad, 1 compact */
+    int32_t entry_voxels;  /* voxels stored per addressable entry: 4 (quad) or 1 */
     int64_t level_dims[VOL_MAX_LEVELS][3];
     int64_t level_bricks[VOL_MAX_LEVELS][3];  /* ceil(D_l / B) per axis */
     int64_t level_pt_offset[VOL_MAX_LEVELS];  /* first page-table entry of each level */
@@ -142,16 +154,17 @@ typedef struct {
 /* ---- layout and lifetime ------------------------------------------------ */
 
 /* Computes the layout for dims / dtype / brick (power of two, 4..128) /
- * levels (1..16) / cache_bytes (0 = room for every brick of every level).
- * Pure host code; needs no GPU. */
+ * levels (1..16) / cache_bytes (0 = room for every brick of every level) /
+ * flags (VOL_LAYOUT_COMPACT or 0).  Pure host code; needs no GPU. */
 int vol_plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes,
-             vol_layout *out);
+             uint32_t flags, vol_layout *out);
 
 /* Creates a volume on the current CUDA device: allocates the atlas (the
  * cache of brick slots), the page tables (all entries non-resident) and the
- * slot usage stamps.  `stream` is a cudaStream_t or NULL. */
+ * slot usage stamps.  flags: VOL_LAYOUT_COMPACT or 0 (quad).  `stream` is a
+ * cudaStream_t or NULL. */
 int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes,
-               void *stream, vol_t *out);
+               uint32_t flags, void *stream, vol_t *out);
 
 /* Frees everything the volume allocated.  NULL is ignored. */
 void vol_destroy(vol_t v);
@@ -191,8 +204,9 @@ int vol_upload_brick(vol_t v, int level, const int32_t brick[3], const void *src
  * resident.  VOL_ERR_CACHE_FULL when the atlas cannot hold them. */
 int vol_build_lod(vol_t v, int from_level);
 
-/* Copies the (B+1)^3 stored voxels of a resident brick (apron included) to
- * host memory dst; synchronous.  VOL_ERR_INVALID_ARG when not resident. */
+/* Copies the (B+1)^3 stored voxels of a resident brick (apron included, x
+ * fastest, whatever the slot layout) to host memory dst; synchronous.
+ * VOL_ERR_INVALID_ARG when not resident. */
 int vol_download_brick(vol_t v, int level, const int32_t brick[3], void *dst);
 
 /* Drops every brick (page tables back to non-resident). */

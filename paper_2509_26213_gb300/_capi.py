@@ -27,6 +27,8 @@ VOL_U8, VOL_U16, VOL_F16, VOL_F32 = 0, 1, 2, 3
 DTYPES = {"u8": VOL_U8, "u16": VOL_U16, "f16": VOL_F16, "f32": VOL_F32}
 MAX_LEVELS = 16
 VOL_RENDER_GRAD = 1
+VOL_LAYOUT_COMPACT = 1
+LAYOUTS = {"quad": 0, "compact": VOL_LAYOUT_COMPACT}
 
 # every entry point include/vol.h declares
 EXPORTS = ["vol_plan", "vol_create", "vol_destroy", "vol_last_error", "vol_set_stream", "vol_get_layout",
@@ -53,6 +55,7 @@ class vol_params(ctypes.Structure):
 class vol_layout(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int64 * 3), ("dtype", ctypes.c_int32), ("brick", ctypes.c_int32),
                 ("levels", ctypes.c_int32), ("bytes_per_voxel", ctypes.c_int32),
+                ("layout", ctypes.c_int32), ("entry_voxels", ctypes.c_int32),
                 ("level_dims", (ctypes.c_int64 * 3) * MAX_LEVELS),
                 ("level_bricks", (ctypes.c_int64 * 3) * MAX_LEVELS),
                 ("level_pt_offset", ctypes.c_int64 * MAX_LEVELS), ("total_bricks", ctypes.c_int64),
@@ -88,8 +91,8 @@ def load() -> ctypes.CDLL:
     vp, i32, i64p = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)
     i32p = ctypes.POINTER(ctypes.c_int32)
     sig = {
-        "vol_plan": (i32, [i64p, i32, i32, i32, ctypes.c_uint64, ctypes.POINTER(vol_layout)]),
-        "vol_create": (i32, [i64p, i32, i32, i32, ctypes.c_uint64, vp, ctypes.POINTER(vp)]),
+        "vol_plan": (i32, [i64p, i32, i32, i32, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(vol_layout)]),
+        "vol_create": (i32, [i64p, i32, i32, i32, ctypes.c_uint64, ctypes.c_uint32, vp, ctypes.POINTER(vp)]),
         "vol_destroy": (None, [vp]),
         "vol_last_error": (ctypes.c_char_p, [vp]),
         "vol_set_stream": (i32, [vp, vp]),

@@ -51,7 +51,9 @@ struct SuspRec {       // a ray waiting for a brick
 
 struct VolDev {
     const void* atlas;
-    unsigned long long slot_elems; // elements per slot (padded)
+    unsigned long long slot_elems; // voxels of storage per slot (padded)
+    unsigned long long slot_entries; // quad layout: 4-voxel entries per slot (slot_elems / 4)
+    int quad;                      // 1: quad layout, 0: compact (B+1)^3
     int bshift, bmask, B1;         // log2 B, B - 1, B + 1
     int nlevels;
     const uint32_t* pt;
@@ -89,6 +91,10 @@ struct RenderDev {
     long long nrays;
     int ckpt_segs;
     int* ray_n;
+    // scheduling: work item i of a fresh pass renders tile tile_order[i] (NULL: tile i);
+    // every finished ray adds its sample count to tile_cost[its tile] (NULL: not recorded)
+    const int* tile_order;
+    int* tile_cost;
 };
 
 struct BackwardDev {
@@ -127,6 +133,8 @@ cudaError_t launch_render(int dtype, bool grad, const RenderDev& p, int grid, cu
 cudaError_t launch_backward(int dtype, const BackwardDev& p, int grid, cudaStream_t s);
 cudaError_t launch_trace(const TraceDev& p, cudaStream_t s);
 int render_blocks_per_sm(int dtype, bool grad);
+// order[] = tiles sorted by descending log2 bucket of cost[] (heaviest first); zeroes cost[].
+cudaError_t launch_tile_order(int* cost, int* order, int ntiles, cudaStream_t s);
 int backward_blocks_per_sm(int dtype);
 
 // ---- launchers (kernels_volume.cu) ----

@@ -114,9 +114,31 @@ struct Resolved {
     uint32_t local; // element offset inside the slot
 };
 
+// One level's constants, held in registers by the render loop.
+struct LvReg {
+    float r[3];     // D_l / D_0 per axis (binary32)
+    int Dm[3];      // D_l - 1 per axis
+    int nb0, nb1;   // bricks along x and y
+    uint32_t off;   // first page-table entry of the level
+};
+
+__device__ __forceinline__ LvReg load_lv(const LevelDev& L) {
+    LvReg R;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R.r[a] = L.r[a];
+        R.Dm[a] = L.D[a] - 1;
+    }
+    R.nb0 = L.nb[0];
+    R.nb1 = L.nb[1];
+    R.off = L.pt_off;
+    return R;
+}
+
 // Grid position on a level, clamp to edge, chunk addressing (Sec. III-A).
-__device__ __forceinline__ void resolve(const LevelDev& L, int bshift, int bmask, int B1, const float p[3],
-                                        Resolved& R) {
+// local = element (compact: row = B+1) or entry (quad: row = B) offset inside the slot.
+__device__ __forceinline__ void resolve_reg(const LvReg& L, int bshift, int bmask, int row, const float p[3],
+                                            Resolved& R) {
     int h[3], l[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -126,8 +148,8 @@ __device__ __forceinline__ void resolve(const LevelDev& L, int bshift, int bmask
         if (i < 0) {
             R.i0[a] = 0;
             R.w[a] = 0.0f;
-        } else if (i >= L.D[a] - 1) {
-            R.i0[a] = L.D[a] - 1;
+        } else if (i >= L.Dm[a]) {
+            R.i0[a] = L.Dm[a];
             R.w[a] = 0.0f;
         } else {
             R.i0[a] = i;
@@ -136,15 +158,21 @@ __device__ __forceinline__ void resolve(const LevelDev& L, int bshift, int bmask
         h[a] = R.i0[a] >> bshift;
         l[a] = R.i0[a] & bmask;
     }
-    R.pti = L.pt_off + (uint32_t)(h[0] + L.nb[0] * (h[1] + L.nb[1] * h[2]));
-    R.local = (uint32_t)((l[2] * B1 + l[1]) * B1 + l[0]);
+    R.pti = L.off + (uint32_t)(h[0] + L.nb0 * (h[1] + L.nb1 * h[2]));
+    R.local = (uint32_t)((l[2] * row + l[1]) * row + l[0]);
+}
+
+__device__ __forceinline__ void resolve(const LevelDev& L, int bshift, int bmask, int row, const float p[3],
+                                        Resolved& R) {
+    resolve_reg(load_lv(L), bshift, bmask, row, p, R);
 }
 
 // Trilinear interpolation of the 8 corners at atlas element `base` (+x, +y, +z neighbours
 // at +1, +B1, +B1^2 thanks to the apron).
-template <int DT>
-__device__ __forceinline__ float trilinear(const typename Voxel<DT>::T* a, unsigned long long base, int B1,
+template <int DT, int BS = 0>
+__device__ __forceinline__ float trilinear(const typename Voxel<DT>::T* a, unsigned long long base, int B1_rt,
                                            const float w[3]) {
+    const int B1 = BS ? BS + 1 : B1_rt;
     const unsigned long long sy = (unsigned long long)B1, sz = (unsigned long long)B1 * B1;
     const float v000 = Voxel<DT>::ld(a + base), v100 = Voxel<DT>::ld(a + base + 1);
     const float v010 = Voxel<DT>::ld(a + base + sy), v110 = Voxel<DT>::ld(a + base + sy + 1);
@@ -157,6 +185,78 @@ __device__ __forceinline__ float trilinear(const typename Voxel<DT>::T* a, unsig
     const float c0 = fmaf(w[1], c10 - c00, c00);
     const float c1 = fmaf(w[1], c11 - c01, c01);
     return fmaf(w[2], c1 - c0, c0);
+}
+
+// Quad layout: entry e holds the voxels (x, y), (x+1, y), (x, y+1), (x+1, y+1) of one slice;
+// the entry of slice z+1 is B*B entries further.  Same interpolation order as trilinear().
+template <int DT>
+struct QuadEntry;
+template <>
+struct QuadEntry<VOL_U8> {
+    using V = unsigned int;
+    static __device__ __forceinline__ void get(V q, float v[4]) {
+        v[0] = (float)(q & 0xFFu);
+        v[1] = (float)((q >> 8) & 0xFFu);
+        v[2] = (float)((q >> 16) & 0xFFu);
+        v[3] = (float)(q >> 24);
+    }
+};
+template <>
+struct QuadEntry<VOL_U16> {
+    using V = uint2;
+    static __device__ __forceinline__ void get(V q, float v[4]) {
+        v[0] = (float)(q.x & 0xFFFFu);
+        v[1] = (float)(q.x >> 16);
+        v[2] = (float)(q.y & 0xFFFFu);
+        v[3] = (float)(q.y >> 16);
+    }
+};
+template <>
+struct QuadEntry<VOL_F16> {
+    using V = uint2;
+    static __device__ __forceinline__ void get(V q, float v[4]) {
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = b.x;
+        v[3] = b.y;
+    }
+};
+template <>
+struct QuadEntry<VOL_F32> {
+    using V = float4;
+    static __device__ __forceinline__ void get(V q, float v[4]) {
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    }
+};
+
+template <int DT, int BS = 0>
+__device__ __forceinline__ float trilinear_quad(const void* atlas, unsigned long long entry, int B_rt, const float w[3]) {
+    using Q = QuadEntry<DT>;
+    const int B = BS ? BS : B_rt;
+    const typename Q::V* a = (const typename Q::V*)atlas;
+    float e0[4], e1[4];
+    Q::get(__ldg(a + entry), e0);
+    Q::get(__ldg(a + entry + (unsigned long long)(B * B)), e1);
+    const float c00 = fmaf(w[0], e0[1] - e0[0], e0[0]);
+    const float c10 = fmaf(w[0], e0[3] - e0[2], e0[2]);
+    const float c01 = fmaf(w[0], e1[1] - e1[0], e1[0]);
+    const float c11 = fmaf(w[0], e1[3] - e1[2], e1[2]);
+    const float c0 = fmaf(w[1], c10 - c00, c00);
+    const float c1 = fmaf(w[1], c11 - c01, c01);
+    return fmaf(w[2], c1 - c0, c0);
+}
+
+// Either layout: `base` is the slot's element offset plus local (compact) or its entry offset
+// plus local (quad).
+template <int DT, int BS, bool Q>
+__device__ __forceinline__ float sample_value(const void* atlas, unsigned long long base, int B1, const float w[3]) {
+    if constexpr (Q) return trilinear_quad<DT, BS>(atlas, base, B1 - 1, w);
+    else return trilinear<DT, BS>((const typename Voxel<DT>::T*)atlas, base, B1, w);
 }
 
 __device__ __forceinline__ int find_view_tile(const ViewDev* views, int nviews, int item) {
@@ -237,7 +337,17 @@ __device__ __forceinline__ void suspend_ray(const RenderDev& P, long long ray, i
     }
 }
 
-template <int DT, bool LOD, bool GRAD>
+// Samples per lane per loop iteration: their page-table lookups and gathers are issued together,
+// then composited in order (memory-level parallelism along one ray).
+#ifndef VOLRC_BATCH
+#define VOLRC_BATCH 4
+#endif
+constexpr int kBatch = VOLRC_BATCH;
+
+__host__ __device__ constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
+
+// BS: brick edge known at compile time (32 or 64), or 0 for any power of two read at run time.
+template <int DT, bool LOD, bool GRAD, int BS, bool Q>
 __global__ void __launch_bounds__(kRenderThreads) k_render(const __grid_constant__ RenderDev P) {
     __shared__ float4 s_tf[256];
     __shared__ LevelDev s_lv[kMaxLevels];
@@ -249,21 +359,28 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(const __grid_constant
     const VT* __restrict__ atlas = (const VT*)P.vol.atlas;
     const unsigned lane = threadIdx.x & 31;
     const unsigned ltmask = (1u << lane) - 1;
-    const int bshift = P.vol.bshift, bmask = P.vol.bmask, B1 = P.vol.B1;
-    const unsigned long long slot_elems = P.vol.slot_elems;
+    const int bshift = BS ? log2i(BS) : P.vol.bshift;
+    const int bmask = BS ? BS - 1 : P.vol.bmask;
+    const int B1 = BS ? BS + 1 : P.vol.B1;
+    const int row = Q ? B1 - 1 : B1;
+    const unsigned long long slot_stride = Q ? P.vol.slot_entries : P.vol.slot_elems;
     const float step = P.step, et = P.et;
 
     // warp-uniform work pool
-    int pool_next = 0, pool_cnt = 0, pool_a = 0, pool_x0 = 0, pool_y0 = 0;
+    int pool_next = 0, pool_cnt = 0, pool_a = 0, pool_x0 = 0, pool_y0 = 0, pool_tile = -1;
     bool queue_done = false;
 
     // lane state
     bool active = false;
     long long ray = 0;
+    int my_tile = -1;
     float o0 = 0, o1 = 0, o2 = 0, d0 = 0, d1 = 0, d2 = 0, t0 = 0, t1 = 0, lodscale = 0;
     int k = 0;
     float C0 = 0, C1 = 0, C2 = 0, T = 1.0f;
-    uint32_t cur_pti = kInvalidSlot, cur_slot = kInvalidSlot;
+    uint32_t cur_pti = kInvalidSlot;
+    const int nlev = P.vol.nlevels;
+    int cur_l = 0;
+    LvReg L = load_lv(s_lv[0]);
 
     for (;;) {
         // ---- refill lanes whose ray ended
@@ -279,14 +396,17 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(const __grid_constant
                     break;
                 }
                 if (!P.resume) {
-                    const int v = find_view_tile(P.views, P.nviews, item);
-                    const int tl = item - P.views[v].tile_off;
+                    const int tile = P.tile_order ? P.tile_order[item] : item;
+                    const int v = find_view_tile(P.views, P.nviews, tile);
+                    const int tl = tile - P.views[v].tile_off;
                     const int tx = P.views[v].tiles_x;
+                    pool_tile = tile;
                     pool_a = v;
                     pool_x0 = (tl % tx) * P.tile_w;
                     pool_y0 = (tl / tx) * P.tile_h;
                     pool_cnt = P.tile_w * P.tile_h;
                 } else {
+                    pool_tile = -1;
                     pool_a = item * 32;
                     pool_cnt = min(32, P.nsusp_in - item * 32);
                 }
@@ -318,6 +438,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(const __grid_constant
                     py = (int)(loc / P.views[view].w);
                     ok = true;
                 }
+                my_tile = pool_tile;
                 if (ok) {
                     Ray R;
                     make_ray(P.views[view], P.vol.D0f, px, py, R);
@@ -329,7 +450,6 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(const __grid_constant
                         lodscale = P.views[view].lodscale;
                         k = k0; C0 = c0; C1 = c1; C2 = c2; T = tt;
                         cur_pti = kInvalidSlot;
-                        cur_slot = kInvalidSlot;
                     } else {
                         P.out[ray] = P.bg;
                         if (P.nsamp) P.nsamp[ray] = 0;
@@ -341,39 +461,68 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(const __grid_constant
         unsigned act = __ballot_sync(kFull, active);
         if (!act) break;
 
-        // ---- march
+        // ---- march: per iteration up to kBatch samples of each active ray
         const int thresh = queue_done ? 1 : P.refill_thresh;
         do {
             if (active) {
-                bool fin = false;
-                const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
-                if (!(t < t1)) {
-                    fin = true;
-                } else {
-                    if (GRAD && k > 0 && (k & (kCkptEvery - 1)) == 0)
-                        P.ckpt[(long long)(k / kCkptEvery - 1) * P.nrays + ray] = T;
+                // (a) decisions for the batch (ALU only)
+                uint32_t pti[kBatch], loc[kBatch];
+                float wgt[kBatch][3];
+                int nvalid = kBatch;
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const float t = __fadd_rn(t0, __fmul_rn((float)(k + j), step));
+                    if (!(t < t1) && nvalid == kBatch) nvalid = j;
                     const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
                                         __fadd_rn(o2, __fmul_rn(t, d2))};
-                    const int l = LOD ? lod_level(t, lodscale, P.lod_bias, P.vol.nlevels) : 0;
-                    Resolved R;
-                    resolve(s_lv[l], bshift, bmask, B1, p, R);
-                    if (R.pti != cur_pti) {
-                        cur_pti = R.pti;
-                        cur_slot = __ldg(P.vol.pt + R.pti);
-                        if (cur_slot != kInvalidSlot && P.last_used) P.last_used[cur_slot] = P.frame;
-                    }
-                    if (cur_slot == kInvalidSlot) {
-                        if (P.req_table) {
-                            request_brick(P, R.pti + 1u);
-                            suspend_ray(P, ray, k, C0, C1, C2, T);
-                        } else {
-                            atomicAdd(&P.counters[kDevError], 1u);
+                    if (LOD) {
+                        const int l = lod_level(t, lodscale, P.lod_bias, nlev);
+                        if (l != cur_l) {
+                            cur_l = l;
+                            L = load_lv(s_lv[l]);
                         }
-                        active = false;
-                    } else {
-                        const unsigned long long base = (unsigned long long)cur_slot * slot_elems + R.local;
-                        const float v = trilinear<DT>(atlas, base, B1, R.w);
-                        const float x = tf_coord<DT>(v);
+                    }
+                    Resolved R;
+                    resolve_reg(L, bshift, bmask, row, p, R);
+                    pti[j] = R.pti;
+                    loc[j] = R.local;
+                    wgt[j][0] = R.w[0];
+                    wgt[j][1] = R.w[1];
+                    wgt[j][2] = R.w[2];
+                }
+                // (b) page-table lookups, all issued together (samples past the exit read entry 0)
+                uint32_t slot[kBatch];
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) slot[j] = __ldg(P.vol.pt + (j < nvalid ? pti[j] : 0u));
+                int miss_at = kBatch;
+#pragma unroll
+                for (int j = kBatch - 1; j >= 0; --j)
+                    if (j < nvalid && slot[j] == kInvalidSlot) miss_at = j;
+                const uint32_t miss_pti = miss_at < kBatch ? pti[miss_at] : 0u;
+                // usage stamps: one store per brick change
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    if (j < nvalid && j < miss_at && pti[j] != cur_pti) {
+                        cur_pti = pti[j];
+                        if (P.last_used) P.last_used[slot[j]] = P.frame;
+                    }
+                }
+                // (c) gathers, all issued together (unused samples read slot 0, element 0)
+                float val[kBatch];
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const bool use = j < nvalid && j < miss_at;
+                    const unsigned long long base = use ? (unsigned long long)slot[j] * slot_stride + loc[j] : 0ull;
+                    val[j] = sample_value<DT, BS, Q>(P.vol.atlas, base, B1, wgt[j]);
+                }
+                const int stop = min(nvalid, miss_at);
+                bool fin = false;
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    if (j < stop && !fin) {
+                        if (GRAD && k > 0 && (k & (kCkptEvery - 1)) == 0)
+                            P.ckpt[(long long)(k / kCkptEvery - 1) * P.nrays + ray] = T;
+                        const float x = tf_coord<DT>(val[j]);
                         const int i = min((int)x, 254);
                         const float wt = x - (float)i;
                         const float4 a = s_tf[i], b = s_tf[i + 1];
@@ -387,12 +536,23 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(const __grid_constant
                         if (__fsub_rn(1.0f, T) >= et) fin = true;
                     }
                 }
+                if (!fin && nvalid < kBatch && nvalid <= miss_at) fin = true;  // left the volume
                 if (fin) {
                     const float4 bg = P.bg;
                     P.out[ray] = make_float4(fmaf(T, bg.x, C0), fmaf(T, bg.y, C1), fmaf(T, bg.z, C2),
                                              fmaf(T, bg.w, 1.0f - T));
                     if (P.nsamp) P.nsamp[ray] = k;
                     if (GRAD) P.ray_n[ray] = k;
+                    if (P.tile_cost && my_tile >= 0) atomicAdd(&P.tile_cost[my_tile], k);
+                    active = false;
+                } else if (miss_at < kBatch) {
+                    // wait for the missing brick: sample k (= the first missing one) resumes later
+                    if (P.req_table) {
+                        request_brick(P, miss_pti + 1u);
+                        suspend_ray(P, ray, k, C0, C1, C2, T);
+                    } else {
+                        atomicAdd(&P.counters[kDevError], 1u);
+                    }
                     active = false;
                 }
             }
@@ -423,6 +583,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_backward(const __grid_consta
     const unsigned long long slot_elems = P.vol.slot_elems;
     const int Dx = P.D0[0], Dy = P.D0[1];
     const float step = P.step;
+    const bool quad = P.vol.quad != 0;
 
     for (;;) {
         int item = 0;
@@ -453,11 +614,13 @@ __global__ void __launch_bounds__(kRenderThreads) k_backward(const __grid_consta
                     const float p[3] = {__fadd_rn(R.o[0], __fmul_rn(t, R.d[0])), __fadd_rn(R.o[1], __fmul_rn(t, R.d[1])),
                                         __fadd_rn(R.o[2], __fmul_rn(t, R.d[2]))};
                     Resolved Q;
-                    resolve(s_l0, bshift, bmask, B1, p, Q);
+                    resolve(s_l0, bshift, bmask, quad ? B1 - 1 : B1, p, Q);
                     const uint32_t slot = __ldg(P.vol.pt + Q.pti);
                     float val = 0.0f;
                     if (slot != kInvalidSlot) {
-                        val = trilinear<DT>(atlas, (unsigned long long)slot * slot_elems + Q.local, B1, Q.w);
+                        val = quad ? trilinear_quad<DT>(P.vol.atlas, (unsigned long long)slot * P.vol.slot_entries + Q.local,
+                                                        B1 - 1, Q.w)
+                                   : trilinear<DT>(atlas, (unsigned long long)slot * slot_elems + Q.local, B1, Q.w);
                     } else {
                         atomicAdd(&P.counters[kDevError], 1u);
                     }
@@ -475,7 +638,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_backward(const __grid_consta
                     const float p[3] = {__fadd_rn(R.o[0], __fmul_rn(t, R.d[0])), __fadd_rn(R.o[1], __fmul_rn(t, R.d[1])),
                                         __fadd_rn(R.o[2], __fmul_rn(t, R.d[2]))};
                     Resolved Q;
-                    resolve(s_l0, bshift, bmask, B1, p, Q);
+                    resolve(s_l0, bshift, bmask, quad ? B1 - 1 : B1, p, Q);
                     const float val = s_V[k - k0][tid];
                     const float Tk = s_T[k - k0][tid];
                     const float x = tf_coord<DT>(val);
@@ -526,6 +689,36 @@ __global__ void __launch_bounds__(kRenderThreads) k_backward(const __grid_consta
             if (s_dtf[i] != 0.0f) atomicAdd(&P.dtf[i], s_dtf[i]);
 }
 
+// ------------------------------------------------------------------ scheduling
+
+// Heaviest-first work order for the next frame (an approximate longest-processing-time-first
+// schedule): tiles bucketed by floor(log2(cost + 1)), buckets in descending order.  One CTA.
+constexpr int kOrderThreads = 1024;
+__global__ void __launch_bounds__(kOrderThreads) k_tile_order(int* cost, int* order, int ntiles) {
+    __shared__ int s_count[32];
+    __shared__ int s_off[32];
+    if (threadIdx.x < 32) s_count[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
+        const int b = 31 - __clz(cost[i] + 1);
+        atomicAdd(&s_count[b], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 31; b >= 0; --b) {
+            s_off[b] = acc;
+            acc += s_count[b];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
+        const int b = 31 - __clz(cost[i] + 1);
+        order[atomicAdd(&s_off[b], 1)] = i;
+        cost[i] = 0;
+    }
+}
+
 // ------------------------------------------------------------------ trace
 
 __global__ void k_trace(const __grid_constant__ TraceDev P) {
@@ -544,7 +737,7 @@ __global__ void k_trace(const __grid_constant__ TraceDev P) {
             const int l = P.lod_mode ? lod_level(t, P.view.lodscale, P.lod_bias, P.vol.nlevels) : 0;
             const LevelDev& L = P.vol.lv[l];
             Resolved Q;
-            resolve(L, P.vol.bshift, P.vol.bmask, P.vol.B1, p, Q);
+            resolve(L, P.vol.bshift, P.vol.bmask, P.vol.quad ? P.vol.B1 - 1 : P.vol.B1, p, Q);
             vol_trace_rec rec;
             rec.k = k;
             rec.t_bits = __float_as_uint(t);
@@ -563,17 +756,28 @@ __global__ void k_trace(const __grid_constant__ TraceDev P) {
     P.counts[q] = k;
 }
 
-const void* pick_render(int dtype, bool lod, bool grad) {
-#define VOLRC_PICK(DT)                                                              \
-    if (dtype == DT) {                                                              \
-        if (grad) return (const void*)k_render<DT, false, true>;                    \
-        return lod ? (const void*)k_render<DT, true, false> : (const void*)k_render<DT, false, false>; \
+template <int DT, int BS, bool Q>
+const void* pick_render_b(bool lod, bool grad) {
+    if (grad) return (const void*)k_render<DT, false, true, BS, Q>;
+    return lod ? (const void*)k_render<DT, true, false, BS, Q> : (const void*)k_render<DT, false, false, BS, Q>;
+}
+
+// quad layout: specialised for bricks of 32 and 64; compact layout: any brick size
+template <int DT>
+const void* pick_render_d(int brick, bool quad, bool lod, bool grad) {
+    if (!quad) return pick_render_b<DT, 0, false>(lod, grad);
+    if (brick == 32) return pick_render_b<DT, 32, true>(lod, grad);
+    if (brick == 64) return pick_render_b<DT, 64, true>(lod, grad);
+    return pick_render_b<DT, 0, true>(lod, grad);
+}
+
+const void* pick_render(int dtype, int brick, bool quad, bool lod, bool grad) {
+    switch (dtype) {
+    case VOL_U8: return pick_render_d<VOL_U8>(brick, quad, lod, grad);
+    case VOL_U16: return pick_render_d<VOL_U16>(brick, quad, lod, grad);
+    case VOL_F16: return pick_render_d<VOL_F16>(brick, quad, lod, grad);
+    case VOL_F32: return pick_render_d<VOL_F32>(brick, quad, lod, grad);
     }
-    VOLRC_PICK(VOL_U8)
-    VOLRC_PICK(VOL_U16)
-    VOLRC_PICK(VOL_F16)
-    VOLRC_PICK(VOL_F32)
-#undef VOLRC_PICK
     return nullptr;
 }
 
@@ -590,7 +794,7 @@ const void* pick_backward(int dtype) {
 }  // namespace
 
 cudaError_t launch_render(int dtype, bool grad, const RenderDev& p, int grid, cudaStream_t s) {
-    const void* fn = pick_render(dtype, p.lod_mode != 0, grad);
+    const void* fn = pick_render(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0, grad);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&p};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kRenderThreads), args, 0, s);
@@ -603,6 +807,12 @@ cudaError_t launch_backward(int dtype, const BackwardDev& p, int grid, cudaStrea
     return cudaLaunchKernel(fn, dim3(grid), dim3(kRenderThreads), args, 0, s);
 }
 
+cudaError_t launch_tile_order(int* cost, int* order, int ntiles, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    k_tile_order<<<1, kOrderThreads, 0, s>>>(cost, order, ntiles);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_trace(const TraceDev& p, cudaStream_t s) {
     const int threads = 64;
     k_trace<<<(p.npix + threads - 1) / threads, threads, 0, s>>>(p);
@@ -611,7 +821,7 @@ cudaError_t launch_trace(const TraceDev& p, cudaStream_t s) {
 
 int render_blocks_per_sm(int dtype, bool grad) {
     int n = 0;
-    const void* fn = pick_render(dtype, false, grad);
+    const void* fn = pick_render(dtype, 64, true, false, grad);
     if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kRenderThreads, 0) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }

@@ -1,4 +1,8 @@
 // kernels_volume.cu -- brick upload/transcode with apron, LOD downsample, page-table update.
+//
+// Slot layouts (include/vol.h): compact slots hold the (B+1)^3 voxels of a brick and its
+// +x/+y/+z apron; quad slots hold B x B x (B+1) entries of four voxels each, entry (x, y, z)
+// = voxels (x, y), (x+1, y), (x, y+1), (x+1, y+1) of slice z of that region.
 #include "internal.cuh"
 
 namespace volrc {
@@ -36,11 +40,31 @@ template <> struct Stored<VOL_U16> { using T = uint16_t; };
 template <> struct Stored<VOL_F16> { using T = __half; };
 template <> struct Stored<VOL_F32> { using T = float; };
 
+// one quad entry written with a single vector store
+template <int DT>
+__device__ __forceinline__ void store4(typename Stored<DT>::T* p, typename Stored<DT>::T a, typename Stored<DT>::T b,
+                                       typename Stored<DT>::T c, typename Stored<DT>::T d) {
+    if constexpr (DT == VOL_U8) {
+        *(uchar4*)p = make_uchar4(a, b, c, d);
+    } else if constexpr (DT == VOL_U16) {
+        *(ushort4*)p = make_ushort4(a, b, c, d);
+    } else if constexpr (DT == VOL_F16) {
+        *(ushort4*)p = make_ushort4(__half_as_ushort(a), __half_as_ushort(b), __half_as_ushort(c), __half_as_ushort(d));
+    } else {
+        *(float4*)p = make_float4(a, b, c, d);
+    }
+}
+
 constexpr int kThreads = 256;
 
-// One thread per slot voxel (apron included): grid.x covers (B+1)^3, grid.y/z the bricks.
+// One thread per slot voxel (compact) or entry (quad): grid.x covers the slot, grid.y/z bricks.
 __device__ __forceinline__ long long brick_index() {
     return (long long)blockIdx.y + (long long)gridDim.y * blockIdx.z;
+}
+
+__device__ __forceinline__ int slot_items(const VolDev& vol) {
+    const int B1 = vol.B1, B = B1 - 1;
+    return vol.quad ? B * B * B1 : B1 * B1 * B1;
 }
 
 template <int SRC, int DST>
@@ -51,82 +75,134 @@ __global__ void __launch_bounds__(kThreads) k_upload_level(const typename Stored
     const long long b = brick_index();
     if (b >= nbricks) return;
     const int B1 = vol.B1, B = B1 - 1;
-    const int nvox = B1 * B1 * B1;
     const int r = blockIdx.x * kThreads + threadIdx.x;
-    if (r >= nvox) return;
+    if (r >= slot_items(vol)) return;
     const uint32_t slot = slots[b];
     if (slot == kInvalidSlot) return;
     const LevelDev& L = vol.lv[level];
-    const int lx = r % B1, ly = (r / B1) % B1, lz = r / (B1 * B1);
     const int bx = (int)(b % L.nb[0]), by = (int)((b / L.nb[0]) % L.nb[1]), bz = (int)(b / ((long long)L.nb[0] * L.nb[1]));
-    const int gx = min(bx * B + lx, L.D[0] - 1), gy = min(by * B + ly, L.D[1] - 1), gz = min(bz * B + lz, L.D[2] - 1);
-    const long long si = (long long)gx + (long long)L.D[0] * ((long long)gy + (long long)L.D[1] * gz);
-    atlas[(unsigned long long)slot * vol.slot_elems + r] = Convert<SRC, DST>::run(src[si]);
+    const long long sy = L.D[0], sz = (long long)L.D[0] * L.D[1];
+    if (!vol.quad) {
+        const int lx = r % B1, ly = (r / B1) % B1, lz = r / (B1 * B1);
+        const long long gx = min(bx * B + lx, L.D[0] - 1), gy = min(by * B + ly, L.D[1] - 1), gz = min(bz * B + lz, L.D[2] - 1);
+        atlas[(unsigned long long)slot * vol.slot_elems + r] = Convert<SRC, DST>::run(src[gx + gy * sy + gz * sz]);
+        return;
+    }
+    const int lx = r % B, ly = (r / B) % B, lz = r / (B * B);
+    const long long x0 = min(bx * B + lx, L.D[0] - 1), x1 = min(bx * B + lx + 1, L.D[0] - 1);
+    const long long y0 = min(by * B + ly, L.D[1] - 1), y1 = min(by * B + ly + 1, L.D[1] - 1);
+    const long long zo = (long long)min(bz * B + lz, L.D[2] - 1) * sz;
+    store4<DST>(atlas + ((unsigned long long)slot * vol.slot_entries + r) * 4,
+                Convert<SRC, DST>::run(src[x0 + y0 * sy + zo]), Convert<SRC, DST>::run(src[x1 + y0 * sy + zo]),
+                Convert<SRC, DST>::run(src[x0 + y1 * sy + zo]), Convert<SRC, DST>::run(src[x1 + y1 * sy + zo]));
 }
 
-// n bricks of (B+1)^3 voxels each, packed in src, into slots[i].
+// n bricks of (B+1)^3 voxels each (compact, apron included), packed in src, into slots[i].
 template <int SRC, int DST>
 __global__ void __launch_bounds__(kThreads) k_upload_bricks(const typename Stored<SRC>::T* __restrict__ src,
-                                                            typename Stored<DST>::T* __restrict__ atlas,
-                                                            unsigned long long slot_elems, int nvox,
+                                                            typename Stored<DST>::T* __restrict__ atlas, VolDev vol,
                                                             const uint32_t* __restrict__ slots, long long n) {
     const long long b = brick_index();
     const int r = blockIdx.x * kThreads + threadIdx.x;
-    if (b >= n || r >= nvox) return;
+    if (b >= n || r >= slot_items(vol)) return;
     const uint32_t slot = slots[b];
     if (slot == kInvalidSlot) return;
-    atlas[(unsigned long long)slot * slot_elems + r] = Convert<SRC, DST>::run(src[b * nvox + r]);
+    const int B1 = vol.B1, B = B1 - 1;
+    const long long nvox = (long long)B1 * B1 * B1;
+    const typename Stored<SRC>::T* s = src + b * nvox;
+    if (!vol.quad) {
+        atlas[(unsigned long long)slot * vol.slot_elems + r] = Convert<SRC, DST>::run(s[r]);
+        return;
+    }
+    const int lx = r % B, ly = (r / B) % B, lz = r / (B * B);
+    const int i = (lz * B1 + ly) * B1 + lx;
+    store4<DST>(atlas + ((unsigned long long)slot * vol.slot_entries + r) * 4, Convert<SRC, DST>::run(s[i]),
+                Convert<SRC, DST>::run(s[i + 1]), Convert<SRC, DST>::run(s[i + B1]), Convert<SRC, DST>::run(s[i + B1 + 1]));
 }
 
-// 2x2x2 box filter from level-1 into the slots of `level` (Sec. III-D).  Children are read
-// through the fine level's page table; a child index past the edge is replaced by the last
-// fine voxel.  Integer: (sum + 4) >> 3.  Float: binary32 sum in (dz, dy, dx) order, * 0.125.
+// Voxel (cx, cy, cz) of a fine level, read through that level's page table (any layout).
+// *bad is set when its brick is not resident.
 template <int DT>
-__global__ void __launch_bounds__(kThreads) k_downsample(typename Stored<DT>::T* __restrict__ atlas, VolDev vol,
-                                                         int level, const uint32_t* __restrict__ slots,
-                                                         long long nbricks, unsigned* err) {
+__device__ __forceinline__ typename Stored<DT>::T fine_voxel(const typename Stored<DT>::T* atlas, const VolDev& vol,
+                                                             const LevelDev& F, int cx, int cy, int cz, bool* bad) {
+    const uint32_t pti =
+        F.pt_off + (uint32_t)((cx >> vol.bshift) + F.nb[0] * ((cy >> vol.bshift) + F.nb[1] * (cz >> vol.bshift)));
+    const uint32_t cs = vol.pt[pti];
+    if (cs == kInvalidSlot) {
+        *bad = true;
+        return typename Stored<DT>::T(0);
+    }
+    const int lx = cx & vol.bmask, ly = cy & vol.bmask, lz = cz & vol.bmask;
+    if (vol.quad) {
+        const int B = vol.B1 - 1;
+        return atlas[((unsigned long long)cs * vol.slot_entries + (unsigned)((lz * B + ly) * B + lx)) * 4];
+    }
+    const int B1 = vol.B1;
+    return atlas[(unsigned long long)cs * vol.slot_elems + (unsigned)((lz * B1 + ly) * B1 + lx)];
+}
+
+// Coarse voxel g of a level from the level below by the 2x2x2 box filter (Sec. III-D):
+// children 2g and 2g+1 per axis, an index past the edge replaced by the last fine voxel;
+// integer types (sum + 4) >> 3, float types a binary32 sum in (dz, dy, dx) order times 0.125.
+template <int DT>
+__device__ __forceinline__ typename Stored<DT>::T coarse_voxel(const typename Stored<DT>::T* atlas, const VolDev& vol,
+                                                               const LevelDev& F, int gx, int gy, int gz, bool* bad) {
     using VT = typename Stored<DT>::T;
-    const long long b = brick_index();
-    if (b >= nbricks) return;
-    const int B1 = vol.B1, B = B1 - 1;
-    const int nvox = B1 * B1 * B1;
-    const int r = blockIdx.x * kThreads + threadIdx.x;
-    if (r >= nvox) return;
-    const uint32_t slot = slots[b];
-    if (slot == kInvalidSlot) return;
-    const LevelDev& L = vol.lv[level];
-    const LevelDev& F = vol.lv[level - 1];
-    const int lx = r % B1, ly = (r / B1) % B1, lz = r / (B1 * B1);
-    const int bx = (int)(b % L.nb[0]), by = (int)((b / L.nb[0]) % L.nb[1]), bz = (int)(b / ((long long)L.nb[0] * L.nb[1]));
-    const int g[3] = {min(bx * B + lx, L.D[0] - 1), min(by * B + ly, L.D[1] - 1), min(bz * B + lz, L.D[2] - 1)};
     int isum = 0;
     float fsum = 0.0f;
-    bool bad = false;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int dz = c >> 2, dy = (c >> 1) & 1, dx = c & 1;
-        const int cx = min(2 * g[0] + dx, F.D[0] - 1), cy = min(2 * g[1] + dy, F.D[1] - 1), cz = min(2 * g[2] + dz, F.D[2] - 1);
-        const uint32_t pti = F.pt_off + (uint32_t)((cx >> vol.bshift) + F.nb[0] * ((cy >> vol.bshift) + F.nb[1] * (cz >> vol.bshift)));
-        const uint32_t cs = vol.pt[pti];
-        if (cs == kInvalidSlot) {
-            bad = true;
-            continue;
-        }
-        const int lo = ((cz & vol.bmask) * B1 + (cy & vol.bmask)) * B1 + (cx & vol.bmask);
-        const VT val = atlas[(unsigned long long)cs * vol.slot_elems + lo];
+        const VT val = fine_voxel<DT>(atlas, vol, F, min(2 * gx + dx, F.D[0] - 1), min(2 * gy + dy, F.D[1] - 1),
+                                      min(2 * gz + dz, F.D[2] - 1), bad);
         if constexpr (DT == VOL_U8 || DT == VOL_U16) isum += (int)val;
         else if constexpr (DT == VOL_F16) fsum = __fadd_rn(fsum, __half2float(val));
         else fsum = __fadd_rn(fsum, val);
     }
+    if constexpr (DT == VOL_U8 || DT == VOL_U16) return (VT)((isum + 4) >> 3);
+    else if constexpr (DT == VOL_F16) return __float2half_rn(__fmul_rn(fsum, 0.125f));
+    else return __fmul_rn(fsum, 0.125f);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads) k_downsample(typename Stored<DT>::T* __restrict__ atlas, VolDev vol,
+                                                         int level, const uint32_t* __restrict__ slots,
+                                                         long long nbricks, unsigned* err) {
+    const long long b = brick_index();
+    if (b >= nbricks) return;
+    const int B1 = vol.B1, B = B1 - 1;
+    const int r = blockIdx.x * kThreads + threadIdx.x;
+    if (r >= slot_items(vol)) return;
+    const uint32_t slot = slots[b];
+    if (slot == kInvalidSlot) return;
+    const LevelDev& L = vol.lv[level];
+    const LevelDev& F = vol.lv[level - 1];
+    const int bx = (int)(b % L.nb[0]), by = (int)((b / L.nb[0]) % L.nb[1]), bz = (int)(b / ((long long)L.nb[0] * L.nb[1]));
+    bool bad = false;
+    if (!vol.quad) {
+        const int lx = r % B1, ly = (r / B1) % B1, lz = r / (B1 * B1);
+        const auto v = coarse_voxel<DT>(atlas, vol, F, min(bx * B + lx, L.D[0] - 1), min(by * B + ly, L.D[1] - 1),
+                                        min(bz * B + lz, L.D[2] - 1), &bad);
+        if (bad) {
+            atomicAdd(err, 1u);
+            return;
+        }
+        atlas[(unsigned long long)slot * vol.slot_elems + r] = v;
+        return;
+    }
+    const int lx = r % B, ly = (r / B) % B, lz = r / (B * B);
+    const int x0 = min(bx * B + lx, L.D[0] - 1), x1 = min(bx * B + lx + 1, L.D[0] - 1);
+    const int y0 = min(by * B + ly, L.D[1] - 1), y1 = min(by * B + ly + 1, L.D[1] - 1);
+    const int z = min(bz * B + lz, L.D[2] - 1);
+    const auto v0 = coarse_voxel<DT>(atlas, vol, F, x0, y0, z, &bad);
+    const auto v1 = coarse_voxel<DT>(atlas, vol, F, x1, y0, z, &bad);
+    const auto v2 = coarse_voxel<DT>(atlas, vol, F, x0, y1, z, &bad);
+    const auto v3 = coarse_voxel<DT>(atlas, vol, F, x1, y1, z, &bad);
     if (bad) {
         atomicAdd(err, 1u);
         return;
     }
-    VT out;
-    if constexpr (DT == VOL_U8 || DT == VOL_U16) out = (VT)((isum + 4) >> 3);
-    else if constexpr (DT == VOL_F16) out = __float2half_rn(__fmul_rn(fsum, 0.125f));
-    else out = __fmul_rn(fsum, 0.125f);
-    atlas[(unsigned long long)slot * vol.slot_elems + r] = out;
+    store4<DT>(atlas + ((unsigned long long)slot * vol.slot_entries + r) * 4, v0, v1, v2, v3);
 }
 
 __global__ void k_pt_update(uint32_t* pt, const uint32_t* idx, const uint32_t* val, int n) {
@@ -134,8 +210,10 @@ __global__ void k_pt_update(uint32_t* pt, const uint32_t* idx, const uint32_t* v
     if (i < n) atomicExch(&pt[idx[i]], val[i]);
 }
 
-dim3 brick_grid(int nvox, long long nbricks) {
-    const unsigned gx = (unsigned)((nvox + kThreads - 1) / kThreads);
+dim3 brick_grid(const VolDev& vol, long long nbricks) {
+    const int B1 = vol.B1, B = B1 - 1;
+    const int items = vol.quad ? B * B * B1 : B1 * B1 * B1;
+    const unsigned gx = (unsigned)((items + kThreads - 1) / kThreads);
     const long long gy = nbricks < 65535 ? nbricks : 65535;
     const long long gz = (nbricks + gy - 1) / gy;
     return dim3(gx, (unsigned)(gy > 0 ? gy : 1), (unsigned)(gz > 0 ? gz : 1));
@@ -146,8 +224,7 @@ dim3 brick_grid(int nvox, long long nbricks) {
 cudaError_t launch_upload_level(int dst, int src_t, const void* src, const VolDev& vol, int level,
                                 const uint32_t* slots, long long nbricks, cudaStream_t s) {
     if (nbricks <= 0) return cudaSuccess;
-    const int nvox = vol.B1 * vol.B1 * vol.B1;
-    const dim3 grid = brick_grid(nvox, nbricks);
+    const dim3 grid = brick_grid(vol, nbricks);
 #define VOLRC_UP(S, D)                                                                                  \
     if (src_t == S && dst == D) {                                                                       \
         k_upload_level<S, D><<<grid, kThreads, 0, s>>>((const Stored<S>::T*)src, (Stored<D>::T*)vol.atlas, \
@@ -168,13 +245,12 @@ cudaError_t launch_upload_level(int dst, int src_t, const void* src, const VolDe
 cudaError_t launch_upload_bricks(int dst, int src_t, const void* src, const VolDev& vol, const uint32_t* slots,
                                  long long n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const int nvox = vol.B1 * vol.B1 * vol.B1;
-    const dim3 grid = brick_grid(nvox, n);
-#define VOLRC_UPB(S, D)                                                                                     \
-    if (src_t == S && dst == D) {                                                                           \
-        k_upload_bricks<S, D><<<grid, kThreads, 0, s>>>((const Stored<S>::T*)src, (Stored<D>::T*)vol.atlas, \
-                                                        vol.slot_elems, nvox, slots, n);                    \
-        return cudaGetLastError();                                                                          \
+    const dim3 grid = brick_grid(vol, n);
+#define VOLRC_UPB(S, D)                                                                                      \
+    if (src_t == S && dst == D) {                                                                            \
+        k_upload_bricks<S, D><<<grid, kThreads, 0, s>>>((const Stored<S>::T*)src, (Stored<D>::T*)vol.atlas,  \
+                                                        vol, slots, n);                                      \
+        return cudaGetLastError();                                                                           \
     }
     VOLRC_UPB(VOL_U8, VOL_U8)
     VOLRC_UPB(VOL_U16, VOL_U16)
@@ -190,8 +266,7 @@ cudaError_t launch_upload_bricks(int dst, int src_t, const void* src, const VolD
 cudaError_t launch_downsample(int dtype, const VolDev& vol, int level, const uint32_t* slots, long long nbricks,
                               unsigned* err, cudaStream_t s) {
     if (nbricks <= 0) return cudaSuccess;
-    const int nvox = vol.B1 * vol.B1 * vol.B1;
-    const dim3 grid = brick_grid(nvox, nbricks);
+    const dim3 grid = brick_grid(vol, nbricks);
     switch (dtype) {
     case VOL_U8: k_downsample<VOL_U8><<<grid, kThreads, 0, s>>>((uint8_t*)vol.atlas, vol, level, slots, nbricks, err); break;
     case VOL_U16: k_downsample<VOL_U16><<<grid, kThreads, 0, s>>>((uint16_t*)vol.atlas, vol, level, slots, nbricks, err); break;

@@ -37,7 +37,8 @@ bool conversion_ok(int src, int dst) {
     return (src == VOL_U16 && dst == VOL_F16) || (src == VOL_U8 && dst == VOL_F32) || (src == VOL_U16 && dst == VOL_F32);
 }
 
-int plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes, vol_layout* o, std::string& err) {
+int plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes, uint32_t flags, vol_layout* o,
+         std::string& err) {
     if (!dims || !o) { err = "null argument"; return VOL_ERR_INVALID_ARG; }
     memset(o, 0, sizeof(*o));
     const int bpv = bpv_of(dtype);
@@ -50,6 +51,9 @@ int plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache
     o->brick = brick;
     o->levels = levels;
     o->bytes_per_voxel = bpv;
+    if (flags & ~VOL_LAYOUT_COMPACT) { err = "unknown flags"; return VOL_ERR_INVALID_ARG; }
+    o->layout = (flags & VOL_LAYOUT_COMPACT) ? 1 : 0;
+    o->entry_voxels = o->layout ? 1 : 4;
     int64_t off = 0;
     for (int l = 0; l < levels; ++l) {
         for (int a = 0; a < 3; ++a) {
@@ -63,7 +67,8 @@ int plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache
     if (off >= (int64_t)0xFFFFFFF0ll) { err = "too many bricks for 32-bit page-table indices"; return VOL_ERR_UNSUPPORTED; }
     o->total_bricks = off;
     const int64_t B1 = brick + 1;
-    o->slot_bytes = ((B1 * B1 * B1 * bpv + 255) / 256) * 256;
+    const int64_t slot_voxels = o->layout ? B1 * B1 * B1 : 4 * (int64_t)brick * brick * B1;
+    o->slot_bytes = ((slot_voxels * bpv + 255) / 256) * 256;
     int64_t ns = cache_bytes == 0 ? off : (int64_t)(cache_bytes / (uint64_t)o->slot_bytes);
     if (ns > off) ns = off;
     if (ns < 1) { err = "cache smaller than one brick"; return VOL_ERR_INVALID_ARG; }
@@ -143,6 +148,14 @@ struct vol_s {
     uint32_t* stage_slots_dev = nullptr;
     int stage_bricks = 0;
 
+    // heaviest-first scheduling from the previous frame's per-tile sample counts
+    int* tile_cost = nullptr;
+    size_t tile_cost_cap = 0;
+    int* tile_order = nullptr;
+    size_t tile_order_cap = 0;
+    std::vector<unsigned char> order_key;  // view table + tile shape the order was built for
+    bool order_ready = false;
+
     vol_stats stats{};
     int occ_cache[4][2] = {{0}};
 };
@@ -170,6 +183,8 @@ VolDev vol_dev(const vol_t v) {
     VolDev d{};
     d.atlas = v->atlas;
     d.slot_elems = (unsigned long long)(v->lay.slot_bytes / v->lay.bytes_per_voxel);
+    d.quad = v->lay.layout == 0 ? 1 : 0;
+    d.slot_entries = d.slot_elems / 4;
     d.bshift = v->bshift;
     d.bmask = v->B - 1;
     d.B1 = v->B + 1;
@@ -370,7 +385,9 @@ int run_pass(vol_t v, bool resume, bool may_miss) {
         p.resume = 0;
         p.susp_out = v->susp[v->susp_cur];
         p.nwork = v->ntiles;
+        p.tile_order = v->order_ready ? v->tile_order : nullptr;
     }
+    p.tile_cost = v->tile_cost;
     CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
     const int grid = grid_for(v, v->dtype, v->grad, v->params.ctas_per_sm);
     CK(v, launch_render(v->dtype, v->grad, p, grid, v->stream));
@@ -485,18 +502,19 @@ int miss_loop(vol_t v, bool first_resumed) {
 // =====================================================================================
 extern "C" {
 
-int vol_plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes, vol_layout* out) {
+int vol_plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes, uint32_t flags,
+             vol_layout* out) {
     std::string err;
-    return plan(dims, dtype, brick, levels, cache_bytes, out, err);
+    return plan(dims, dtype, brick, levels, cache_bytes, flags, out, err);
 }
 
-int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes, void* stream,
-               vol_t* out) {
+int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes, uint32_t flags,
+               void* stream, vol_t* out) {
     if (!out) return fail(nullptr, VOL_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     vol_layout lay;
     std::string err;
-    if (int rc = plan(dims, dtype, brick, levels, cache_bytes, &lay, err)) return fail(nullptr, rc, err);
+    if (int rc = plan(dims, dtype, brick, levels, cache_bytes, flags, &lay, err)) return fail(nullptr, rc, err);
     vol_t v = new vol_s();
     v->lay = lay;
     v->dtype = dtype;
@@ -537,7 +555,8 @@ void vol_destroy(vol_t v) {
     if (v->stream) cudaStreamSynchronize(v->stream);
     else cudaDeviceSynchronize();
     void* bufs[] = {v->atlas, v->pt, v->last_used, v->counters, v->aux, v->upd_dev, v->views_dev, v->req_table,
-                    v->req_list, v->susp[0], v->susp[1], v->ckpt, v->ray_n, v->stage_dev, v->stage_slots_dev};
+                    v->req_list, v->susp[0], v->susp[1], v->ckpt, v->ray_n, v->stage_dev, v->stage_slots_dev,
+                    v->tile_cost, v->tile_order};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (v->stage_host) cudaFreeHost(v->stage_host);
@@ -674,11 +693,28 @@ int vol_download_brick(vol_t v, int level, const int32_t brick[3], void* dst) {
     if (!dst || brick_pti(v, level, brick, &pti)) return fail(v, VOL_ERR_INVALID_ARG, "bad level, brick or dst");
     const uint32_t s = v->pt_host[pti];
     if (s == kInvalidSlot) return fail(v, VOL_ERR_INVALID_ARG, "brick not resident");
-    const int64_t B1 = v->B + 1;
-    const size_t bytes = (size_t)(B1 * B1 * B1) * v->lay.bytes_per_voxel;
-    CK(v, cudaMemcpyAsync(dst, (const char*)v->atlas + (size_t)s * v->lay.slot_bytes, bytes, cudaMemcpyDeviceToHost,
-                          v->stream));
+    const int64_t B = v->B, B1 = B + 1;
+    const int bpv = v->lay.bytes_per_voxel;
+    const char* src = (const char*)v->atlas + (size_t)s * v->lay.slot_bytes;
+    if (v->lay.layout == 1) {
+        CK(v, cudaMemcpyAsync(dst, src, (size_t)(B1 * B1 * B1) * bpv, cudaMemcpyDeviceToHost, v->stream));
+        CK(v, cudaStreamSynchronize(v->stream));
+        return VOL_OK;
+    }
+    // quad layout: voxel (x, y, z) of the (B+1)^3 region is component (x == B) + 2 (y == B) of
+    // entry (min(x, B-1), min(y, B-1), z)
+    std::vector<char> raw((size_t)v->lay.slot_bytes);
+    CK(v, cudaMemcpyAsync(raw.data(), src, raw.size(), cudaMemcpyDeviceToHost, v->stream));
     CK(v, cudaStreamSynchronize(v->stream));
+    char* out = (char*)dst;
+    for (int64_t z = 0; z < B1; ++z)
+        for (int64_t y = 0; y < B1; ++y)
+            for (int64_t x = 0; x < B1; ++x) {
+                const int64_t ex = x < B ? x : B - 1, ey = y < B ? y : B - 1;
+                const int comp = (x == B ? 1 : 0) + (y == B ? 2 : 0);
+                const int64_t e = (z * B + ey) * B + ex;
+                memcpy(out + ((z * B1 + y) * B1 + x) * bpv, raw.data() + (e * 4 + comp) * bpv, bpv);
+            }
     return VOL_OK;
 }
 
@@ -716,10 +752,10 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     vol_params p = *params;
     if (!(p.step > 0.0f) || !std::isfinite(p.step)) return fail(v, VOL_ERR_INVALID_ARG, "step must be > 0");
     if (p.tile_w <= 0) p.tile_w = 8;
-    if (p.tile_h <= 0) p.tile_h = 8;
-    if ((p.tile_w * p.tile_h) % 32 != 0 || p.tile_w * p.tile_h > 4096)
-        return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be a multiple of 32, at most 4096");
-    if (p.refill <= 0 || p.refill > 32) p.refill = 24;
+    if (p.tile_h <= 0) p.tile_h = 4;
+    if (p.tile_w > 4096 || p.tile_h > 4096 || p.tile_w * p.tile_h > 4096)
+        return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be at most 4096");
+    if (p.refill <= 0 || p.refill > 32) p.refill = 30;
     if (p.lod_mode != 0 && p.lod_mode != 1) return fail(v, VOL_ERR_INVALID_ARG, "lod_mode must be 0 or 1");
     const bool grad = (p.flags & VOL_RENDER_GRAD) != 0;
     if (grad && p.lod_mode != 0) return fail(v, VOL_ERR_UNSUPPORTED, "gradients need lod_mode 0");
@@ -781,16 +817,38 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         if (int rc = ensure(v, v->ckpt, v->ckpt_cap, (size_t)std::max<int64_t>(1, segs - 1) * (size_t)rays, "checkpoints")) return rc;
         if (int rc = ensure(v, v->ray_n, v->ray_n_cap, (size_t)rays, "ray sample counts")) return rc;
     }
+    // scheduling state: the previous frame's heaviest-first order is reused while the tile
+    // partition (tile shape, number of views, image sizes) is unchanged; cameras may move.
+    // The order is only a schedule: the image never depends on it.
+    {
+        std::vector<int> key;
+        key.reserve(3 + 2 * (size_t)nviews);
+        key.push_back(p.tile_w);
+        key.push_back(p.tile_h);
+        key.push_back(nviews);
+        for (int i = 0; i < nviews; ++i) {
+            key.push_back(cams[i].w);
+            key.push_back(cams[i].h);
+        }
+        std::vector<unsigned char> kb((const unsigned char*)key.data(), (const unsigned char*)(key.data() + key.size()));
+        if (kb != v->order_key || !v->tile_cost || !v->tile_order) {
+            if (int rc = ensure(v, v->tile_cost, v->tile_cost_cap, (size_t)tiles, "tile costs")) return rc;
+            if (int rc = ensure(v, v->tile_order, v->tile_order_cap, (size_t)tiles, "tile order")) return rc;
+            CK(v, cudaMemsetAsync(v->tile_cost, 0, sizeof(int) * (size_t)tiles, v->stream));
+            v->order_ready = false;
+            v->order_key = kb;
+        }
+    }
     const bool may_miss = !all_resident(v, p.lod_mode != 0);
     if (may_miss)
         if (int rc = ensure_miss_buffers(v)) return rc;
     if (int rc = run_pass(v, false, may_miss)) return rc;
-    if (!may_miss) {
-        v->have_forward = true;
-        return VOL_OK;
-    }
-    int rc = miss_loop(v, false);
+    int rc = may_miss ? miss_loop(v, false) : VOL_OK;
     if (rc == VOL_OK) v->have_forward = true;
+    if (rc == VOL_OK || rc == VOL_ERR_INCOMPLETE) {
+        CK(v, launch_tile_order(v->tile_cost, v->tile_order, (int)tiles, v->stream));
+        v->order_ready = true;
+    }
     return rc;
 }
 
@@ -957,10 +1015,10 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
     vol_params p = *params;
     if (!(p.step > 0.0f) || !std::isfinite(p.step)) return fail(v, VOL_ERR_INVALID_ARG, "step must be > 0");
     if (p.tile_w <= 0) p.tile_w = 8;
-    if (p.tile_h <= 0) p.tile_h = 8;
-    if ((p.tile_w * p.tile_h) % 32 != 0 || p.tile_w * p.tile_h > 4096)
-        return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be a multiple of 32, at most 4096");
-    if (p.refill <= 0 || p.refill > 32) p.refill = 24;
+    if (p.tile_h <= 0) p.tile_h = 4;
+    if (p.tile_w > 4096 || p.tile_h > 4096 || p.tile_w * p.tile_h > 4096)
+        return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be at most 4096");
+    if (p.refill <= 0 || p.refill > 32) p.refill = 30;
     if (p.lod_mode != 0 && p.lod_mode != 1) return fail(v, VOL_ERR_INVALID_ARG, "lod_mode must be 0 or 1");
     if (p.flags & VOL_RENDER_GRAD)
         return fail(v, VOL_ERR_UNSUPPORTED, "vol_render_noalloc keeps no gradient state; use vol_render");

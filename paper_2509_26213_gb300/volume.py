@@ -41,10 +41,11 @@ def params_struct(step=0.5, et=0.99, bg=(0.0, 0.0, 0.0, 0.0), lod_mode=0, lod_bi
     return p
 
 
-def plan(dims, dtype: str, brick: int, levels: int, cache_bytes: int = 0) -> C.vol_layout:
+def plan(dims, dtype: str, brick: int, levels: int, cache_bytes: int = 0, layout: str = "quad") -> C.vol_layout:
     lay = C.vol_layout()
     d = (ctypes.c_int64 * 3)(*[int(x) for x in dims])
-    C.check(C.load().vol_plan(d, C.DTYPES[dtype], int(brick), int(levels), int(cache_bytes), ctypes.byref(lay)))
+    C.check(C.load().vol_plan(d, C.DTYPES[dtype], int(brick), int(levels), int(cache_bytes), C.LAYOUTS[layout],
+                              ctypes.byref(lay)))
     return lay
 
 
@@ -57,9 +58,10 @@ class Volume:
 
     dims = (Dx, Dy, Dz) level-0 voxels; dtype in {"u8", "u16", "f16", "f32"} (storage);
     brick = brick edge B (power of two); levels = LOD levels; cache_bytes = atlas size
-    (0 = room for every brick of every level)."""
+    (0 = room for every brick of every level); layout = "quad" (four-voxel entries, two
+    loads per sample, about 4x memory) or "compact" ((B+1)^3 voxels per brick)."""
 
-    def __init__(self, dims, dtype: str, brick: int, levels: int, cache_bytes: int = 0):
+    def __init__(self, dims, dtype: str, brick: int, levels: int, cache_bytes: int = 0, layout: str = "quad"):
         self.lib = C.load()
         self.dims = tuple(int(x) for x in dims)
         self.dtype = dtype
@@ -67,8 +69,8 @@ class Volume:
         self.levels = int(levels)
         h = ctypes.c_void_p()
         d = (ctypes.c_int64 * 3)(*self.dims)
-        C.check(self.lib.vol_create(d, C.DTYPES[dtype], self.brick, self.levels, int(cache_bytes), _stream_ptr(),
-                                    ctypes.byref(h)))
+        C.check(self.lib.vol_create(d, C.DTYPES[dtype], self.brick, self.levels, int(cache_bytes),
+                                    C.LAYOUTS[layout], _stream_ptr(), ctypes.byref(h)))
         self.h = h
         self._provider = None
         lay = C.vol_layout()

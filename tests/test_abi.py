@@ -46,10 +46,12 @@ def test_plan_chunk_addressing(lib):
     assert [tuple(lay.level_bricks[l]) for l in range(4)] == [(63, 1, 1), (32, 1, 1), (16, 1, 1), (8, 1, 1)]
     assert list(lay.level_pt_offset[:4]) == [0, 63, 95, 111]
     assert lay.total_bricks == 119
-    assert lay.slot_bytes == ((17 ** 3 * 2 + 255) // 256) * 256
+    assert lay.slot_bytes == ((4 * 16 * 16 * 17 * 2 + 255) // 256) * 256   # quad: B*B*(B+1) entries of 4
     assert lay.nslots == 119
+    cmp = plan((1000, 7, 1), "u16", 16, 4, layout="compact")
+    assert cmp.slot_bytes == ((17 ** 3 * 2 + 255) // 256) * 256         # compact: (B+1)^3 voxels
+    assert (lay.layout, lay.entry_voxels, cmp.layout, cmp.entry_voxels) == (0, 4, 1, 1)
     c3 = plan((2048, 2048, 2048), "u8", 32, 6)
-    assert c3.total_bricks == sum(8 ** (3 * (6 - l)) // 8 ** 3 * 8 ** 3 // 8 ** 3 for l in range(6)) or True
     assert c3.total_bricks == 64 ** 3 + 32 ** 3 + 16 ** 3 + 8 ** 3 + 4 ** 3 + 2 ** 3
     # a cache budget caps the slot count
     c5 = plan((4096, 4096, 4096), "u8", 64, 7, cache_bytes=16 << 30)
@@ -63,7 +65,7 @@ def test_plan_rejects(lib, bad):
     args.update(bad)
     lay = lib.vol_layout()
     d = (ctypes.c_int64 * 3)(*args["dims"])
-    rc = lib.load().vol_plan(d, args["dtype"], args["brick"], args["levels"], 0, ctypes.byref(lay))
+    rc = lib.load().vol_plan(d, args["dtype"], args["brick"], args["levels"], 0, 0, ctypes.byref(lay))
     assert rc == lib.VOL_ERR_INVALID_ARG
 
 

@@ -23,9 +23,9 @@ def P():
     return volume
 
 
-def gpu_volume(P, raw0, src_dtype, store_dtype, brick, levels, cache_bytes=0):
+def gpu_volume(P, raw0, src_dtype, store_dtype, brick, levels, cache_bytes=0, layout="quad"):
     Dz, Dy, Dx = raw0.shape
-    vol = P.Volume((Dx, Dy, Dz), store_dtype, brick, levels, cache_bytes)
+    vol = P.Volume((Dx, Dy, Dz), store_dtype, brick, levels, cache_bytes, layout=layout)
     vol.upload_level(0, raw0, src_dtype)
     if levels > 1:
         vol.build_lod(0)
@@ -79,9 +79,10 @@ def test_trace_bit_exact(P, orc, lod):
         assert (lv == 0).any() and (lv == 1).any()
 
 
+@pytest.mark.parametrize("layout", ["quad", "compact"])
 @pytest.mark.parametrize("store,src", [("u8", "u8"), ("u16", "u16"), ("f16", "u16"), ("f32", "f32"),
                                        ("f32", "u8"), ("f16", "f16")])
-def test_upload_and_downsample_bit_exact(P, orc, store, src):
+def test_upload_and_downsample_bit_exact(P, orc, store, src, layout):
     rng = np.random.default_rng(5)
     shape = (33, 45, 70)  # ragged against 16^3 bricks on every axis
     if src == "u8":
@@ -93,7 +94,7 @@ def test_upload_and_downsample_bit_exact(P, orc, store, src):
     else:
         raw = rng.random(shape, dtype=np.float32)
     L = 4
-    vol = gpu_volume(P, raw, src, store, 16, L)
+    vol = gpu_volume(P, raw, src, store, 16, L, layout=layout)
     levels = store_levels(orc, raw, src, store, L)
     npdt = {"u8": np.uint8, "u16": np.uint16, "f16": np.uint16, "f32": np.float32}[store]
     for l, arr in enumerate(levels):
@@ -234,3 +235,48 @@ def test_requests_without_provider_then_resume(P, orc):
         if vol.resume() == 0:
             break
     np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("dtype,brick", [("u8", 32), ("u16", 64), ("f16", 16), ("f32", 32)])
+def test_quad_and_compact_layouts_give_identical_images(P, orc, dtype, brick):
+    """The two atlas layouts gather the same eight corners and interpolate in the same order."""
+    D = (70, 45, 66)
+    base = synth.blobs(D, 12, dtype="f32", nblobs=7, sigma=(4, 12), amp=(0.2, 0.9), noise=0.05, vmax=1.0)
+    raw = {"u8": (base * 255).astype(np.uint8), "u16": (base * 65535).astype(np.uint16),
+           "f16": base.astype(np.float16).view(np.uint16), "f32": base}[dtype]
+    tf = synth.tf_peaks(12)
+    tf[:, 3] = np.clip(tf[:, 3] + 0.02, 0, 1)
+    cams = [synth.seeded_orbit(D, 61, 47, 12, view=v) for v in range(3)]
+    imgs = []
+    for layout in ("quad", "compact"):
+        vol = gpu_volume(P, raw, dtype, dtype, brick, 3, layout=layout)
+        imgs.append(vol.render(cams, tf_dev(tf), {"lod_mode": 1, "lod_bias": 1}).cpu().numpy())
+        vol.close()
+    np.testing.assert_array_equal(imgs[0], imgs[1])
+    ovol = orc.Volume(store_levels(orc, raw, dtype, dtype, 3), dtype, brick)
+    off = 0
+    for cam in cams:
+        n = cam["w"] * cam["h"]
+        ref = orc.render(ovol, cam, tf, {"lod_mode": 1, "lod_bias": 1}, amb=AMB)
+        err, bad, _ = compare(imgs[0][off:off + n], ref, TOL_FP32)
+        assert len(bad) == 0, err
+        off += n
+
+
+def test_compact_layout_miss_path(P, orc):
+    """Out-of-core use with the compact layout (more bricks per cache byte): still the resident image."""
+    D, raw, cam, tf, params = c1_inputs(seed=8)
+    levels = store_levels(orc, raw, "u8", "u8", 1)
+    want = gpu_volume(P, raw, "u8", "u8", 16, 1).render(cam, tf_dev(tf), params).cpu().numpy()
+    slot = P.plan(D, "u8", 16, 1, layout="compact").slot_bytes
+    vol = P.Volume(D, "u8", 16, 1, cache_bytes=200 * slot, layout="compact")
+
+    def provider(level, b):
+        arr = levels[level]
+        Dz, Dy, Dx = arr.shape
+        idx = [np.minimum(b[a] * 16 + np.arange(17), d - 1) for a, d in ((2, Dz), (1, Dy), (0, Dx))]
+        return arr[np.ix_(*idx)]
+
+    vol.set_provider(provider, "u8")
+    got = vol.render(cam, tf_dev(tf), dict(params, max_passes=300)).cpu().numpy()
+    np.testing.assert_array_equal(got, want)
