@@ -392,8 +392,8 @@ def run_ours(args, dist, rank, ws, local):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": 4096,
                     "d2h_bytes_per_step": npx * 16, "ms_per_step": e2e_step},
-            # per step: the render kernel and the heaviest-first scheduling kernel
-            "gpu_launches": 2 * args.steps,
+            # per step: the render kernel and the two heaviest-first scheduling kernels
+            "gpu_launches": 3 * args.steps,
             "clocks": clocks,
             "wall_s_timed": wall,
             "variants": variants,
@@ -427,7 +427,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="primary line only (no storage variants, no fwd+bwd)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s", "c3", "c4"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-frac", type=float, default=0.25, help="reference arm: fraction of pixels per step")
     args = ap.parse_args()

@@ -78,12 +78,12 @@ typedef struct {
     float bg[4];         /* background RGBA composited behind the volume */
     int32_t lod_mode;    /* 0: all samples on level 0; 1: footprint LOD (Sec. V-C) */
     int32_t lod_bias;    /* added to the footprint level before clamping to [0, L-1] */
-    int32_t tile_w;      /* ray tile (work item) width in pixels; 0 = default 8 */
-    int32_t tile_h;      /* ray tile height (tile_w * tile_h <= 4096); 0 = 4 */
+    int32_t tile_w;      /* ray tile (work item) width in pixels; 0 = default 4 */
+    int32_t tile_h;      /* ray tile height (tile_w * tile_h <= 4096); 0 = 8 */
     int32_t max_passes;  /* miss/refill passes per render when a provider is set; 0 = 64 */
     uint32_t flags;      /* VOL_RENDER_* bits */
     int32_t refill;      /* a warp fetches new rays once fewer lanes than this are busy
-                            (1..32; 0 = default 30); performance only, never the image */
+                            (1..32; 0 = default 20); performance only, never the image */
     int32_t ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
 } vol_params;
 

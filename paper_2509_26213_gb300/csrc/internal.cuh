@@ -114,6 +114,7 @@ struct BackwardDev {
     const float* ckpt;
     long long nrays;
     const int* ray_n;
+    const int* tile_order;  // heaviest-first order of the tiles (NULL: tile i)
 };
 
 struct TraceDev {
@@ -134,7 +135,8 @@ cudaError_t launch_backward(int dtype, const BackwardDev& p, int grid, cudaStrea
 cudaError_t launch_trace(const TraceDev& p, cudaStream_t s);
 int render_blocks_per_sm(int dtype, bool grad);
 // order[] = tiles sorted by descending log2 bucket of cost[] (heaviest first); zeroes cost[].
-cudaError_t launch_tile_order(int* cost, int* order, int ntiles, cudaStream_t s);
+// buckets: 64 ints of device scratch.
+cudaError_t launch_tile_order(int* cost, int* order, int ntiles, int* buckets, cudaStream_t s);
 int backward_blocks_per_sm(int dtype);
 
 // ---- launchers (kernels_volume.cu) ----

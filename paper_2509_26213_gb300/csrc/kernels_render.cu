@@ -343,12 +343,16 @@ __device__ __forceinline__ void suspend_ray(const RenderDev& P, long long ray, i
 #define VOLRC_BATCH 4
 #endif
 constexpr int kBatch = VOLRC_BATCH;
+// Minimum resident CTAs per SM the register allocation must allow.
+#ifndef VOLRC_MIN_CTAS
+#define VOLRC_MIN_CTAS 6
+#endif
 
 __host__ __device__ constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
 
 // BS: brick edge known at compile time (32 or 64), or 0 for any power of two read at run time.
 template <int DT, bool LOD, bool GRAD, int BS, bool Q>
-__global__ void __launch_bounds__(kRenderThreads) k_render(const __grid_constant__ RenderDev P) {
+__global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const __grid_constant__ RenderDev P) {
     __shared__ float4 s_tf[256];
     __shared__ LevelDev s_lv[kMaxLevels];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = P.tf[i];
@@ -563,6 +567,35 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(const __grid_constant
 
 // ------------------------------------------------------------------ adjoint
 
+__device__ __forceinline__ void flush_dtf(float* s_dtf, int idx, float acc[8]) {
+    if (idx >= 0) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (acc[c] != 0.0f) atomicAdd(&s_dtf[4 * idx + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
+}
+
+__device__ __forceinline__ void flush_vox(float* dvox, long long cell, int mask, int Dx, int Dy, float cacc[8]) {
+    if (cell >= 0) {
+        const long long sy = Dx, sz = (long long)Dx * Dy;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+            const bool exists = (!cx || (mask & 1)) && (!cy || (mask & 2)) && (!cz || (mask & 4));
+            if (exists && cacc[c] != 0.0f) atomicAdd(&dvox[cell + cx + cy * sy + cz * sz], cacc[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cacc[c] = 0.0f;
+}
+
+// Adjoint, warp-synchronous by checkpoint segment: in each round every lane holding a ray
+// processes one segment of it (samples 32 s .. 32 s + 31, the last one partial), first
+// forward -- transmittance from the segment's checkpoint and the sample values into shared
+// memory -- then in reverse, accumulating dL/dtf and dL/dvoxel.  Lanes take a new ray between
+// rounds, so a warp waits only on segments, not on whole rays.
 template <int DT>
 __global__ void __launch_bounds__(kRenderThreads) k_backward(const __grid_constant__ BackwardDev P) {
     __shared__ float4 s_tf[256];
@@ -578,111 +611,174 @@ __global__ void __launch_bounds__(kRenderThreads) k_backward(const __grid_consta
     using VT = typename Voxel<DT>::T;
     const VT* __restrict__ atlas = (const VT*)P.vol.atlas;
     const unsigned lane = threadIdx.x & 31;
+    const unsigned ltmask = (1u << lane) - 1;
     const int tid = threadIdx.x;
     const int bshift = P.vol.bshift, bmask = P.vol.bmask, B1 = P.vol.B1;
     const unsigned long long slot_elems = P.vol.slot_elems;
     const int Dx = P.D0[0], Dy = P.D0[1];
     const float step = P.step;
     const bool quad = P.vol.quad != 0;
+    const int row = quad ? B1 - 1 : B1;
+    // per-lane accumulators: dL/dtf for entries acc_i, acc_i + 1; dL/dvoxel for the 8 corners
+    // of cell cell_cur (cell_mask: which +1 corners exist)
+    int acc_i = -1;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    long long cell_cur = -1;
+    int cell_mask = 0;
+    float cacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+
+    // warp-uniform tile pool
+    int pool_next = 0, pool_cnt = 0, pool_view = 0, pool_x0 = 0, pool_y0 = 0;
+    bool queue_done = false;
+    // lane state
+    bool has = false;
+    long long ray = 0;
+    float o0 = 0, o1 = 0, o2 = 0, d0 = 0, d1 = 0, d2 = 0, t0 = 0;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    float R0 = 0, R1 = 0, R2 = 0, R3 = 0;
+    int n = 0, s = 0;
 
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = (int)atomicAdd(&P.counters[kWork], 1u);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= P.nwork) break;
-        const int v = find_view_tile(P.views, P.nviews, item);
-        const ViewDev& V = P.views[v];
-        const int tl = item - V.tile_off;
-        const int x0 = (tl % V.tiles_x) * P.tile_w, y0 = (tl / V.tiles_x) * P.tile_h;
-        for (int idx = lane; idx < P.tile_w * P.tile_h; idx += 32) {
-            const int px = x0 + idx % P.tile_w, py = y0 + idx / P.tile_w;
-            if (px >= V.w || py >= V.h) continue;
-            const long long ray = V.ray_off + (long long)py * V.w + px;
-            const int n = P.ray_n[ray];
-            if (n <= 0) continue;
-            Ray R;
-            make_ray(V, P.vol.D0f, px, py, R);
-            const float4 g = P.drgba[ray];
-            float R0 = P.bg.x, R1 = P.bg.y, R2 = P.bg.z, R3 = P.bg.w;
-            const int nseg = (n + kCkptEvery - 1) / kCkptEvery;
-            for (int s = nseg - 1; s >= 0; --s) {
-                const int k0 = s * kCkptEvery, k1 = min(n, k0 + kCkptEvery);
-                float T = s == 0 ? 1.0f : P.ckpt[(long long)(s - 1) * P.nrays + ray];
-                // forward over the segment: transmittance before each sample, and its value
-                for (int k = k0; k < k1; ++k) {
-                    const float t = __fadd_rn(R.t0, __fmul_rn((float)k, step));
-                    const float p[3] = {__fadd_rn(R.o[0], __fmul_rn(t, R.d[0])), __fadd_rn(R.o[1], __fmul_rn(t, R.d[1])),
-                                        __fadd_rn(R.o[2], __fmul_rn(t, R.d[2]))};
-                    Resolved Q;
-                    resolve(s_l0, bshift, bmask, quad ? B1 - 1 : B1, p, Q);
-                    const uint32_t slot = __ldg(P.vol.pt + Q.pti);
-                    float val = 0.0f;
-                    if (slot != kInvalidSlot) {
-                        val = quad ? trilinear_quad<DT>(P.vol.atlas, (unsigned long long)slot * P.vol.slot_entries + Q.local,
-                                                        B1 - 1, Q.w)
-                                   : trilinear<DT>(atlas, (unsigned long long)slot * slot_elems + Q.local, B1, Q.w);
-                    } else {
-                        atomicAdd(&P.counters[kDevError], 1u);
-                    }
-                    const float x = tf_coord<DT>(val);
-                    const int i = min((int)x, 254);
-                    const float wt = x - (float)i;
-                    const float al = fmaf(wt, s_tf[i + 1].w - s_tf[i].w, s_tf[i].w);
-                    s_T[k - k0][tid] = T;
-                    s_V[k - k0][tid] = val;
-                    T = T * (1.0f - al);
+        // ---- give lanes without a ray the next rays of the tile queue
+        while (!queue_done) {
+            const unsigned need = __ballot_sync(kFull, !has);
+            if (!need) break;
+            if (pool_next >= pool_cnt) {
+                int item = 0;
+                if (lane == 0) item = (int)atomicAdd(&P.counters[kWork], 1u);
+                item = __shfl_sync(kFull, item, 0);
+                if (item >= P.nwork) {
+                    queue_done = true;
+                    break;
                 }
-                // reverse over the segment
-                for (int k = k1 - 1; k >= k0; --k) {
-                    const float t = __fadd_rn(R.t0, __fmul_rn((float)k, step));
-                    const float p[3] = {__fadd_rn(R.o[0], __fmul_rn(t, R.d[0])), __fadd_rn(R.o[1], __fmul_rn(t, R.d[1])),
-                                        __fadd_rn(R.o[2], __fmul_rn(t, R.d[2]))};
-                    Resolved Q;
-                    resolve(s_l0, bshift, bmask, quad ? B1 - 1 : B1, p, Q);
-                    const float val = s_V[k - k0][tid];
-                    const float Tk = s_T[k - k0][tid];
-                    const float x = tf_coord<DT>(val);
-                    const int i = min((int)x, 254);
-                    const float wt = x - (float)i;
-                    const float4 a = s_tf[i], b = s_tf[i + 1];
-                    const float cr = fmaf(wt, b.x - a.x, a.x), cg = fmaf(wt, b.y - a.y, a.y);
-                    const float cb = fmaf(wt, b.z - a.z, a.z), al = fmaf(wt, b.w - a.w, a.w);
-                    const float dal = Tk * (g.x * (cr - R0) + g.y * (cg - R1) + g.z * (cb - R2) + g.w * (1.0f - R3));
-                    const float Ta = Tk * al;
-                    const float dr = g.x * Ta, dg = g.y * Ta, db = g.z * Ta;
-                    if (P.dtf) {
-                        const float w0 = 1.0f - wt;
-                        atomicAdd(&s_dtf[4 * i + 0], w0 * dr);
-                        atomicAdd(&s_dtf[4 * i + 1], w0 * dg);
-                        atomicAdd(&s_dtf[4 * i + 2], w0 * db);
-                        atomicAdd(&s_dtf[4 * i + 3], w0 * dal);
-                        atomicAdd(&s_dtf[4 * i + 4], wt * dr);
-                        atomicAdd(&s_dtf[4 * i + 5], wt * dg);
-                        atomicAdd(&s_dtf[4 * i + 6], wt * db);
-                        atomicAdd(&s_dtf[4 * i + 7], wt * dal);
+                const int tile = P.tile_order ? P.tile_order[item] : item;
+                const int v = find_view_tile(P.views, P.nviews, tile);
+                const int tl = tile - P.views[v].tile_off;
+                pool_view = v;
+                pool_x0 = (tl % P.views[v].tiles_x) * P.tile_w;
+                pool_y0 = (tl / P.views[v].tiles_x) * P.tile_h;
+                pool_cnt = P.tile_w * P.tile_h;
+                pool_next = 0;
+            }
+            const int idx = pool_next + __popc(need & ltmask);
+            pool_next = min(pool_cnt, pool_next + __popc(need));
+            if (!has && idx < pool_cnt) {
+                const ViewDev& V = P.views[pool_view];
+                const int px = pool_x0 + idx % P.tile_w, py = pool_y0 + idx / P.tile_w;
+                if (px < V.w && py < V.h) {
+                    ray = V.ray_off + (long long)py * V.w + px;
+                    n = P.ray_n[ray];
+                    if (n > 0) {
+                        Ray R;
+                        make_ray(V, P.vol.D0f, px, py, R);
+                        o0 = R.o[0]; o1 = R.o[1]; o2 = R.o[2];
+                        d0 = R.d[0]; d1 = R.d[1]; d2 = R.d[2];
+                        t0 = R.t0;
+                        g = P.drgba[ray];
+                        R0 = P.bg.x; R1 = P.bg.y; R2 = P.bg.z; R3 = P.bg.w;
+                        s = (n - 1) / kCkptEvery;
+                        has = true;
                     }
-                    if (P.dvox && tf_inside<DT>(val)) {
-                        const float dv = 255.0f * (dr * (b.x - a.x) + dg * (b.y - a.y) + db * (b.z - a.z) + dal * (b.w - a.w));
-                        if (dv != 0.0f) {
-                            const long long b0 = (long long)Q.i0[0] + (long long)Dx * ((long long)Q.i0[1] + (long long)Dy * Q.i0[2]);
-                            const long long sy = Dx, sz = (long long)Dx * Dy;
-                            const float wx = Q.w[0], wy = Q.w[1], wz = Q.w[2];
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
-                                const float wgt = (cx ? wx : 1.0f - wx) * (cy ? wy : 1.0f - wy) * (cz ? wz : 1.0f - wz);
-                                if (wgt != 0.0f) atomicAdd(&P.dvox[b0 + cx + cy * sy + cz * sz], wgt * dv);
-                            }
-                        }
-                    }
-                    R0 = fmaf(al, cr - R0, R0);
-                    R1 = fmaf(al, cg - R1, R1);
-                    R2 = fmaf(al, cb - R2, R2);
-                    R3 = fmaf(al, 1.0f - R3, R3);
                 }
             }
         }
+        if (!__ballot_sync(kFull, has)) break;
+
+        // ---- one round: segment s of every lane's ray
+        const int k0 = s * kCkptEvery;
+        const int len = has ? min(kCkptEvery, n - k0) : 0;
+        float T = (has && s > 0) ? P.ckpt[(long long)(s - 1) * P.nrays + ray] : 1.0f;
+        const int maxlen = __reduce_max_sync(kFull, len);
+        for (int j = 0; j < maxlen; ++j) {
+            if (j < len) {
+                const int k = k0 + j;
+                const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
+                const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
+                                    __fadd_rn(o2, __fmul_rn(t, d2))};
+                Resolved Q;
+                resolve(s_l0, bshift, bmask, row, p, Q);
+                const uint32_t slot = __ldg(P.vol.pt + Q.pti);
+                float val = 0.0f;
+                if (slot != kInvalidSlot) {
+                    val = quad ? trilinear_quad<DT>(P.vol.atlas, (unsigned long long)slot * P.vol.slot_entries + Q.local,
+                                                    B1 - 1, Q.w)
+                               : trilinear<DT>(atlas, (unsigned long long)slot * slot_elems + Q.local, B1, Q.w);
+                } else {
+                    atomicAdd(&P.counters[kDevError], 1u);
+                }
+                const float x = tf_coord<DT>(val);
+                const int i = min((int)x, 254);
+                const float wt = x - (float)i;
+                const float al = fmaf(wt, s_tf[i + 1].w - s_tf[i].w, s_tf[i].w);
+                s_T[j][tid] = T;
+                s_V[j][tid] = val;
+                T = T * (1.0f - al);
+            }
+        }
+        for (int j = maxlen - 1; j >= 0; --j) {
+            if (j < len) {
+                const int k = k0 + j;
+                const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
+                const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
+                                    __fadd_rn(o2, __fmul_rn(t, d2))};
+                Resolved Q;
+                resolve(s_l0, bshift, bmask, row, p, Q);
+                const float val = s_V[j][tid];
+                const float Tk = s_T[j][tid];
+                const float x = tf_coord<DT>(val);
+                const int i = min((int)x, 254);
+                const float wt = x - (float)i;
+                const float4 a = s_tf[i], b = s_tf[i + 1];
+                const float cr = fmaf(wt, b.x - a.x, a.x), cg = fmaf(wt, b.y - a.y, a.y);
+                const float cb = fmaf(wt, b.z - a.z, a.z), al = fmaf(wt, b.w - a.w, a.w);
+                const float dal = Tk * (g.x * (cr - R0) + g.y * (cg - R1) + g.z * (cb - R2) + g.w * (1.0f - R3));
+                const float Ta = Tk * al;
+                const float dr = g.x * Ta, dg = g.y * Ta, db = g.z * Ta;
+                if (P.dtf) {
+                    // register accumulation while the TF index stays the same
+                    if (i != acc_i) {
+                        flush_dtf(s_dtf, acc_i, acc);
+                        acc_i = i;
+                    }
+                    const float w0 = 1.0f - wt;
+                    acc[0] = fmaf(w0, dr, acc[0]);
+                    acc[1] = fmaf(w0, dg, acc[1]);
+                    acc[2] = fmaf(w0, db, acc[2]);
+                    acc[3] = fmaf(w0, dal, acc[3]);
+                    acc[4] = fmaf(wt, dr, acc[4]);
+                    acc[5] = fmaf(wt, dg, acc[5]);
+                    acc[6] = fmaf(wt, db, acc[6]);
+                    acc[7] = fmaf(wt, dal, acc[7]);
+                }
+                if (P.dvox && tf_inside<DT>(val)) {
+                    const float dv = 255.0f * (dr * (b.x - a.x) + dg * (b.y - a.y) + db * (b.z - a.z) + dal * (b.w - a.w));
+                    if (dv != 0.0f) {
+                        // register accumulation while the trilinear cell stays the same
+                        const long long cell = (long long)Q.i0[0] + (long long)Dx * ((long long)Q.i0[1] + (long long)Dy * Q.i0[2]);
+                        if (cell != cell_cur) {
+                            flush_vox(P.dvox, cell_cur, cell_mask, Dx, Dy, cacc);
+                            cell_cur = cell;
+                            cell_mask = (Q.i0[0] < Dx - 1 ? 1 : 0) | (Q.i0[1] < Dy - 1 ? 2 : 0) | (Q.i0[2] < P.D0[2] - 1 ? 4 : 0);
+                        }
+                        const float wx = Q.w[0], wy = Q.w[1], wz = Q.w[2];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+                            const float wgt = (cx ? wx : 1.0f - wx) * (cy ? wy : 1.0f - wy) * (cz ? wz : 1.0f - wz);
+                            cacc[c] = fmaf(wgt, dv, cacc[c]);
+                        }
+                    }
+                }
+                R0 = fmaf(al, cr - R0, R0);
+                R1 = fmaf(al, cg - R1, R1);
+                R2 = fmaf(al, cb - R2, R2);
+                R3 = fmaf(al, 1.0f - R3, R3);
+            }
+        }
+        if (has && --s < 0) has = false;
     }
+    if (P.dtf) flush_dtf(s_dtf, acc_i, acc);
+    if (P.dvox) flush_vox(P.dvox, cell_cur, cell_mask, Dx, Dy, cacc);
     __syncthreads();
     if (P.dtf)
         for (int i = threadIdx.x; i < 1024; i += blockDim.x)
@@ -693,28 +789,39 @@ __global__ void __launch_bounds__(kRenderThreads) k_backward(const __grid_consta
 
 // Heaviest-first work order for the next frame (an approximate longest-processing-time-first
 // schedule): tiles bucketed by floor(log2(cost + 1)), buckets in descending order.  One CTA.
-constexpr int kOrderThreads = 1024;
-__global__ void __launch_bounds__(kOrderThreads) k_tile_order(int* cost, int* order, int ntiles) {
+constexpr int kOrderThreads = 256;
+
+__device__ __forceinline__ int cost_bucket(int c) { return 31 - __clz(c + 1); }
+
+// buckets[0..31]: tiles per bucket; one thread per tile, one global atomic per bucket per block
+__global__ void __launch_bounds__(kOrderThreads) k_order_count(const int* cost, int ntiles, int* buckets) {
     __shared__ int s_count[32];
-    __shared__ int s_off[32];
     if (threadIdx.x < 32) s_count[threadIdx.x] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
-        const int b = 31 - __clz(cost[i] + 1);
-        atomicAdd(&s_count[b], 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ntiles) atomicAdd(&s_count[cost_bucket(cost[i])], 1);
+    __syncthreads();
+    if (threadIdx.x < 32 && s_count[threadIdx.x]) atomicAdd(&buckets[threadIdx.x], s_count[threadIdx.x]);
+}
+
+// order[] = tiles grouped by bucket, heaviest bucket first; each block reserves its places in
+// every bucket with one atomic on the bucket's fill cursor (buckets[32 + b]).  Zeroes cost[].
+__global__ void __launch_bounds__(kOrderThreads) k_order_scatter(int* cost, int* order, int ntiles, int* buckets) {
+    __shared__ int s_count[32], s_base[32];
+    if (threadIdx.x < 32) s_count[threadIdx.x] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = i < ntiles ? cost_bucket(cost[i]) : 0;
+    const int rank = i < ntiles ? atomicAdd(&s_count[b], 1) : 0;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int base = 0;
+        for (int q = 31; q > (int)threadIdx.x; --q) base += buckets[q];
+        s_base[threadIdx.x] = s_count[threadIdx.x] ? base + atomicAdd(&buckets[32 + threadIdx.x], s_count[threadIdx.x]) : 0;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int b = 31; b >= 0; --b) {
-            s_off[b] = acc;
-            acc += s_count[b];
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
-        const int b = 31 - __clz(cost[i] + 1);
-        order[atomicAdd(&s_off[b], 1)] = i;
+    if (i < ntiles) {
+        order[s_base[b] + rank] = i;
         cost[i] = 0;
     }
 }
@@ -807,9 +914,13 @@ cudaError_t launch_backward(int dtype, const BackwardDev& p, int grid, cudaStrea
     return cudaLaunchKernel(fn, dim3(grid), dim3(kRenderThreads), args, 0, s);
 }
 
-cudaError_t launch_tile_order(int* cost, int* order, int ntiles, cudaStream_t s) {
+cudaError_t launch_tile_order(int* cost, int* order, int ntiles, int* buckets, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    k_tile_order<<<1, kOrderThreads, 0, s>>>(cost, order, ntiles);
+    cudaError_t e = cudaMemsetAsync(buckets, 0, sizeof(int) * 64, s);
+    if (e != cudaSuccess) return e;
+    const int grid = (ntiles + kOrderThreads - 1) / kOrderThreads;
+    k_order_count<<<grid, kOrderThreads, 0, s>>>(cost, ntiles, buckets);
+    k_order_scatter<<<grid, kOrderThreads, 0, s>>>(cost, order, ntiles, buckets);
     return cudaGetLastError();
 }
 

@@ -153,8 +153,9 @@ struct vol_s {
     size_t tile_cost_cap = 0;
     int* tile_order = nullptr;
     size_t tile_order_cap = 0;
-    std::vector<unsigned char> order_key;  // view table + tile shape the order was built for
+    std::vector<unsigned char> order_key;  // tile partition the order was built for
     bool order_ready = false;
+    int* order_buckets = nullptr;          // 64 ints: bucket counts and fill cursors
 
     vol_stats stats{};
     int occ_cache[4][2] = {{0}};
@@ -530,6 +531,7 @@ int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->last_used, sizeof(unsigned) * (size_t)lay.nslots);
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->counters, sizeof(unsigned) * kNumCounters);
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->aux, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v->order_buckets, sizeof(int) * 64);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * (size_t)lay.total_bricks, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->last_used, 0, sizeof(unsigned) * (size_t)lay.nslots, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->aux, 0, sizeof(unsigned) * 4, v->stream);
@@ -556,7 +558,7 @@ void vol_destroy(vol_t v) {
     else cudaDeviceSynchronize();
     void* bufs[] = {v->atlas, v->pt, v->last_used, v->counters, v->aux, v->upd_dev, v->views_dev, v->req_table,
                     v->req_list, v->susp[0], v->susp[1], v->ckpt, v->ray_n, v->stage_dev, v->stage_slots_dev,
-                    v->tile_cost, v->tile_order};
+                    v->tile_cost, v->tile_order, v->order_buckets};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (v->stage_host) cudaFreeHost(v->stage_host);
@@ -751,11 +753,11 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     if (nviews < 1 || nviews > VOL_MAX_VIEWS) return fail(v, VOL_ERR_INVALID_ARG, "nviews out of range");
     vol_params p = *params;
     if (!(p.step > 0.0f) || !std::isfinite(p.step)) return fail(v, VOL_ERR_INVALID_ARG, "step must be > 0");
-    if (p.tile_w <= 0) p.tile_w = 8;
-    if (p.tile_h <= 0) p.tile_h = 4;
+    if (p.tile_w <= 0) p.tile_w = 4;
+    if (p.tile_h <= 0) p.tile_h = 8;
     if (p.tile_w > 4096 || p.tile_h > 4096 || p.tile_w * p.tile_h > 4096)
         return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be at most 4096");
-    if (p.refill <= 0 || p.refill > 32) p.refill = 30;
+    if (p.refill <= 0 || p.refill > 32) p.refill = 20;
     if (p.lod_mode != 0 && p.lod_mode != 1) return fail(v, VOL_ERR_INVALID_ARG, "lod_mode must be 0 or 1");
     const bool grad = (p.flags & VOL_RENDER_GRAD) != 0;
     if (grad && p.lod_mode != 0) return fail(v, VOL_ERR_UNSUPPORTED, "gradients need lod_mode 0");
@@ -846,7 +848,7 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     int rc = may_miss ? miss_loop(v, false) : VOL_OK;
     if (rc == VOL_OK) v->have_forward = true;
     if (rc == VOL_OK || rc == VOL_ERR_INCOMPLETE) {
-        CK(v, launch_tile_order(v->tile_cost, v->tile_order, (int)tiles, v->stream));
+        CK(v, launch_tile_order(v->tile_cost, v->tile_order, (int)tiles, v->order_buckets, v->stream));
         v->order_ready = true;
     }
     return rc;
@@ -903,6 +905,8 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
     b.ckpt = v->ckpt;
     b.nrays = v->nrays;
     b.ray_n = v->ray_n;
+    // the order built from this forward's per-tile sample counts: the heaviest tiles first
+    b.tile_order = v->order_ready ? v->tile_order : nullptr;
     CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
     const int grid = backward_blocks_per_sm(v->dtype) * v->nsm;
     CK(v, launch_backward(v->dtype, b, grid, v->stream));
@@ -1014,11 +1018,11 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
         return fail(v, VOL_ERR_INVALID_ARG, "nviews must be 1..VOL_NOALLOC_MAX_VIEWS (64) for vol_render_noalloc");
     vol_params p = *params;
     if (!(p.step > 0.0f) || !std::isfinite(p.step)) return fail(v, VOL_ERR_INVALID_ARG, "step must be > 0");
-    if (p.tile_w <= 0) p.tile_w = 8;
-    if (p.tile_h <= 0) p.tile_h = 4;
+    if (p.tile_w <= 0) p.tile_w = 4;
+    if (p.tile_h <= 0) p.tile_h = 8;
     if (p.tile_w > 4096 || p.tile_h > 4096 || p.tile_w * p.tile_h > 4096)
         return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be at most 4096");
-    if (p.refill <= 0 || p.refill > 32) p.refill = 30;
+    if (p.refill <= 0 || p.refill > 32) p.refill = 20;
     if (p.lod_mode != 0 && p.lod_mode != 1) return fail(v, VOL_ERR_INVALID_ARG, "lod_mode must be 0 or 1");
     if (p.flags & VOL_RENDER_GRAD)
         return fail(v, VOL_ERR_UNSUPPORTED, "vol_render_noalloc keeps no gradient state; use vol_render");

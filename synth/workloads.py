@@ -81,3 +81,18 @@ def c5(seed: int = 5) -> dict:
         "noise": {"octaves": 5, "period0": 512.0, "nspheres": 1000, "radius": (8.0, 120.0), "value": (0.3, 1.0)},
         "name": "out-of-core 4096^3 procedural, 64^3 bricks, 7 levels, 16 GiB cache, 30-frame fly-through",
     }
+
+
+def c2s(seed: int = 2) -> dict:
+    """c2 at 512^3 (same generator scaled by 1/2, same image and TF): the case profiled in detail,
+    a few GB on the device at most."""
+    D = (512, 512, 512)
+    return {
+        "key": "c2s", "D": D, "brick": 64, "levels": 4, "src": "u16", "store": "u16",
+        "make": lambda: noise_spheres(D, seed, octaves=5, period0=64.0, nspheres=200, radius=(2.0, 30.0),
+                                      value=(0.3, 1.0)),
+        "cams": [seeded_orbit(D, 1920, 1080, seed)],
+        "tf": tf_peaks(seed),
+        "params": {"step": 0.5, "et": 0.99, "lod_mode": 1, "lod_bias": 0},
+        "name": "reduced-precision single view, 512^3 u16 noise+spheres, 64^3 bricks, 4 levels, 1920x1080",
+    }
