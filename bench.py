@@ -284,7 +284,17 @@ def run_ours(args, dist, rank, ws, local):
     store = wl["store"]
     bpv = bytes_per_voxel(store)
 
-    vol = build_volume(P, wl, store, raw)
+    tuned = None
+    if args.workload == "c3" or args.autotune:
+        # ray-tile shape, refill threshold and brick size chosen by the autotuner (untimed)
+        from paper_2509_26213_gb300.tune import autotune
+        cache = os.environ.get("VOLRC_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "volrc_autotune.json"))
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        tuned = autotune(lambda b: build_volume(P, dict(wl, brick=b), store, raw), cams, tf, params,
+                         key=f"{wl['key']}|{wl['name']}", cache_path=cache)
+        wl["brick"] = tuned["brick"]
+        params.update(tile_w=tuned["tile_w"], tile_h=tuned["tile_h"], refill=tuned["refill"])
+    vol = (tuned or {}).pop("volume", None) or build_volume(P, wl, store, raw)
     out, ns = vol.render(cams, tf, params, nsamples=True)
     torch.cuda.synchronize()
     samples = int(ns.sum().item())
@@ -386,7 +396,9 @@ def run_ours(args, dist, rank, ws, local):
                        "step": params["step"], "et": params["et"], "samples_per_frame": samples,
                        "bricks_touched": touched,
                        "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"replicas x{ws}",
+                       "tile": [params.get("tile_w", 0), params.get("tile_h", 0)], "refill": params.get("refill", 0),
+                       "autotuned": None if tuned is None else {k: tuned[k] for k in ("brick", "tile_w", "tile_h", "refill", "ms", "cached")}},
             "ms_per_frame": t_mean,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -402,21 +414,82 @@ def run_ours(args, dist, rank, ws, local):
     vol.close()
 
 
+def run_outofcore(args, dist, rank, ws, local):
+    """Out-of-core fly-through: 4096^3 u8 volume whose bricks (every level) are generated on
+    demand on the host cores into pinned memory, 64^3 bricks, 7 levels, a 16 GiB brick cache with
+    LRU eviction, 30 frames at 1920x1080.  Steady state = frames 10-29.  Frame times are wall
+    times of the render call: it waits for the request/load/resume passes."""
+    import torch
+    import paper_2509_26213_gb300 as pkg
+    pkg.build()
+    import paper_2509_26213_gb300.volume as P
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workloads.c5()
+    g = wl["noise"]
+    vol = P.Volume(wl["D"], "u8", wl["brick"], wl["levels"], cache_bytes=wl["cache_bytes"], layout="compact")
+    src = synth.brick_source(wl["D"], wl["brick"], wl["levels"], 5, dtype="u8", **g)
+    vol.set_provider_batch(synth.brick_provider_address(), src, "u8")
+    tf = torch.from_numpy(wl["tf"]).to(dev)
+    params = dict(wl["params"], max_passes=100000)
+    cams = wl["cams"]
+    if ws > 1:
+        cams = cams[rank::ws] * ws
+    frames = []
+    barrier(dist)
+    with Clocks(local) as clk:
+        for i, cam in enumerate(cams):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            out, ns = vol.render(cam, tf, params, nsamples=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            st = vol.stats()
+            frames.append({"ms": 1e3 * dt, "samples": int(ns.sum().item()), "passes": st["passes"],
+                           "bricks_loaded": st["bricks_loaded"], "bytes_loaded": st["bytes_loaded"],
+                           "evicted": st["evicted"], "resident": st["resident"], "touched": st["touched"]})
+    clocks = clk.summary()
+    steady = frames[10:] if len(frames) > 10 else frames
+    ms = statistics.mean(f["ms"] for f in steady)
+    samples = statistics.mean(f["samples"] for f in steady)
+    t_step = max_over_ranks(dist, ms)
+    value = sum_over_ranks(dist, samples) / (t_step * 1e-3)
+    if rank == 0:
+        line = {
+            "metric": "ray samples/s", "value": value, "unit": "samples/s", "n_gpus": ws, "steps": len(steady),
+            "warmup": len(frames) - len(steady), "ms_per_step": t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "store": "u8", "brick": wl["brick"], "levels": wl["levels"],
+                       "layout": "compact", "cache_bytes": wl["cache_bytes"], "provider": "host cores, pinned memory",
+                       "parallelism": f"replicas x{ws}"},
+            "steady_state": {"ms_per_frame": ms,
+                             "miss_bytes_per_frame": statistics.mean(f["bytes_loaded"] for f in steady),
+                             "bricks_loaded_per_frame": statistics.mean(f["bricks_loaded"] for f in steady),
+                             "passes_per_frame": statistics.mean(f["passes"] for f in steady)},
+            "frames": frames,
+            "clocks": clocks,
+            "gpu_launches": None,
+        }
+        print(json.dumps(line), flush=True)
+    vol.close()
+
+
 def cpu_baseline(wl, raw, seconds):
-    """The oracle as it stands on the host cores: whole frames (every view) repeated until `seconds`."""
+    """The oracle as it stands on the host cores: seeded 1/64 samples of every view's pixels
+    (a new sample each round) until `seconds` have passed."""
     import oracle
     ovol = oracle_volume(wl, raw)
-    samples, frames = 0, 0
+    samples, rounds = 0, 0
     t = time.perf_counter()
     while True:
-        for v, cam in enumerate(wl["cams"]):
-            samples += int(oracle.render(ovol, cam, wl["tf"], wl["params"])["n"].sum())
-        frames += 1
+        samples += oracle_samples(ovol, wl, frame_pixels(wl, 1.0 / 64, 7000 + rounds))
+        rounds += 1
         dt = time.perf_counter() - t
         if dt >= seconds:
             break
     return {"value": samples / dt, "unit": "samples/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{frames} whole frame(s) of the workload, {samples} samples in {dt:.1f} s"}
+            "sample": f"{rounds} x (1/64 of every view's pixels, seeded), {samples} samples in {dt:.1f} s"}
 
 
 def main():
@@ -427,7 +500,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="primary line only (no storage variants, no fwd+bwd)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s", "c3", "c4"])
+    ap.add_argument("--autotune", action="store_true", help="autotune tile, refill and brick size first")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s", "c3", "c4", "c5"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-frac", type=float, default=0.25, help="reference arm: fraction of pixels per step")
     args = ap.parse_args()
@@ -437,7 +511,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, dist, rank, ws)
     else:
-        run_ours(args, dist, rank, ws, local)
+        if args.workload == "c5":
+            run_outofcore(args, dist, rank, ws, local)
+        else:
+            run_ours(args, dist, rank, ws, local)
     if dist:
         dist.destroy_process_group()
 

@@ -138,6 +138,12 @@ typedef struct {
  * Returns 0 on success. Called from the host thread that called vol_render(). */
 typedef int (*vol_provider_fn)(void *user, int level, const int32_t brick[3], void *dst);
 
+/* Batch form of the provider: fills n bricks in one call (so the source can work on them in
+ * parallel).  reqs: host int32 [n][4] = level, bx, by, bz; dst: host memory owned by the
+ * library (pinned), n consecutive (B+1)^3 regions of src_dtype in request order, each with
+ * the voxel contract of vol_provider_fn.  Returns 0 on success. */
+typedef int (*vol_provider_batch_fn)(void *user, int n, const int32_t *reqs, void *dst);
+
 /* Debug record of one sample's decisions (vol_trace). */
 typedef struct {
     int32_t k;          /* sample index */
@@ -215,6 +221,10 @@ int vol_evict_all(vol_t v);
 /* Installs (or with fn = NULL removes) the provider used by vol_render() to
  * load missing bricks; src_dtype is the type the provider writes. */
 int vol_set_provider(vol_t v, vol_provider_fn fn, void *user, int src_dtype);
+
+/* Installs (or with fn = NULL removes) a batch provider; it takes precedence over the
+ * per-brick provider.  Bricks are requested in batches of up to 64 MiB of source voxels. */
+int vol_set_provider_batch(vol_t v, vol_provider_batch_fn fn, void *user, int src_dtype);
 
 /* ---- rendering ----------------------------------------------------------- */
 

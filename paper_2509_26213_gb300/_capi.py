@@ -34,7 +34,7 @@ LAYOUTS = {"quad": 0, "compact": VOL_LAYOUT_COMPACT}
 EXPORTS = ["vol_plan", "vol_create", "vol_destroy", "vol_last_error", "vol_set_stream", "vol_get_layout",
            "vol_get_stats", "vol_upload_level", "vol_upload_brick", "vol_build_lod", "vol_download_brick",
            "vol_evict_all", "vol_set_provider", "vol_render", "vol_render_resume", "vol_poll_requests",
-           "vol_render_backward", "vol_trace", "vol_render_noalloc"]
+           "vol_render_backward", "vol_trace", "vol_render_noalloc", "vol_set_provider_batch"]
 VOL_NOALLOC_SCRATCH_BYTES = 8192
 VOL_NOALLOC_MAX_VIEWS = 64
 
@@ -111,6 +111,7 @@ def load() -> ctypes.CDLL:
         "vol_trace": (i32, [vp, ctypes.POINTER(vol_camera), ctypes.POINTER(vol_params), i32p, i32, i32,
                             ctypes.POINTER(vol_trace_rec), i32p]),
         "vol_render_noalloc": (i32, [vp, ctypes.POINTER(vol_camera), i32, vp, ctypes.POINTER(vol_params), vp, vp]),
+        "vol_set_provider_batch": (i32, [vp, vp, vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

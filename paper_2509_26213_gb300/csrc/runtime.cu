@@ -141,6 +141,7 @@ struct vol_s {
 
     // provider
     vol_provider_fn prov = nullptr;
+    vol_provider_batch_fn prov_batch = nullptr;
     void* prov_user = nullptr;
     int prov_dtype = 0;
     void* stage_host = nullptr;
@@ -436,44 +437,53 @@ int load_requests(vol_t v) {
     ++v->op_epoch;
     const std::vector<uint32_t> reqs = v->last_requests;
     std::vector<uint32_t> slots;
+    std::vector<int32_t> batch;  // [n][4] level, bx, by, bz of the bricks to load
     const int64_t loaded0 = v->stats.bricks_loaded;
     bool full = false;
-    for (size_t i0 = 0; i0 < reqs.size() && !full; i0 += v->stage_bricks) {
-        size_t n = std::min<size_t>(v->stage_bricks, reqs.size() - i0);
-        slots.assign(n, kInvalidSlot);
-        for (size_t j = 0; j < n; ++j) {
-            const uint32_t pti = reqs[i0 + j] - 1u;
+    size_t next = 0;
+    while (next < reqs.size() && !full) {
+        // collect up to stage_bricks bricks that need a slot
+        slots.clear();
+        batch.clear();
+        while (next < reqs.size() && slots.size() < (size_t)v->stage_bricks) {
+            const uint32_t pti = reqs[next] - 1u;
             if (pti >= v->pt_host.size()) return fail(v, VOL_ERR_DEVICE, "corrupt brick request");
             if (v->pt_host[pti] != kInvalidSlot) {  // already resident (e.g. a duplicate)
                 v->protect[v->pt_host[pti]] = v->op_epoch;
+                ++next;
                 continue;
             }
-            const int l = level_of_pti(v, pti);
-            const int64_t id = (int64_t)pti - v->lay.level_pt_offset[l];
-            const int64_t nbx = v->lay.level_bricks[l][0], nby = v->lay.level_bricks[l][1];
-            const int32_t b[3] = {(int32_t)(id % nbx), (int32_t)((id / nbx) % nby), (int32_t)(id / (nbx * nby))};
-            if (v->prov(v->prov_user, l, b, (char*)v->stage_host + j * src_bytes) != 0)
-                return fail(v, VOL_ERR_PROVIDER, "brick provider failed");
             uint32_t s;
             if (int rc = slot_for(v, pti, &s)) {
                 // the cache cannot take more bricks in this pass: load what fits, the rest is
                 // requested again by the rays that still wait for it
-                if (rc == VOL_ERR_CACHE_FULL && (v->stats.bricks_loaded > loaded0 || j > 0)) {
+                if (rc == VOL_ERR_CACHE_FULL && (v->stats.bricks_loaded > loaded0 || !slots.empty())) {
                     full = true;
                     break;
                 }
                 return rc;
             }
-            slots[j] = s;
-            v->stats.bricks_loaded++;
-            v->stats.bytes_loaded += (int64_t)src_bytes;
+            ++next;
+            const int l = level_of_pti(v, pti);
+            const int64_t id = (int64_t)pti - v->lay.level_pt_offset[l];
+            const int64_t nbx = v->lay.level_bricks[l][0], nby = v->lay.level_bricks[l][1];
+            slots.push_back(s);
+            batch.insert(batch.end(), {(int32_t)l, (int32_t)(id % nbx), (int32_t)((id / nbx) % nby),
+                                       (int32_t)(id / (nbx * nby))});
         }
-        if (full) {
-            size_t used = 0;
+        const size_t n = slots.size();
+        if (!n) break;
+        // fill the pinned stage from the source
+        if (v->prov_batch) {
+            if (v->prov_batch(v->prov_user, (int)n, batch.data(), v->stage_host) != 0)
+                return fail(v, VOL_ERR_PROVIDER, "brick provider failed");
+        } else {
             for (size_t j = 0; j < n; ++j)
-                if (slots[j] != kInvalidSlot) used = j + 1;
-            n = used;
+                if (v->prov(v->prov_user, batch[4 * j], &batch[4 * j + 1], (char*)v->stage_host + j * src_bytes) != 0)
+                    return fail(v, VOL_ERR_PROVIDER, "brick provider failed");
         }
+        v->stats.bricks_loaded += (int64_t)n;
+        v->stats.bytes_loaded += (int64_t)(n * src_bytes);
         CK(v, cudaMemcpyAsync(v->stage_dev, v->stage_host, src_bytes * n, cudaMemcpyHostToDevice, v->stream));
         CK(v, cudaMemcpyAsync(v->stage_slots_dev, slots.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, v->stream));
         CK(v, launch_upload_bricks(v->dtype, v->prov_dtype, v->stage_dev, vol_dev(v), v->stage_slots_dev, (long long)n,
@@ -489,7 +499,8 @@ int miss_loop(vol_t v, bool first_resumed) {
     if (int rc = collect_pass(v, first_resumed)) return rc;
     const int max_passes = v->params.max_passes > 0 ? v->params.max_passes : 64;
     while (v->nsusp > 0) {
-        if (!v->prov) return fail(v, VOL_ERR_INCOMPLETE, "rays wait for non-resident bricks (no provider)");
+        if (!v->prov && !v->prov_batch)
+            return fail(v, VOL_ERR_INCOMPLETE, "rays wait for non-resident bricks (no provider)");
         if (v->stats.passes >= max_passes) return fail(v, VOL_ERR_INCOMPLETE, "max_passes reached");
         if (int rc = load_requests(v)) return rc;
         if (int rc = run_pass(v, true, true)) return rc;
@@ -741,6 +752,17 @@ int vol_set_provider(vol_t v, vol_provider_fn fn, void* user, int src_dtype) {
     if (!v) return VOL_ERR_INVALID_ARG;
     if (fn && !conversion_ok(src_dtype, v->dtype)) return fail(v, VOL_ERR_UNSUPPORTED, "unsupported provider dtype");
     v->prov = fn;
+    v->prov_batch = nullptr;
+    v->prov_user = user;
+    v->prov_dtype = src_dtype;
+    return VOL_OK;
+}
+
+int vol_set_provider_batch(vol_t v, vol_provider_batch_fn fn, void* user, int src_dtype) {
+    if (!v) return VOL_ERR_INVALID_ARG;
+    if (fn && !conversion_ok(src_dtype, v->dtype)) return fail(v, VOL_ERR_UNSUPPORTED, "unsupported provider dtype");
+    v->prov_batch = fn;
+    v->prov = nullptr;
     v->prov_user = user;
     v->prov_dtype = src_dtype;
     return VOL_OK;

@@ -157,6 +157,14 @@ class Volume:
         self._provider = C.PROVIDER_FN(tramp)
         C.check(self.lib.vol_set_provider(self.h, self._provider, None, C.DTYPES[src_dtype]), self.h)
 
+    def set_provider_batch(self, fn_address: int, user, src_dtype: str):
+        """Install a native batch provider: fn_address is the address of a C function
+        int fn(void* user, int n, const int32_t* reqs, void* dst); `user` (a ctypes object) is
+        passed by reference and kept alive by this volume."""
+        self._provider = user
+        C.check(self.lib.vol_set_provider_batch(self.h, ctypes.c_void_p(fn_address), ctypes.byref(user),
+                                                C.DTYPES[src_dtype]), self.h)
+
     # ------------------------------------------------------------ render
     def render(self, cams, tf: torch.Tensor, params: dict | None = None, out: torch.Tensor | None = None,
                nsamples: bool = False, grad: bool = False, check_incomplete: bool = True):

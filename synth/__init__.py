@@ -241,3 +241,67 @@ def pixel_subset(w, h, n, seed) -> np.ndarray:
         idx = rng.choice(w * h, size=n, replace=False)
     idx = np.sort(idx)
     return np.stack([idx % w, idx // w], axis=1).astype(np.int32)
+
+
+# --------------------------------------------------- on-demand brick source
+
+class BrickSource(ctypes.Structure):
+    """Parameters of a procedural noise + spheres volume served brick by brick (synth.c)."""
+    _fields_ = [("D0", ctypes.c_int64 * 3), ("brick", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("out8", ctypes.c_int32), ("nthreads", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("octaves", ctypes.c_int32), ("nspheres", ctypes.c_int32), ("period0", ctypes.c_double),
+                ("r_lo", ctypes.c_double), ("r_hi", ctypes.c_double), ("v_lo", ctypes.c_double),
+                ("v_hi", ctypes.c_double)]
+
+
+def brick_source(D0, brick, levels, seed, *, dtype="u8", octaves=5, period0=128.0, nspheres=200,
+                 radius=(4.0, 60.0), value=(0.3, 1.0), nthreads=0) -> BrickSource:
+    s = BrickSource()
+    s.D0[:] = [int(v) for v in D0]
+    s.brick, s.levels, s.out8 = int(brick), int(levels), 1 if dtype == "u8" else 0
+    s.nthreads = _threads(nthreads)
+    s.seed, s.octaves, s.nspheres = int(seed), int(octaves), int(nspheres)
+    s.period0, s.r_lo, s.r_hi, s.v_lo, s.v_hi = float(period0), radius[0], radius[1], value[0], value[1]
+    return s
+
+
+def brick_provider_address() -> int:
+    """Address of synth_brick_provider(void* user, int n, const int32_t* reqs, void* dst): fills n
+    bricks of (B+1)^3 voxels (apron included) for requests [level, bx, by, bz]."""
+    lib = _load()
+    return ctypes.cast(lib.synth_brick_provider, ctypes.c_void_p).value
+
+
+def provide_bricks(src: BrickSource, reqs) -> np.ndarray:
+    """Host call of the same provider: [n, B+1, B+1, B+1] voxels for requests [n, 4]."""
+    lib = _load()
+    reqs = np.ascontiguousarray(reqs, dtype=np.int32).reshape(-1, 4)
+    B1 = src.brick + 1
+    out = np.empty((reqs.shape[0], B1, B1, B1), dtype=np.uint8 if src.out8 else np.uint16)
+    lib.synth_brick_provider.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.synth_brick_provider.restype = ctypes.c_int
+    if lib.synth_brick_provider(ctypes.byref(src), reqs.shape[0], reqs.ctypes.data, out.ctypes.data) != 0:
+        raise RuntimeError("synth_brick_provider failed")
+    return out
+
+
+def noise_spheres_level(D0, level, seed, *, dtype="u8", **kw) -> np.ndarray:
+    """A whole level of the procedural volume (for small sizes), shape (Dz, Dy, Dx)."""
+    Dl = [int(v) for v in D0]
+    for _ in range(level):
+        Dl = [(v + 1) // 2 for v in Dl]
+    if dtype == "u16":
+        return noise_spheres_region(D0, level, Dl, (0, 0, 0), Dl, seed, **kw)
+    lib = _load()
+    lib.synth_noise_spheres_region8.argtypes = lib.synth_noise_spheres_region.argtypes
+    lib.synth_noise_spheres_region8.restype = ctypes.c_int
+    nthreads = kw.pop("nthreads", 0)
+    octaves, period0 = kw.pop("octaves", 5), kw.pop("period0", 128.0)
+    nspheres, radius, value = kw.pop("nspheres", 200), kw.pop("radius", (4.0, 60.0)), kw.pop("value", (0.3, 1.0))
+    out = np.empty((Dl[2], Dl[1], Dl[0]), dtype=np.uint8)
+    rc = lib.synth_noise_spheres_region8(_dims(D0), level, _dims(Dl), _dims((0, 0, 0)), _dims(Dl), seed, octaves,
+                                         period0, nspheres, radius[0], radius[1], value[0], value[1],
+                                         out.ctypes.data, _threads(nthreads))
+    if rc != 0:
+        raise RuntimeError("synth_noise_spheres_region8 failed")
+    return out

@@ -154,11 +154,78 @@ typedef struct {
  * version of the field (this is how procedural on-demand bricks define levels).
  * Output: uint16 round(f * 65535), x fastest.
  */
+static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], const int64_t origin[3],
+                       const int64_t extent[3], uint64_t seed, int octaves, double period0, int nspheres,
+                       double r_lo, double r_hi, double v_lo, double v_hi, void *out, int out8, int nthreads);
+
 int synth_noise_spheres_region(const int64_t D0[3], int level, const int64_t Dl[3],
                                const int64_t origin[3], const int64_t extent[3],
                                uint64_t seed, int octaves, double period0, int nspheres,
                                double r_lo, double r_hi, double v_lo, double v_hi,
                                uint16_t *out, int nthreads)
+{
+    return region_impl(D0, level, Dl, origin, extent, seed, octaves, period0, nspheres, r_lo, r_hi, v_lo, v_hi,
+                       out, 0, nthreads);
+}
+
+/* The same field stored as uint8 round(f * 255). */
+int synth_noise_spheres_region8(const int64_t D0[3], int level, const int64_t Dl[3],
+                                const int64_t origin[3], const int64_t extent[3],
+                                uint64_t seed, int octaves, double period0, int nspheres,
+                                double r_lo, double r_hi, double v_lo, double v_hi,
+                                uint8_t *out, int nthreads)
+{
+    return region_impl(D0, level, Dl, origin, extent, seed, octaves, period0, nspheres, r_lo, r_hi, v_lo, v_hi,
+                       out, 1, nthreads);
+}
+
+/*
+ * Brick source for on-demand loading: the parameters of a noise + spheres volume and its
+ * brick grid.  synth_brick_provider() fills n bricks of (B+1)^3 voxels each (the brick plus
+ * one voxel on its +x/+y/+z sides, indices clamped to the level), bricks in parallel.
+ * reqs[n][4] = level, bx, by, bz.  Level l has ceil(D_{l-1} / 2) voxels per axis and every
+ * level is generated directly from the field (see region_impl).  Returns 0 on success.
+ */
+typedef struct {
+    int64_t D0[3];
+    int32_t brick, levels, out8, nthreads;
+    uint64_t seed;
+    int32_t octaves, nspheres;
+    double period0, r_lo, r_hi, v_lo, v_hi;
+} synth_brick_source;
+
+int synth_brick_provider(void *user, int n, const int32_t *reqs, void *dst)
+{
+    const synth_brick_source *S = (const synth_brick_source *)user;
+    const int64_t B1 = S->brick + 1;
+    const int64_t nvox = B1 * B1 * B1;
+    int err = 0;
+#ifdef _OPENMP
+    if (S->nthreads > 0) omp_set_num_threads(S->nthreads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+#endif
+    for (int i = 0; i < n; ++i) {
+        const int level = reqs[4 * i];
+        if (level < 0 || level >= S->levels) {
+            err |= 1;
+            continue;
+        }
+        int64_t Dl[3], origin[3], extent[3] = {B1, B1, B1};
+        for (int a = 0; a < 3; ++a) {
+            Dl[a] = S->D0[a];
+            for (int l = 0; l < level; ++l) Dl[a] = (Dl[a] + 1) / 2;
+            origin[a] = (int64_t)reqs[4 * i + 1 + a] * S->brick;
+        }
+        void *o = (char *)dst + (size_t)i * (size_t)nvox * (S->out8 ? 1 : 2);
+        err |= region_impl(S->D0, level, Dl, origin, extent, S->seed, S->octaves, S->period0, S->nspheres, S->r_lo,
+                           S->r_hi, S->v_lo, S->v_hi, o, S->out8, 1) != 0;
+    }
+    return err;
+}
+
+static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], const int64_t origin[3],
+                       const int64_t extent[3], uint64_t seed, int octaves, double period0, int nspheres,
+                       double r_lo, double r_hi, double v_lo, double v_hi, void *out, int out8, int nthreads)
 {
     if (octaves < 1 || octaves > 16 || nspheres < 0 || level < 0) return -1;
     double sp[3];
@@ -254,12 +321,15 @@ int synth_noise_spheres_region(const int64_t D0[3], int level, const int64_t Dl[
                     if (dx * dx + dy * dy + dz * dz <= s->r * s->r) acc[x] = s->v;
                 }
             }
-            uint16_t *row = out + Ex * (y + Ey * z);
+            const int64_t ro = Ex * (y + Ey * z);
             for (int64_t x = 0; x < Ex; ++x) {
                 double v = acc[x];
                 if (v < 0) v = 0;
                 if (v > 1) v = 1;
-                row[x] = (uint16_t)floor(v * 65535.0 + 0.5);
+                if (out8)
+                    ((uint8_t *)out)[ro + x] = (uint8_t)floor(v * 255.0 + 0.5);
+                else
+                    ((uint16_t *)out)[ro + x] = (uint16_t)floor(v * 65535.0 + 0.5);
             }
         }
         free(cand);
