@@ -349,6 +349,10 @@ def run_ours(args, dist, rank, ws, local):
                 "per_sample_gather_GBps": b_sample / (t_mean * 1e-3) / 1e9}
 
     variants = {}
+    # empty-space skipping (the paper's ES column): same image and sample counts, less work
+    ms_es = time_frames(torch, vol, cams, tf, dict(params, flags=2), max(5, args.steps // 4), args.warmup, flush)
+    variants["skip_empty"] = {"ms_per_frame": statistics.mean(ms_es),
+                              "samples_per_s": samples / (statistics.mean(ms_es) * 1e-3)}
     if not args.quick and args.workload == "c2":
         for st2 in ("f16", "f32"):
             v2 = build_volume(P, wl, st2, raw)

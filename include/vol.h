@@ -71,6 +71,11 @@ typedef struct {
 } vol_camera;
 
 #define VOL_RENDER_GRAD 1u /* keep transmittance checkpoints for vol_render_backward */
+/* Empty-space skipping (the paper's empty-brick skipping, Sec. III-H and Sec. IV-A): a ray that
+ * enters a brick whose stored value range the transfer function maps to zero opacity jumps
+ * to the brick's last sample.  Those samples would composite nothing (alpha exactly 0), so
+ * the image and the per-pixel sample counts are identical with or without it. */
+#define VOL_RENDER_SKIP_EMPTY 2u
 
 typedef struct {
     float step;          /* sample spacing in level-0 voxels (> 0) */

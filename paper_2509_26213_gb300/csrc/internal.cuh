@@ -57,6 +57,7 @@ struct VolDev {
     int bshift, bmask, B1;         // log2 B, B - 1, B + 1
     int nlevels;
     const uint32_t* pt;
+    const float2* range;           // per slot: min and max stored value (stored units)
     LevelDev lv[kMaxLevels];
     float D0f[3];
 };
@@ -73,6 +74,7 @@ struct RenderDev {
     float step, et;
     float4 bg;
     int lod_mode, lod_bias;
+    int skip_empty;     // skip bricks whose value range the TF maps to zero opacity
     float4* out;
     int* nsamp;
     unsigned* counters;
@@ -150,6 +152,9 @@ cudaError_t launch_upload_bricks(int dst_dtype, int src_dtype, const void* src, 
 // Build level `level` (all bricks; slots_of_bricks indexed by brick id) from level-1.
 cudaError_t launch_downsample(int dtype, const VolDev& vol, int level, const uint32_t* slots_of_bricks,
                               long long nbricks, unsigned* err, cudaStream_t s);
+// range[slots[i]] = (min, max) of the stored values of each listed slot (one CTA per slot).
+cudaError_t launch_slot_range(int dtype, const VolDev& vol, float2* range, const uint32_t* slots, long long n,
+                              cudaStream_t s);
 // pt[idx[i]] = val[i] for i < n (atomic exchange; Sec. III-E parallel insert/remove).
 cudaError_t launch_pt_update(uint32_t* pt, const uint32_t* idx, const uint32_t* val, int n,
                              cudaStream_t s);

@@ -259,6 +259,56 @@ __device__ __forceinline__ float sample_value(const void* atlas, unsigned long l
     else return trilinear<DT, BS>((const typename Voxel<DT>::T*)atlas, base, B1, w);
 }
 
+// A brick whose stored values lie in [rng.x, rng.y] has zero opacity at every sample when no
+// TF entry that a lookup in that range can touch has non-zero alpha (one entry of margin on
+// each side covers the last-bit rounding of the interpolation).
+template <int DT>
+__device__ __forceinline__ bool brick_empty(float2 rng, const int* s_apre) {
+    const float xlo = tf_coord<DT>(rng.x), xhi = tf_coord<DT>(rng.y);
+    const int ilo = max((int)xlo - 1, 0), ihi = min((int)xhi + 2, 255);
+    return s_apre[ihi + 1] - s_apre[ilo] == 0;
+}
+
+// Last sample of the ray that resolves to the same page-table entry (level and brick) as
+// sample k_start: estimated from the brick's exit faces (and the next LOD switch), then fixed
+// by the exact decision arithmetic.  Samples with one page-table entry are contiguous along a
+// ray (level, voxel and brick indices are monotone in t).
+template <bool LOD>
+__device__ __noinline__ int brick_last_sample(int k_start, uint32_t pti_start, const float o[3], const float d[3],
+                                              float t0, float t1, float step, float lodscale, int bias, int nlev,
+                                              const LevelDev* s_lv, int bshift, int bmask, int row, int B) {
+    auto pti_of = [&](int k) -> uint32_t {
+        const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
+        if (!(t < t1)) return kInvalidSlot;
+        const float p[3] = {__fadd_rn(o[0], __fmul_rn(t, d[0])), __fadd_rn(o[1], __fmul_rn(t, d[1])),
+                            __fadd_rn(o[2], __fmul_rn(t, d[2]))};
+        const int l = LOD ? lod_level(t, lodscale, bias, nlev) : 0;
+        Resolved R;
+        resolve(s_lv[l], bshift, bmask, row, p, R);
+        return R.pti;
+    };
+    const float ts = __fadd_rn(t0, __fmul_rn((float)k_start, step));
+    const float ps[3] = {__fadd_rn(o[0], __fmul_rn(ts, d[0])), __fadd_rn(o[1], __fmul_rn(ts, d[1])),
+                         __fadd_rn(o[2], __fmul_rn(ts, d[2]))};
+    const int l = LOD ? lod_level(ts, lodscale, bias, nlev) : 0;
+    const LevelDev& L = s_lv[l];
+    Resolved R;
+    resolve(L, bshift, bmask, row, ps, R);
+    float te = t1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int h = R.i0[a] >> bshift;
+        if (d[a] > 0.0f && h < L.nb[a] - 1) te = fminf(te, (((float)((h + 1) * B) + 0.5f) / L.r[a] - o[a]) / d[a]);
+        else if (d[a] < 0.0f && h > 0) te = fminf(te, (((float)(h * B) + 0.5f) / L.r[a] - o[a]) / d[a]);
+    }
+    if (LOD && l < nlev - 1) te = fminf(te, ldexpf(1.0f, l + 1 - bias) / lodscale);
+    int ke = max(k_start, (int)floorf((te - t0) / step));
+    for (int s = 0; s < 8 && ke > k_start && pti_of(ke) != pti_start; ++s) --ke;
+    if (pti_of(ke) != pti_start) ke = k_start;
+    for (int s = 0; s < 8 && pti_of(ke + 1) == pti_start; ++s) ++ke;
+    return ke;
+}
+
 __device__ __forceinline__ int find_view_tile(const ViewDev* views, int nviews, int item) {
     int lo = 0, hi = nviews - 1;
     while (lo < hi) {
@@ -355,8 +405,18 @@ template <int DT, bool LOD, bool GRAD, int BS, bool Q>
 __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const __grid_constant__ RenderDev P) {
     __shared__ float4 s_tf[256];
     __shared__ LevelDev s_lv[kMaxLevels];
+    __shared__ int s_apre[257];  // s_apre[i]: TF entries below i with non-zero opacity
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = P.tf[i];
     if (threadIdx.x < P.vol.nlevels) s_lv[threadIdx.x] = P.vol.lv[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int i = 0; i < 256; ++i) {
+            s_apre[i] = c;
+            c += s_tf[i].w != 0.0f;
+        }
+        s_apre[256] = c;
+    }
     __syncthreads();
 
     using VT = typename Voxel<DT>::T;
@@ -382,6 +442,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
     int k = 0;
     float C0 = 0, C1 = 0, C2 = 0, T = 1.0f;
     uint32_t cur_pti = kInvalidSlot;
+    bool cur_empty = false;  // the brick of cur_pti has zero opacity everywhere
     const int nlev = P.vol.nlevels;
     int cur_l = 0;
     LvReg L = load_lv(s_lv[0]);
@@ -503,12 +564,17 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 for (int j = kBatch - 1; j >= 0; --j)
                     if (j < nvalid && slot[j] == kInvalidSlot) miss_at = j;
                 const uint32_t miss_pti = miss_at < kBatch ? pti[miss_at] : 0u;
-                // usage stamps: one store per brick change
+                // usage stamps (one store per brick change) and empty-brick test
+                int empty_at = kBatch;
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
-                    if (j < nvalid && j < miss_at && pti[j] != cur_pti) {
-                        cur_pti = pti[j];
-                        if (P.last_used) P.last_used[slot[j]] = P.frame;
+                    if (j < nvalid && j < miss_at) {
+                        if (pti[j] != cur_pti) {
+                            cur_pti = pti[j];
+                            if (P.last_used) P.last_used[slot[j]] = P.frame;
+                            if (P.skip_empty) cur_empty = brick_empty<DT>(__ldg(P.vol.range + slot[j]), s_apre);
+                        }
+                        if (cur_empty && empty_at == kBatch) empty_at = j;
                     }
                 }
                 // (c) gathers, all issued together (unused samples read slot 0, element 0)
@@ -519,7 +585,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     const unsigned long long base = use ? (unsigned long long)slot[j] * slot_stride + loc[j] : 0ull;
                     val[j] = sample_value<DT, BS, Q>(P.vol.atlas, base, B1, wgt[j]);
                 }
-                const int stop = min(nvalid, miss_at);
+                const int stop = min(min(nvalid, miss_at), empty_at);
                 bool fin = false;
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
@@ -540,8 +606,18 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         if (__fsub_rn(1.0f, T) >= et) fin = true;
                     }
                 }
-                if (!fin && nvalid < kBatch && nvalid <= miss_at) fin = true;  // left the volume
-                if (fin) {
+                if (!fin && nvalid < kBatch && nvalid <= miss_at && nvalid <= empty_at) fin = true;  // left the volume
+                if (!fin && empty_at < kBatch && empty_at < miss_at && empty_at < nvalid) {
+                    // sample k is in a brick of zero opacity: every sample up to the brick's last
+                    // composites nothing, so continue after it
+                    const float o3[3] = {o0, o1, o2}, d3[3] = {d0, d1, d2};
+                    const int klast = brick_last_sample<LOD>(k, pti[empty_at], o3, d3, t0, t1, step, lodscale,
+                                                             P.lod_bias, nlev, s_lv, bshift, bmask, row, B1 - 1);
+                    if (GRAD)
+                        for (int kk = ((k + kCkptEvery - 1) / kCkptEvery) * kCkptEvery; kk <= klast; kk += kCkptEvery)
+                            if (kk > 0) P.ckpt[(long long)(kk / kCkptEvery - 1) * P.nrays + ray] = T;
+                    k = klast + 1;
+                } else if (fin) {
                     const float4 bg = P.bg;
                     P.out[ray] = make_float4(fmaf(T, bg.x, C0), fmaf(T, bg.y, C1), fmaf(T, bg.z, C2),
                                              fmaf(T, bg.w, 1.0f - T));

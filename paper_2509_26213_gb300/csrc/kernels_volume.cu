@@ -205,6 +205,43 @@ __global__ void __launch_bounds__(kThreads) k_downsample(typename Stored<DT>::T*
     store4<DT>(atlas + ((unsigned long long)slot * vol.slot_entries + r) * 4, v0, v1, v2, v3);
 }
 
+// Value range of a slot (its brick plus apron, any layout): the render loop skips bricks whose
+// range the transfer function maps to zero opacity.
+template <int DT>
+__global__ void __launch_bounds__(kThreads) k_slot_range(const typename Stored<DT>::T* __restrict__ atlas, VolDev vol,
+                                                         float2* range, const uint32_t* __restrict__ slots) {
+    __shared__ float s_lo[kThreads / 32], s_hi[kThreads / 32];
+    const uint32_t slot = slots[blockIdx.x];
+    if (slot == kInvalidSlot) return;
+    const int B1 = vol.B1, B = B1 - 1;
+    const long long n = vol.quad ? 4ll * B * B * B1 : (long long)B1 * B1 * B1;
+    const typename Stored<DT>::T* a = atlas + (unsigned long long)slot * vol.slot_elems;
+    float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        float v;
+        if constexpr (DT == VOL_F16) v = __half2float(a[i]);
+        else v = (float)a[i];
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
+    }
+    for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kThreads / 32; ++w) {
+            lo = fminf(lo, s_lo[w]);
+            hi = fmaxf(hi, s_hi[w]);
+        }
+        range[slot] = make_float2(lo, hi);
+    }
+}
+
 __global__ void k_pt_update(uint32_t* pt, const uint32_t* idx, const uint32_t* val, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicExch(&pt[idx[i]], val[i]);
@@ -273,6 +310,22 @@ cudaError_t launch_downsample(int dtype, const VolDev& vol, int level, const uin
     case VOL_F16: k_downsample<VOL_F16><<<grid, kThreads, 0, s>>>((__half*)vol.atlas, vol, level, slots, nbricks, err); break;
     case VOL_F32: k_downsample<VOL_F32><<<grid, kThreads, 0, s>>>((float*)vol.atlas, vol, level, slots, nbricks, err); break;
     default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slot_range(int dtype, const VolDev& vol, float2* range, const uint32_t* slots, long long n,
+                              cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    for (long long i0 = 0; i0 < n; i0 += 1ll << 30) {
+        const unsigned g = (unsigned)((n - i0) < (1ll << 30) ? (n - i0) : (1ll << 30));
+        switch (dtype) {
+        case VOL_U8: k_slot_range<VOL_U8><<<g, kThreads, 0, s>>>((const uint8_t*)vol.atlas, vol, range, slots + i0); break;
+        case VOL_U16: k_slot_range<VOL_U16><<<g, kThreads, 0, s>>>((const uint16_t*)vol.atlas, vol, range, slots + i0); break;
+        case VOL_F16: k_slot_range<VOL_F16><<<g, kThreads, 0, s>>>((const __half*)vol.atlas, vol, range, slots + i0); break;
+        case VOL_F32: k_slot_range<VOL_F32><<<g, kThreads, 0, s>>>((const float*)vol.atlas, vol, range, slots + i0); break;
+        default: return cudaErrorInvalidValue;
+        }
     }
     return cudaGetLastError();
 }

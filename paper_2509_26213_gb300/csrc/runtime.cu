@@ -157,6 +157,7 @@ struct vol_s {
     std::vector<unsigned char> order_key;  // tile partition the order was built for
     bool order_ready = false;
     int* order_buckets = nullptr;          // 64 ints: bucket counts and fill cursors
+    float2* range = nullptr;               // per slot: min and max stored value
 
     vol_stats stats{};
     int occ_cache[4][2] = {{0}};
@@ -192,6 +193,7 @@ VolDev vol_dev(const vol_t v) {
     d.B1 = v->B + 1;
     d.nlevels = v->L;
     d.pt = v->pt;
+    d.range = v->range;
     for (int l = 0; l < v->L; ++l) {
         for (int a = 0; a < 3; ++a) {
             d.lv[l].D[a] = (int)v->lay.level_dims[l][a];
@@ -354,6 +356,7 @@ RenderDev render_args(vol_t v) {
     p.bg = make_float4(v->params.bg[0], v->params.bg[1], v->params.bg[2], v->params.bg[3]);
     p.lod_mode = v->params.lod_mode;
     p.lod_bias = v->params.lod_bias;
+    p.skip_empty = (v->params.flags & VOL_RENDER_SKIP_EMPTY) ? 1 : 0;
     p.out = (float4*)v->out;
     p.nsamp = v->nsamp;
     p.counters = v->counters;
@@ -488,6 +491,7 @@ int load_requests(vol_t v) {
         CK(v, cudaMemcpyAsync(v->stage_slots_dev, slots.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, v->stream));
         CK(v, launch_upload_bricks(v->dtype, v->prov_dtype, v->stage_dev, vol_dev(v), v->stage_slots_dev, (long long)n,
                                    v->stream));
+        CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, v->stage_slots_dev, (long long)n, v->stream));
         if (int rc = flush_pt_updates(v)) return rc;
         CK(v, cudaStreamSynchronize(v->stream));  // the pinned stage is reused by the next batch
     }
@@ -543,6 +547,7 @@ int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->counters, sizeof(unsigned) * kNumCounters);
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->aux, sizeof(unsigned) * 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->order_buckets, sizeof(int) * 64);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v->range, sizeof(float2) * (size_t)lay.nslots);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * (size_t)lay.total_bricks, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->last_used, 0, sizeof(unsigned) * (size_t)lay.nslots, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->aux, 0, sizeof(unsigned) * 4, v->stream);
@@ -569,7 +574,7 @@ void vol_destroy(vol_t v) {
     else cudaDeviceSynchronize();
     void* bufs[] = {v->atlas, v->pt, v->last_used, v->counters, v->aux, v->upd_dev, v->views_dev, v->req_table,
                     v->req_list, v->susp[0], v->susp[1], v->ckpt, v->ray_n, v->stage_dev, v->stage_slots_dev,
-                    v->tile_cost, v->tile_order, v->order_buckets};
+                    v->tile_cost, v->tile_order, v->order_buckets, v->range};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (v->stage_host) cudaFreeHost(v->stage_host);
@@ -634,6 +639,7 @@ int vol_upload_level(vol_t v, int level, const void* src, int src_dtype, int src
     }
     cudaError_t e = cudaMemcpyAsync(dslots, slots.data(), sizeof(uint32_t) * (size_t)nb, cudaMemcpyHostToDevice, v->stream);
     if (e == cudaSuccess) e = launch_upload_level(v->dtype, src_dtype, dsrc, vol_dev(v), level, dslots, nb, v->stream);
+    if (e == cudaSuccess) e = launch_slot_range(v->dtype, vol_dev(v), v->range, dslots, nb, v->stream);
     int rc = e == cudaSuccess ? flush_pt_updates(v) : cuda_fail(v, e, "upload_level kernel");
     cudaError_t e2 = cudaStreamSynchronize(v->stream);
     cudaFree(dslots);
@@ -661,6 +667,7 @@ int vol_upload_brick(vol_t v, int level, const int32_t brick[3], const void* src
     }
     CK(v, cudaMemcpyAsync(v->stage_slots_dev, &s, sizeof(uint32_t), cudaMemcpyHostToDevice, v->stream));
     CK(v, launch_upload_bricks(v->dtype, src_dtype, dsrc, vol_dev(v), v->stage_slots_dev, 1, v->stream));
+    CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, v->stage_slots_dev, 1, v->stream));
     if (int rc = flush_pt_updates(v)) return rc;
     CK(v, cudaStreamSynchronize(v->stream));
     return VOL_OK;
@@ -688,6 +695,7 @@ int vol_build_lod(vol_t v, int from_level) {
         int rc = VOL_OK;
         if (e == cudaSuccess) rc = flush_pt_updates(v);  // the source level's entries must be live
         if (e == cudaSuccess && !rc) e = launch_downsample(v->dtype, vol_dev(v), l, dslots, nb, v->aux, v->stream);
+        if (e == cudaSuccess && !rc) e = launch_slot_range(v->dtype, vol_dev(v), v->range, dslots, nb, v->stream);
         cudaError_t e2 = cudaStreamSynchronize(v->stream);
         cudaFree(dslots);
         if (rc) return rc;
