@@ -404,11 +404,16 @@ __host__ __device__ constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x
 template <int DT, bool LOD, bool GRAD, int BS, bool Q>
 __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const __grid_constant__ RenderDev P) {
     __shared__ float4 s_tf[256];
+    __shared__ float4 s_tfd[255];  // tf[i+1] - tf[i], each difference rounded once
     __shared__ LevelDev s_lv[kMaxLevels];
     __shared__ int s_apre[257];  // s_apre[i]: TF entries below i with non-zero opacity
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = P.tf[i];
     if (threadIdx.x < P.vol.nlevels) s_lv[threadIdx.x] = P.vol.lv[threadIdx.x];
     __syncthreads();
+    for (int i = threadIdx.x; i < 255; i += blockDim.x) {
+        const float4 a = s_tf[i], b = s_tf[i + 1];
+        s_tfd[i] = make_float4(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y), __fsub_rn(b.z, a.z), __fsub_rn(b.w, a.w));
+    }
     if (threadIdx.x == 0) {
         int c = 0;
         for (int i = 0; i < 256; ++i) {
@@ -595,12 +600,12 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         const float x = tf_coord<DT>(val[j]);
                         const int i = min((int)x, 254);
                         const float wt = x - (float)i;
-                        const float4 a = s_tf[i], b = s_tf[i + 1];
-                        const float al = fmaf(wt, b.w - a.w, a.w);
+                        const float4 a = s_tf[i], dab = s_tfd[i];  // entry i and tf[i+1] - tf[i]
+                        const float al = fmaf(wt, dab.w, a.w);
                         const float Ta = T * al;
-                        C0 = fmaf(Ta, fmaf(wt, b.x - a.x, a.x), C0);
-                        C1 = fmaf(Ta, fmaf(wt, b.y - a.y, a.y), C1);
-                        C2 = fmaf(Ta, fmaf(wt, b.z - a.z, a.z), C2);
+                        C0 = fmaf(Ta, fmaf(wt, dab.x, a.x), C0);
+                        C1 = fmaf(Ta, fmaf(wt, dab.y, a.y), C1);
+                        C2 = fmaf(Ta, fmaf(wt, dab.z, a.z), C2);
                         T = T * (1.0f - al);
                         ++k;
                         if (__fsub_rn(1.0f, T) >= et) fin = true;
