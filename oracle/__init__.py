@@ -100,6 +100,10 @@ def _load():
                                        ctypes.POINTER(_Params), vp, ctypes.c_int64, ctypes.c_double,
                                        vp, vp, vp, vp, vp, ctypes.c_int]
             lib.orc_render.restype = ctypes.c_int
+            lib.orc_render_max.argtypes = [ctypes.POINTER(_Volume), ctypes.POINTER(_Camera), vp,
+                                           ctypes.POINTER(_Params), ctypes.c_int, vp, ctypes.c_int64,
+                                           ctypes.c_double, vp, vp, vp, vp, ctypes.c_int]
+            lib.orc_render_max.restype = ctypes.c_int
             lib.orc_render_grad.argtypes = [ctypes.POINTER(_Volume), ctypes.POINTER(_Camera), vp,
                                             ctypes.POINTER(_Params), vp, ctypes.c_int64,
                                             ctypes.c_double, vp, vp, vp, vp, ctypes.c_int]
@@ -254,6 +258,33 @@ def render(vol: Volume, cam: dict, tf: np.ndarray, params: dict, pixels=None, am
     if rc:
         raise RuntimeError("orc_render failed")
     return {"rgba": rgba, "n": n, "alt_rgba": alt, "alt_n": alt_n, "amb": flag.astype(bool)}
+
+
+PROJECTIONS = {"mop": 1, "mip": 2}
+
+
+def render_max(vol: Volume, cam: dict, tf: np.ndarray, params: dict, mode: str, pixels=None, amb=1e-5,
+               nthreads=0) -> dict:
+    """FP64 maximum-opacity ("mop") or maximum-intensity ("mip") projection (Sec. V-A).
+
+    Returns rgba [n,4], n (samples on the ray) and lo/hi [n,4]: per channel the range of the
+    outputs over the samples whose opacity lies within ``amb`` of the maximum (MOP)."""
+    tf = np.ascontiguousarray(tf, dtype=np.float32)
+    assert tf.shape == (256, 4)
+    if pixels is None:
+        npix, pp = int(cam["w"]) * int(cam["h"]), None
+    else:
+        pixels = np.ascontiguousarray(pixels, dtype=np.int32)
+        npix, pp = pixels.shape[0], pixels.ctypes.data
+    rgba = np.zeros((npix, 4)); lo = np.zeros((npix, 4)); hi = np.zeros((npix, 4))
+    n = np.zeros(npix, dtype=np.int32)
+    rc = _load().orc_render_max(ctypes.byref(vol._s), ctypes.byref(_cam(cam)), tf.ctypes.data,
+                                ctypes.byref(_params(**params)), PROJECTIONS[mode], pp, npix, float(amb),
+                                rgba.ctypes.data, lo.ctypes.data, hi.ctypes.data, n.ctypes.data,
+                                int(nthreads))
+    if rc:
+        raise RuntimeError("orc_render_max failed")
+    return {"rgba": rgba, "lo": lo, "hi": hi, "n": n}
 
 
 def render_grad(vol: Volume, cam: dict, tf: np.ndarray, params: dict, dI: np.ndarray, pixels=None,

@@ -13,6 +13,8 @@
  *   - dynamic LOD selection while rendering                    (Sec. V-C; App.)
  *   - front-to-back emission/absorption compositing (DVR) with a 1D RGBA
  *     transfer function                                         (Sec. IV-A; Fig. 1)
+ *   - maximum-opacity projection (MOP), and maximum-intensity projection
+ *     beside it                                                 (Sec. V-A; Table I)
  * The paper gives no formulas for ray setup, interpolation, LOD choice or
  * compositing; the readings used here are listed in the design notes and in
  * the comments of each function.
@@ -381,19 +383,17 @@ static void interp(const orc_volume *V, const orc_resolve *R, orc_interp *I)
 
 typedef struct {
     double rgba[4];
+    double x;       /* TF coordinate */
     int i;          /* lower TF entry */
     double w;       /* weight of entry i + 1 */
     int inside;     /* value was inside [0, 1] (clamp inactive) */
 } orc_tflookup;
 
-/* 1D RGBA transfer function with N = 256 entries (Fig. 1's grey_ramp_tf is
- * such a table): value clamped to [0, 1], x = v * (N - 1),
- * i = min(floor(x), N - 2), rgba = tf[i] + (x - i) * (tf[i+1] - tf[i]). */
-static void tf_lookup(const float *tf, double v, orc_tflookup *L)
+/* The TF at coordinate x in [0, 255]: i = min(floor(x), 254),
+ * rgba = tf[i] + (x - i) * (tf[i+1] - tf[i]). */
+static void tf_at(const float *tf, double x, orc_tflookup *L)
 {
-    L->inside = (v >= 0.0 && v <= 1.0);
-    double vc = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
-    double x = vc * 255.0;
+    L->x = x;
     int i = (int)floor(x);
     if (i > 254) i = 254;
     double w = x - (double)i;
@@ -403,6 +403,15 @@ static void tf_lookup(const float *tf, double v, orc_tflookup *L)
         double a = tf[4 * i + ch], b = tf[4 * (i + 1) + ch];
         L->rgba[ch] = a + w * (b - a);
     }
+}
+
+/* 1D RGBA transfer function with N = 256 entries (Fig. 1's grey_ramp_tf is
+ * such a table): value clamped to [0, 1], x = v * (N - 1), then tf_at(x). */
+static void tf_lookup(const float *tf, double v, orc_tflookup *L)
+{
+    L->inside = (v >= 0.0 && v <= 1.0);
+    double vc = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+    tf_at(tf, vc * 255.0, L);
 }
 
 /* --------------------------------------------------------- tracing */
@@ -549,6 +558,114 @@ int orc_render(const orc_volume *V, const orc_camera *c, const float *tf, const 
                 memcpy(&alt_rgba[4 * i], &out_rgba[4 * i], 4 * sizeof(double));
                 alt_n[i] = (int32_t)n;
                 amb_flag[i] = 0;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ----------------------------------------------- maximum projections */
+
+/*
+ * Maximum-opacity projection (MOP; the Kidney renderings of Sec. V-A, Table I)
+ * and maximum-intensity projection (MIP).  The paper names MOP without a
+ * formula; the reading used here visits every sample of the ray (no early
+ * termination) and keeps one of them:
+ *   MOP -- the first sample of largest TF opacity alpha_k (a later sample
+ *          replaces it only when its opacity is strictly larger), with its
+ *          TF colour c_k;
+ *   MIP -- the largest TF coordinate x_k = 255 clamp(v_k, 0, 1), then the TF
+ *          at that coordinate gives (c, alpha);
+ * and composites the kept (c, alpha) once over the background:
+ *   rgb = alpha c + (1 - alpha) bg_rgb,   a = alpha + (1 - alpha) bg_a.
+ * A ray that misses the box gives bg, and so does MOP when every opacity is 0.
+ */
+enum { ORC_MOP = 1, ORC_MIP = 2 };
+
+static void composite_one(const double rgba[4], const orc_params *P, double *out)
+{
+    double al = rgba[3];
+    for (int ch = 0; ch < 3; ++ch) out[ch] = al * rgba[ch] + (1.0 - al) * (double)P->bg[ch];
+    out[3] = al + (1.0 - al) * (double)P->bg[3];
+}
+
+/* TF lookup of sample k of ray r (value layer); returns 0 past the exit. */
+static int sample_lookup(const orc_volume *V, const orc_camera *c, const float *tf, const orc_params *P,
+                         const orc_ray *r, int64_t k, orc_tflookup *L)
+{
+    float t = sample_t(r, P->step, k);
+    if (!(t < r->t1)) return 0;
+    float p[3];
+    for (int a = 0; a < 3; ++a) p[a] = r->o[a] + t * r->d[a];
+    int l = lod_level(t, lod_scale(c), P->lod_bias, V->nlevels, P->lod_mode);
+    orc_resolve R;
+    resolve(V, l, p, &R);
+    orc_interp I;
+    interp(V, &R, &I);
+    tf_lookup(tf, I.v, L);
+    return 1;
+}
+
+/*
+ * Render npix pixels in projection mode `mode` (ORC_MOP or ORC_MIP); pixel
+ * list as in orc_render.  out_n receives the samples of the ray.
+ * MOP compares float64 opacities here and float32 ones on the GPU, so any
+ * sample whose opacity lies within `amb` of the maximum may be the one kept:
+ * lo and hi receive, per channel, the least and greatest output over those
+ * samples (both equal out when no other sample is that close).  MIP's output
+ * is continuous in the maximum, so there lo = hi = out.
+ */
+int orc_render_max(const orc_volume *V, const orc_camera *c, const float *tf, const orc_params *P, int mode,
+                   const int32_t *pix, int64_t npix, double amb, double *out_rgba, double *lo, double *hi,
+                   int32_t *out_n, int nthreads)
+{
+    if (V->nlevels < 1 || V->nlevels > ORC_MAX_LEVELS || V->brick < 1) return -1;
+    if (mode != ORC_MOP && mode != ORC_MIP) return -1;
+    if (!pix) npix = (int64_t)c->w * c->h;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < npix; ++i) {
+        int32_t px = pix ? pix[2 * i] : (int32_t)(i % c->w);
+        int32_t py = pix ? pix[2 * i + 1] : (int32_t)(i / c->w);
+        orc_ray r;
+        orc_make_ray(c, V->dims[0], px, py, &r);
+        double kept[4] = {0.0, 0.0, 0.0, 0.0};
+        double best = mode == ORC_MOP ? 0.0 : -1.0; /* MOP: largest alpha; MIP: largest x */
+        int64_t n = 0;
+        orc_tflookup L;
+        if (r.hit) {
+            for (; sample_lookup(V, c, tf, P, &r, n, &L); ++n) {
+                if (mode == ORC_MOP && L.rgba[3] > best) {
+                    best = L.rgba[3];
+                    memcpy(kept, L.rgba, sizeof kept);
+                } else if (mode == ORC_MIP && L.x > best) {
+                    best = L.x;
+                }
+            }
+        }
+        if (mode == ORC_MIP && best >= 0.0) {
+            tf_at(tf, best, &L);
+            memcpy(kept, L.rgba, sizeof kept);
+        }
+        double *o = &out_rgba[4 * i];
+        composite_one(kept, P, o);
+        out_n[i] = (int32_t)n;
+        if (lo) {
+            memcpy(&lo[4 * i], o, 4 * sizeof(double));
+            memcpy(&hi[4 * i], o, 4 * sizeof(double));
+            if (mode == ORC_MOP) {
+                for (int64_t k = 0; k < n; ++k) {
+                    sample_lookup(V, c, tf, P, &r, k, &L);
+                    if (!(L.rgba[3] >= best - amb)) continue;
+                    double cand[4];
+                    composite_one(L.rgba, P, cand);
+                    for (int ch = 0; ch < 4; ++ch) {
+                        if (cand[ch] < lo[4 * i + ch]) lo[4 * i + ch] = cand[ch];
+                        if (cand[ch] > hi[4 * i + ch]) hi[4 * i + ch] = cand[ch];
+                    }
+                }
             }
         }
     }
