@@ -108,7 +108,7 @@ def measured_peaks():
 
 def render_kernel_digest():
     h = hashlib.sha256()
-    for f in ("kernels_render.cu", "internal.cuh"):
+    for f in ("kernels_render.cu", "render_common.cuh", "internal.cuh"):
         with open(os.path.join(ROOT, "paper_2509_26213_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -353,6 +353,20 @@ def run_ours(args, dist, rank, ws, local):
     ms_es = time_frames(torch, vol, cams, tf, dict(params, flags=2), max(5, args.steps // 4), args.warmup, flush)
     variants["skip_empty"] = {"ms_per_frame": statistics.mean(ms_es),
                               "samples_per_s": samples / (statistics.mean(ms_es) * 1e-3)}
+    if not args.quick and args.workload in ("c2", "c3"):
+        # maximum-opacity projection (the compositing of the paper's Kidney renderings) and
+        # maximum-intensity projection: every ray runs to its exit unless it reaches the
+        # largest TF opacity (MOP) or coordinate (MIP); with and without empty-space skipping
+        for mode in ("mop", "mip"):
+            pm = dict(params, composite=mode)
+            _, nsm = vol.render(cams, tf, pm, nsamples=True)
+            torch.cuda.synchronize()
+            sm = int(nsm.sum().item())
+            nrep = max(3, args.steps // 4)
+            msm = statistics.mean(time_frames(torch, vol, cams, tf, pm, nrep, args.warmup, flush))
+            msk = statistics.mean(time_frames(torch, vol, cams, tf, dict(pm, flags=2), nrep, args.warmup, flush))
+            variants[mode] = {"ms_per_frame": msm, "samples_per_frame": sm, "samples_per_s": sm / (msm * 1e-3),
+                              "ms_per_frame_skip_empty": msk}
     if not args.quick and args.workload == "c2":
         for st2 in ("f16", "f32"):
             v2 = build_volume(P, wl, st2, raw)

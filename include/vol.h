@@ -77,6 +77,24 @@ typedef struct {
  * the image and the per-pixel sample counts are identical with or without it. */
 #define VOL_RENDER_SKIP_EMPTY 2u
 
+/* Compositing (vol_params.composite).
+ * VOL_COMPOSITE_DVR: front-to-back emission/absorption with early termination (Sec. IV-A).
+ * VOL_COMPOSITE_MOP: maximum-opacity projection, the mode of the paper's Kidney renderings
+ *   (Sec. V-A, Table I): every sample is visited and the first one of largest TF opacity is
+ *   kept (a later one replaces it only when strictly more opaque).  The ray stops early once
+ *   the kept opacity reaches the largest opacity of any TF entry.
+ * VOL_COMPOSITE_MIP: maximum-intensity projection: the largest TF coordinate
+ *   x = 255 clamp(v, 0, 1) over the samples is kept and the TF looked up there.  The ray
+ *   stops early at x = 255.
+ * Both projections composite the kept (rgb, a) once over the background:
+ *   out_rgb = a rgb + (1 - a) bg_rgb,  out_a = a + (1 - a) bg_a,
+ * and give bg for a ray that misses the box.  With VOL_RENDER_SKIP_EMPTY, a ray skips a
+ * brick whose stored value range bounds every sample's opacity (MOP) or coordinate (MIP)
+ * at or below the kept one; the image does not change.  Neither has an adjoint. */
+#define VOL_COMPOSITE_DVR 0
+#define VOL_COMPOSITE_MOP 1
+#define VOL_COMPOSITE_MIP 2
+
 typedef struct {
     float step;          /* sample spacing in level-0 voxels (> 0) */
     float et_threshold;  /* stop a ray after the sample where 1 - T >= et_threshold */
@@ -90,6 +108,7 @@ typedef struct {
     int32_t refill;      /* a warp fetches new rays once fewer lanes than this are busy
                             (1..32; 0 = default 20); performance only, never the image */
     int32_t ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
+    int32_t composite;   /* VOL_COMPOSITE_* (0 = emission/absorption) */
 } vol_params;
 
 /* Atlas slot layouts (vol_plan / vol_create flags).

@@ -27,6 +27,9 @@ VOL_U8, VOL_U16, VOL_F16, VOL_F32 = 0, 1, 2, 3
 DTYPES = {"u8": VOL_U8, "u16": VOL_U16, "f16": VOL_F16, "f32": VOL_F32}
 MAX_LEVELS = 16
 VOL_RENDER_GRAD = 1
+VOL_RENDER_SKIP_EMPTY = 2
+VOL_COMPOSITE_DVR, VOL_COMPOSITE_MOP, VOL_COMPOSITE_MIP = 0, 1, 2
+COMPOSITES = {"dvr": VOL_COMPOSITE_DVR, "mop": VOL_COMPOSITE_MOP, "mip": VOL_COMPOSITE_MIP}
 VOL_LAYOUT_COMPACT = 1
 LAYOUTS = {"quad": 0, "compact": VOL_LAYOUT_COMPACT}
 
@@ -49,7 +52,7 @@ class vol_params(ctypes.Structure):
     _fields_ = [("step", ctypes.c_float), ("et_threshold", ctypes.c_float), ("bg", ctypes.c_float * 4),
                 ("lod_mode", ctypes.c_int32), ("lod_bias", ctypes.c_int32), ("tile_w", ctypes.c_int32),
                 ("tile_h", ctypes.c_int32), ("max_passes", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("refill", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("refill", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("composite", ctypes.c_int32)]
 
 
 class vol_layout(ctypes.Structure):

@@ -14,6 +14,12 @@ constexpr int kCkptEvery = 32;      // transmittance checkpoint spacing (samples
 constexpr int kRenderThreads = 128; // threads per CTA of the render kernels
 constexpr int kMaxProbe = 64;       // bounded linear probing of the request table
 
+// Compositing variants of the forward kernel (template argument MODE of k_render).
+constexpr int kDvr = 0;      // emission/absorption, front to back (Sec. IV-A)
+constexpr int kDvrGrad = 1;  // the same, keeping transmittance checkpoints for the adjoint
+constexpr int kMop = 2;      // maximum-opacity projection (Sec. V-A, Table I)
+constexpr int kMip = 3;      // maximum-intensity projection
+
 // Counter words of one render (device memory, reset before each pass).
 enum Counter : int {
     kWork = 0,       // next work item (tile or suspended-ray chunk)
@@ -132,10 +138,13 @@ struct TraceDev {
 };
 
 // ---- launchers (kernels_render.cu) ----
-cudaError_t launch_render(int dtype, bool grad, const RenderDev& p, int grid, cudaStream_t s);
+// mode: kDvr, kDvrGrad, kMop or kMip.
+cudaError_t launch_render(int dtype, int mode, const RenderDev& p, int grid, cudaStream_t s);
 cudaError_t launch_backward(int dtype, const BackwardDev& p, int grid, cudaStream_t s);
 cudaError_t launch_trace(const TraceDev& p, cudaStream_t s);
 int render_blocks_per_sm(int dtype, bool grad);
+// Maximum projections (kernels_project.cu): the k_render variant for mode kMop or kMip.
+const void* pick_render_projection(int dtype, int brick, bool quad, bool lod, int mode);
 // order[] = tiles sorted by descending log2 bucket of cost[] (heaviest first); zeroes cost[].
 // buckets: 64 ints of device scratch.
 cudaError_t launch_tile_order(int* cost, int* order, int ntiles, int* buckets, cudaStream_t s);

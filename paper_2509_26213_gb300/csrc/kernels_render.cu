@@ -1,650 +1,11 @@
-// kernels_render.cu -- raycast forward (persistent, batched), adjoint, and decision trace.
-//
-// The forward kernel is the data-parallel hot path of the bricked multi-resolution
-// raycaster (Drees & Risse, "Palace", Sec. III-E, III-H, IV-A, V-C): per pixel it builds
-// the camera ray, intersects the volume box, and for each sample picks the LOD level from
-// the pixel footprint, resolves the brick through the level's page table into the atlas,
-// interpolates trilinearly inside the brick (the +side apron makes every corner local),
-// maps the value through the RGBA transfer function, and composites front to back with
-// early termination.
-//
-// Work distribution: one persistent grid; each warp takes ray tiles (or, on a resume
-// pass, chunks of 32 suspended rays) from a global counter and refills lanes whose ray
-// ended as soon as fewer than `refill_thresh` lanes are busy, so early-terminated rays do
-// not leave lanes idle.
-//
-// Decision arithmetic (ray setup, sample positions, LOD level, voxel index, brick id) is
-// binary32 with explicit round-to-nearest intrinsics, so it never contracts into FMAs and
-// is bit-identical to any correct IEEE binary32 evaluation of the same expressions.
-#include "internal.cuh"
+// kernels_render.cu -- variants of the forward kernel for emission/absorption compositing
+// (with and without gradient checkpoints), the adjoint, the heaviest-first tile order and
+// the decision trace.  The forward kernel template and its building blocks are in
+// render_common.cuh.
+#include "render_common.cuh"
 
 namespace volrc {
 namespace {
-
-constexpr unsigned kFull = 0xFFFFFFFFu;
-
-template <int DT>
-struct Voxel;
-template <>
-struct Voxel<VOL_U8> {
-    using T = uint8_t;
-    static __device__ __forceinline__ float ld(const T* p) { return (float)__ldg(p); }
-};
-template <>
-struct Voxel<VOL_U16> {
-    using T = uint16_t;
-    static __device__ __forceinline__ float ld(const T* p) { return (float)__ldg(p); }
-};
-template <>
-struct Voxel<VOL_F16> {
-    using T = __half;
-    static __device__ __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)); }
-};
-template <>
-struct Voxel<VOL_F32> {
-    using T = float;
-    static __device__ __forceinline__ float ld(const T* p) { return __ldg(p); }
-};
-
-// Transfer-function coordinate x = 255 * clamp(v_normalised, 0, 1) from an interpolated
-// stored value (u8: stored = 255 v; u16: stored = 65535 v; floats: v).
-template <int DT>
-__device__ __forceinline__ float tf_coord(float v) {
-    if (DT == VOL_U8) return v;
-    if (DT == VOL_U16) return v * (255.0f / 65535.0f);
-    return fminf(fmaxf(v, 0.0f), 1.0f) * 255.0f;
-}
-template <int DT>
-__device__ __forceinline__ bool tf_inside(float v) {
-    if (DT == VOL_U8 || DT == VOL_U16) return true;
-    return v >= 0.0f && v <= 1.0f;
-}
-
-struct Ray {
-    float o[3], d[3], t0, t1;
-    bool hit;
-};
-
-// Pixel -> ray and slab entry/exit against [0, D0) (Fig. 1 entry_exit_points).
-__device__ __forceinline__ void make_ray(const ViewDev& V, const float D0f[3], int px, int py, Ray& r) {
-    const float u = __fsub_rn(__fmul_rn(__fdiv_rn(__fadd_rn((float)px, 0.5f), (float)V.w), 2.0f), 1.0f);
-    const float v = __fsub_rn(1.0f, __fmul_rn(__fdiv_rn(__fadd_rn((float)py, 0.5f), (float)V.h), 2.0f));
-    const float cx = __fmul_rn(u, V.tan_aspect);
-    const float cy = __fmul_rn(v, V.tan);
-    float dd[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        dd[a] = __fadd_rn(__fadd_rn(V.fwd[a], __fmul_rn(cx, V.right[a])), __fmul_rn(cy, V.up[a]));
-    const float len2 = __fadd_rn(__fadd_rn(__fmul_rn(dd[0], dd[0]), __fmul_rn(dd[1], dd[1])), __fmul_rn(dd[2], dd[2]));
-    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(len2));
-    float t0 = 0.0f, t1 = __int_as_float(0x7f800000);
-    bool hit = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        r.d[a] = __fmul_rn(dd[a], inv);
-        r.o[a] = V.eye[a];
-        if (r.d[a] == 0.0f) {
-            if (r.o[a] < 0.0f || r.o[a] >= D0f[a]) hit = false;
-            continue;
-        }
-        const float ta = __fdiv_rn(__fsub_rn(0.0f, r.o[a]), r.d[a]);
-        const float tb = __fdiv_rn(__fsub_rn(D0f[a], r.o[a]), r.d[a]);
-        const float tn = ta < tb ? ta : tb;
-        const float tf = ta < tb ? tb : ta;
-        if (tn > t0) t0 = tn;
-        if (tf < t1) t1 = tf;
-    }
-    r.t0 = t0;
-    r.t1 = t1;
-    r.hit = hit && (t0 < t1);
-}
-
-// Footprint LOD (Sec. V-C): l = clamp(ilogb(t * lodscale) + bias, 0, L-1); l = 0 when the
-// footprint has no normal exponent.
-__device__ __forceinline__ int lod_level(float t, float lodscale, int bias, int nlevels) {
-    const float q = __fmul_rn(t, lodscale);
-    const int e = (q >= 1.17549435e-38f) ? (int)((__float_as_uint(q) >> 23) & 0xFF) - 127 : -127;
-    return min(max(e + bias, 0), nlevels - 1);
-}
-
-struct Resolved {
-    int i0[3];
-    float w[3];
-    uint32_t pti;   // page-table index (level offset + brick id)
-    uint32_t local; // element offset inside the slot
-};
-
-// One level's constants, held in registers by the render loop.
-struct LvReg {
-    float r[3];     // D_l / D_0 per axis (binary32)
-    int Dm[3];      // D_l - 1 per axis
-    int nb0, nb1;   // bricks along x and y
-    uint32_t off;   // first page-table entry of the level
-};
-
-__device__ __forceinline__ LvReg load_lv(const LevelDev& L) {
-    LvReg R;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        R.r[a] = L.r[a];
-        R.Dm[a] = L.D[a] - 1;
-    }
-    R.nb0 = L.nb[0];
-    R.nb1 = L.nb[1];
-    R.off = L.pt_off;
-    return R;
-}
-
-// Grid position on a level, clamp to edge, chunk addressing (Sec. III-A).
-// local = element (compact: row = B+1) or entry (quad: row = B) offset inside the slot.
-__device__ __forceinline__ void resolve_reg(const LvReg& L, int bshift, int bmask, int row, const float p[3],
-                                            Resolved& R) {
-    int h[3], l[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float x = __fsub_rn(__fmul_rn(p[a], L.r[a]), 0.5f);
-        const float fx = floorf(x);
-        const int i = (int)fx;
-        if (i < 0) {
-            R.i0[a] = 0;
-            R.w[a] = 0.0f;
-        } else if (i >= L.Dm[a]) {
-            R.i0[a] = L.Dm[a];
-            R.w[a] = 0.0f;
-        } else {
-            R.i0[a] = i;
-            R.w[a] = __fsub_rn(x, fx);
-        }
-        h[a] = R.i0[a] >> bshift;
-        l[a] = R.i0[a] & bmask;
-    }
-    R.pti = L.off + (uint32_t)(h[0] + L.nb0 * (h[1] + L.nb1 * h[2]));
-    R.local = (uint32_t)((l[2] * row + l[1]) * row + l[0]);
-}
-
-__device__ __forceinline__ void resolve(const LevelDev& L, int bshift, int bmask, int row, const float p[3],
-                                        Resolved& R) {
-    resolve_reg(load_lv(L), bshift, bmask, row, p, R);
-}
-
-// Trilinear interpolation of the 8 corners at atlas element `base` (+x, +y, +z neighbours
-// at +1, +B1, +B1^2 thanks to the apron).
-template <int DT, int BS = 0>
-__device__ __forceinline__ float trilinear(const typename Voxel<DT>::T* a, unsigned long long base, int B1_rt,
-                                           const float w[3]) {
-    const int B1 = BS ? BS + 1 : B1_rt;
-    const unsigned long long sy = (unsigned long long)B1, sz = (unsigned long long)B1 * B1;
-    const float v000 = Voxel<DT>::ld(a + base), v100 = Voxel<DT>::ld(a + base + 1);
-    const float v010 = Voxel<DT>::ld(a + base + sy), v110 = Voxel<DT>::ld(a + base + sy + 1);
-    const float v001 = Voxel<DT>::ld(a + base + sz), v101 = Voxel<DT>::ld(a + base + sz + 1);
-    const float v011 = Voxel<DT>::ld(a + base + sz + sy), v111 = Voxel<DT>::ld(a + base + sz + sy + 1);
-    const float c00 = fmaf(w[0], v100 - v000, v000);
-    const float c10 = fmaf(w[0], v110 - v010, v010);
-    const float c01 = fmaf(w[0], v101 - v001, v001);
-    const float c11 = fmaf(w[0], v111 - v011, v011);
-    const float c0 = fmaf(w[1], c10 - c00, c00);
-    const float c1 = fmaf(w[1], c11 - c01, c01);
-    return fmaf(w[2], c1 - c0, c0);
-}
-
-// Quad layout: entry e holds the voxels (x, y), (x+1, y), (x, y+1), (x+1, y+1) of one slice;
-// the entry of slice z+1 is B*B entries further.  Same interpolation order as trilinear().
-template <int DT>
-struct QuadEntry;
-template <>
-struct QuadEntry<VOL_U8> {
-    using V = unsigned int;
-    static __device__ __forceinline__ void get(V q, float v[4]) {
-        v[0] = (float)(q & 0xFFu);
-        v[1] = (float)((q >> 8) & 0xFFu);
-        v[2] = (float)((q >> 16) & 0xFFu);
-        v[3] = (float)(q >> 24);
-    }
-};
-template <>
-struct QuadEntry<VOL_U16> {
-    using V = uint2;
-    static __device__ __forceinline__ void get(V q, float v[4]) {
-        v[0] = (float)(q.x & 0xFFFFu);
-        v[1] = (float)(q.x >> 16);
-        v[2] = (float)(q.y & 0xFFFFu);
-        v[3] = (float)(q.y >> 16);
-    }
-};
-template <>
-struct QuadEntry<VOL_F16> {
-    using V = uint2;
-    static __device__ __forceinline__ void get(V q, float v[4]) {
-        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-        v[0] = a.x;
-        v[1] = a.y;
-        v[2] = b.x;
-        v[3] = b.y;
-    }
-};
-template <>
-struct QuadEntry<VOL_F32> {
-    using V = float4;
-    static __device__ __forceinline__ void get(V q, float v[4]) {
-        v[0] = q.x;
-        v[1] = q.y;
-        v[2] = q.z;
-        v[3] = q.w;
-    }
-};
-
-template <int DT, int BS = 0>
-__device__ __forceinline__ float trilinear_quad(const void* atlas, unsigned long long entry, int B_rt, const float w[3]) {
-    using Q = QuadEntry<DT>;
-    const int B = BS ? BS : B_rt;
-    const typename Q::V* a = (const typename Q::V*)atlas;
-    float e0[4], e1[4];
-    Q::get(__ldg(a + entry), e0);
-    Q::get(__ldg(a + entry + (unsigned long long)(B * B)), e1);
-    const float c00 = fmaf(w[0], e0[1] - e0[0], e0[0]);
-    const float c10 = fmaf(w[0], e0[3] - e0[2], e0[2]);
-    const float c01 = fmaf(w[0], e1[1] - e1[0], e1[0]);
-    const float c11 = fmaf(w[0], e1[3] - e1[2], e1[2]);
-    const float c0 = fmaf(w[1], c10 - c00, c00);
-    const float c1 = fmaf(w[1], c11 - c01, c01);
-    return fmaf(w[2], c1 - c0, c0);
-}
-
-// Either layout: `base` is the slot's element offset plus local (compact) or its entry offset
-// plus local (quad).
-template <int DT, int BS, bool Q>
-__device__ __forceinline__ float sample_value(const void* atlas, unsigned long long base, int B1, const float w[3]) {
-    if constexpr (Q) return trilinear_quad<DT, BS>(atlas, base, B1 - 1, w);
-    else return trilinear<DT, BS>((const typename Voxel<DT>::T*)atlas, base, B1, w);
-}
-
-// A brick whose stored values lie in [rng.x, rng.y] has zero opacity at every sample when no
-// TF entry that a lookup in that range can touch has non-zero alpha (one entry of margin on
-// each side covers the last-bit rounding of the interpolation).
-template <int DT>
-__device__ __forceinline__ bool brick_empty(float2 rng, const int* s_apre) {
-    const float xlo = tf_coord<DT>(rng.x), xhi = tf_coord<DT>(rng.y);
-    const int ilo = max((int)xlo - 1, 0), ihi = min((int)xhi + 2, 255);
-    return s_apre[ihi + 1] - s_apre[ilo] == 0;
-}
-
-// Last sample of the ray that resolves to the same page-table entry (level and brick) as
-// sample k_start: estimated from the brick's exit faces (and the next LOD switch), then fixed
-// by the exact decision arithmetic.  Samples with one page-table entry are contiguous along a
-// ray (level, voxel and brick indices are monotone in t).
-template <bool LOD>
-__device__ __noinline__ int brick_last_sample(int k_start, uint32_t pti_start, const float o[3], const float d[3],
-                                              float t0, float t1, float step, float lodscale, int bias, int nlev,
-                                              const LevelDev* s_lv, int bshift, int bmask, int row, int B) {
-    auto pti_of = [&](int k) -> uint32_t {
-        const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
-        if (!(t < t1)) return kInvalidSlot;
-        const float p[3] = {__fadd_rn(o[0], __fmul_rn(t, d[0])), __fadd_rn(o[1], __fmul_rn(t, d[1])),
-                            __fadd_rn(o[2], __fmul_rn(t, d[2]))};
-        const int l = LOD ? lod_level(t, lodscale, bias, nlev) : 0;
-        Resolved R;
-        resolve(s_lv[l], bshift, bmask, row, p, R);
-        return R.pti;
-    };
-    const float ts = __fadd_rn(t0, __fmul_rn((float)k_start, step));
-    const float ps[3] = {__fadd_rn(o[0], __fmul_rn(ts, d[0])), __fadd_rn(o[1], __fmul_rn(ts, d[1])),
-                         __fadd_rn(o[2], __fmul_rn(ts, d[2]))};
-    const int l = LOD ? lod_level(ts, lodscale, bias, nlev) : 0;
-    const LevelDev& L = s_lv[l];
-    Resolved R;
-    resolve(L, bshift, bmask, row, ps, R);
-    float te = t1;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int h = R.i0[a] >> bshift;
-        if (d[a] > 0.0f && h < L.nb[a] - 1) te = fminf(te, (((float)((h + 1) * B) + 0.5f) / L.r[a] - o[a]) / d[a]);
-        else if (d[a] < 0.0f && h > 0) te = fminf(te, (((float)(h * B) + 0.5f) / L.r[a] - o[a]) / d[a]);
-    }
-    if (LOD && l < nlev - 1) te = fminf(te, ldexpf(1.0f, l + 1 - bias) / lodscale);
-    int ke = max(k_start, (int)floorf((te - t0) / step));
-    for (int s = 0; s < 8 && ke > k_start && pti_of(ke) != pti_start; ++s) --ke;
-    if (pti_of(ke) != pti_start) ke = k_start;
-    for (int s = 0; s < 8 && pti_of(ke + 1) == pti_start; ++s) ++ke;
-    return ke;
-}
-
-__device__ __forceinline__ int find_view_tile(const ViewDev* views, int nviews, int item) {
-    int lo = 0, hi = nviews - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (views[mid].tile_off <= item) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int find_view_ray(const ViewDev* views, int nviews, long long ray) {
-    int lo = 0, hi = nviews - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (views[mid].ray_off <= ray) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ uint32_t hash_key(uint32_t x) {
-    x ^= x >> 16;
-    x *= 0x7feb352dU;
-    x ^= x >> 15;
-    x *= 0x846ca68bU;
-    x ^= x >> 16;
-    return x;
-}
-
-// Records a brick request (Sec. III-H): insert key into the open-addressing table with
-// bounded linear probing; a newly inserted key is appended to the request list with one
-// atomic per group of inserting lanes.
-__device__ __forceinline__ void request_brick(const RenderDev& P, uint32_t key) {
-    uint32_t h = hash_key(key) & P.req_cap_mask;
-    int state = 2;  // 0 new, 1 present, 2 overflow
-    for (int probe = 0; probe < kMaxProbe; ++probe) {
-        const uint32_t prev = atomicCAS(&P.req_table[h], 0u, key);
-        if (prev == 0u) { state = 0; break; }
-        if (prev == key) { state = 1; break; }
-        h = (h + 1) & P.req_cap_mask;
-    }
-    if (state == 2) atomicAdd(&P.counters[kReqOverflow], 1u);
-    const unsigned m = __activemask();
-    const unsigned mnew = __ballot_sync(m, state == 0);
-    if (state == 0) {
-        const int leader = __ffs(mnew) - 1;
-        const unsigned lane = threadIdx.x & 31;
-        unsigned base = 0;
-        if ((int)lane == leader) base = atomicAdd(&P.counters[kReqCount], (unsigned)__popc(mnew));
-        base = __shfl_sync(mnew, base, leader);
-        const unsigned pos = base + __popc(mnew & ((1u << lane) - 1));
-        if (pos < P.req_list_cap) P.req_list[pos] = key;
-        else atomicAdd(&P.counters[kReqOverflow], 1u);
-    }
-}
-
-__device__ __forceinline__ void suspend_ray(const RenderDev& P, long long ray, int k, float C0, float C1, float C2,
-                                            float T) {
-    const unsigned m = __activemask();
-    const int leader = __ffs(m) - 1;
-    const unsigned lane = threadIdx.x & 31;
-    unsigned base = 0;
-    if ((int)lane == leader) base = atomicAdd(&P.counters[kSuspCount], (unsigned)__popc(m));
-    base = __shfl_sync(m, base, leader);
-    const unsigned pos = base + __popc(m & ((1u << lane) - 1));
-    if ((long long)pos < P.nrays) {
-        SuspRec r;
-        r.ray = ray;
-        r.k = k;
-        r.pad = 0;
-        r.C[0] = C0;
-        r.C[1] = C1;
-        r.C[2] = C2;
-        r.T = T;
-        P.susp_out[pos] = r;
-    } else {
-        atomicAdd(&P.counters[kDevError], 1u);
-    }
-}
-
-// Samples per lane per loop iteration: their page-table lookups and gathers are issued together,
-// then composited in order (memory-level parallelism along one ray).
-#ifndef VOLRC_BATCH
-#define VOLRC_BATCH 4
-#endif
-constexpr int kBatch = VOLRC_BATCH;
-// Minimum resident CTAs per SM the register allocation must allow.
-#ifndef VOLRC_MIN_CTAS
-#define VOLRC_MIN_CTAS 6
-#endif
-
-__host__ __device__ constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
-
-// BS: brick edge known at compile time (32 or 64), or 0 for any power of two read at run time.
-template <int DT, bool LOD, bool GRAD, int BS, bool Q>
-__global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const __grid_constant__ RenderDev P) {
-    __shared__ float4 s_tf[256];
-    __shared__ float4 s_tfd[255];  // tf[i+1] - tf[i], each difference rounded once
-    __shared__ LevelDev s_lv[kMaxLevels];
-    __shared__ int s_apre[257];  // s_apre[i]: TF entries below i with non-zero opacity
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = P.tf[i];
-    if (threadIdx.x < P.vol.nlevels) s_lv[threadIdx.x] = P.vol.lv[threadIdx.x];
-    __syncthreads();
-    for (int i = threadIdx.x; i < 255; i += blockDim.x) {
-        const float4 a = s_tf[i], b = s_tf[i + 1];
-        s_tfd[i] = make_float4(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y), __fsub_rn(b.z, a.z), __fsub_rn(b.w, a.w));
-    }
-    if (threadIdx.x == 0) {
-        int c = 0;
-        for (int i = 0; i < 256; ++i) {
-            s_apre[i] = c;
-            c += s_tf[i].w != 0.0f;
-        }
-        s_apre[256] = c;
-    }
-    __syncthreads();
-
-    using VT = typename Voxel<DT>::T;
-    const VT* __restrict__ atlas = (const VT*)P.vol.atlas;
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned ltmask = (1u << lane) - 1;
-    const int bshift = BS ? log2i(BS) : P.vol.bshift;
-    const int bmask = BS ? BS - 1 : P.vol.bmask;
-    const int B1 = BS ? BS + 1 : P.vol.B1;
-    const int row = Q ? B1 - 1 : B1;
-    const unsigned long long slot_stride = Q ? P.vol.slot_entries : P.vol.slot_elems;
-    const float step = P.step, et = P.et;
-
-    // warp-uniform work pool
-    int pool_next = 0, pool_cnt = 0, pool_a = 0, pool_x0 = 0, pool_y0 = 0, pool_tile = -1;
-    bool queue_done = false;
-
-    // lane state
-    bool active = false;
-    long long ray = 0;
-    int my_tile = -1;
-    float o0 = 0, o1 = 0, o2 = 0, d0 = 0, d1 = 0, d2 = 0, t0 = 0, t1 = 0, lodscale = 0;
-    int k = 0;
-    float C0 = 0, C1 = 0, C2 = 0, T = 1.0f;
-    uint32_t cur_pti = kInvalidSlot;
-    bool cur_empty = false;  // the brick of cur_pti has zero opacity everywhere
-    const int nlev = P.vol.nlevels;
-    int cur_l = 0;
-    LvReg L = load_lv(s_lv[0]);
-
-    for (;;) {
-        // ---- refill lanes whose ray ended
-        while (!queue_done) {
-            const unsigned need = __ballot_sync(kFull, !active);
-            if (!need) break;
-            if (pool_next >= pool_cnt) {
-                int item = 0;
-                if (lane == 0) item = (int)atomicAdd(&P.counters[kWork], 1u);
-                item = __shfl_sync(kFull, item, 0);
-                if (item >= P.nwork) {
-                    queue_done = true;
-                    break;
-                }
-                if (!P.resume) {
-                    const int tile = P.tile_order ? P.tile_order[item] : item;
-                    const int v = find_view_tile(P.views, P.nviews, tile);
-                    const int tl = tile - P.views[v].tile_off;
-                    const int tx = P.views[v].tiles_x;
-                    pool_tile = tile;
-                    pool_a = v;
-                    pool_x0 = (tl % tx) * P.tile_w;
-                    pool_y0 = (tl / tx) * P.tile_h;
-                    pool_cnt = P.tile_w * P.tile_h;
-                } else {
-                    pool_tile = -1;
-                    pool_a = item * 32;
-                    pool_cnt = min(32, P.nsusp_in - item * 32);
-                }
-                pool_next = 0;
-            }
-            const int idx = pool_next + __popc(need & ltmask);
-            pool_next = min(pool_cnt, pool_next + __popc(need));
-            if (!active && idx < pool_cnt) {
-                int view, px, py, k0 = 0;
-                float c0 = 0.f, c1 = 0.f, c2 = 0.f, tt = 1.0f;
-                bool ok;
-                if (!P.resume) {
-                    view = pool_a;
-                    px = pool_x0 + idx % P.tile_w;
-                    py = pool_y0 + idx / P.tile_w;
-                    ok = px < P.views[view].w && py < P.views[view].h;
-                    ray = P.views[view].ray_off + (long long)py * P.views[view].w + px;
-                } else {
-                    const SuspRec r = P.susp_in[pool_a + idx];
-                    ray = r.ray;
-                    k0 = r.k;
-                    c0 = r.C[0];
-                    c1 = r.C[1];
-                    c2 = r.C[2];
-                    tt = r.T;
-                    view = find_view_ray(P.views, P.nviews, ray);
-                    const long long loc = ray - P.views[view].ray_off;
-                    px = (int)(loc % P.views[view].w);
-                    py = (int)(loc / P.views[view].w);
-                    ok = true;
-                }
-                my_tile = pool_tile;
-                if (ok) {
-                    Ray R;
-                    make_ray(P.views[view], P.vol.D0f, px, py, R);
-                    if (R.hit) {
-                        active = true;
-                        o0 = R.o[0]; o1 = R.o[1]; o2 = R.o[2];
-                        d0 = R.d[0]; d1 = R.d[1]; d2 = R.d[2];
-                        t0 = R.t0; t1 = R.t1;
-                        lodscale = P.views[view].lodscale;
-                        k = k0; C0 = c0; C1 = c1; C2 = c2; T = tt;
-                        cur_pti = kInvalidSlot;
-                    } else {
-                        P.out[ray] = P.bg;
-                        if (P.nsamp) P.nsamp[ray] = 0;
-                        if (GRAD) P.ray_n[ray] = 0;
-                    }
-                }
-            }
-        }
-        unsigned act = __ballot_sync(kFull, active);
-        if (!act) break;
-
-        // ---- march: per iteration up to kBatch samples of each active ray
-        const int thresh = queue_done ? 1 : P.refill_thresh;
-        do {
-            if (active) {
-                // (a) decisions for the batch (ALU only)
-                uint32_t pti[kBatch], loc[kBatch];
-                float wgt[kBatch][3];
-                int nvalid = kBatch;
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const float t = __fadd_rn(t0, __fmul_rn((float)(k + j), step));
-                    if (!(t < t1) && nvalid == kBatch) nvalid = j;
-                    const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
-                                        __fadd_rn(o2, __fmul_rn(t, d2))};
-                    if (LOD) {
-                        const int l = lod_level(t, lodscale, P.lod_bias, nlev);
-                        if (l != cur_l) {
-                            cur_l = l;
-                            L = load_lv(s_lv[l]);
-                        }
-                    }
-                    Resolved R;
-                    resolve_reg(L, bshift, bmask, row, p, R);
-                    pti[j] = R.pti;
-                    loc[j] = R.local;
-                    wgt[j][0] = R.w[0];
-                    wgt[j][1] = R.w[1];
-                    wgt[j][2] = R.w[2];
-                }
-                // (b) page-table lookups, all issued together (samples past the exit read entry 0)
-                uint32_t slot[kBatch];
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) slot[j] = __ldg(P.vol.pt + (j < nvalid ? pti[j] : 0u));
-                int miss_at = kBatch;
-#pragma unroll
-                for (int j = kBatch - 1; j >= 0; --j)
-                    if (j < nvalid && slot[j] == kInvalidSlot) miss_at = j;
-                const uint32_t miss_pti = miss_at < kBatch ? pti[miss_at] : 0u;
-                // usage stamps (one store per brick change) and empty-brick test
-                int empty_at = kBatch;
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    if (j < nvalid && j < miss_at) {
-                        if (pti[j] != cur_pti) {
-                            cur_pti = pti[j];
-                            if (P.last_used) P.last_used[slot[j]] = P.frame;
-                            if (P.skip_empty) cur_empty = brick_empty<DT>(__ldg(P.vol.range + slot[j]), s_apre);
-                        }
-                        if (cur_empty && empty_at == kBatch) empty_at = j;
-                    }
-                }
-                // (c) gathers, all issued together (unused samples read slot 0, element 0)
-                float val[kBatch];
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const bool use = j < nvalid && j < miss_at;
-                    const unsigned long long base = use ? (unsigned long long)slot[j] * slot_stride + loc[j] : 0ull;
-                    val[j] = sample_value<DT, BS, Q>(P.vol.atlas, base, B1, wgt[j]);
-                }
-                const int stop = min(min(nvalid, miss_at), empty_at);
-                bool fin = false;
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    if (j < stop && !fin) {
-                        if (GRAD && k > 0 && (k & (kCkptEvery - 1)) == 0)
-                            P.ckpt[(long long)(k / kCkptEvery - 1) * P.nrays + ray] = T;
-                        const float x = tf_coord<DT>(val[j]);
-                        const int i = min((int)x, 254);
-                        const float wt = x - (float)i;
-                        const float4 a = s_tf[i], dab = s_tfd[i];  // entry i and tf[i+1] - tf[i]
-                        const float al = fmaf(wt, dab.w, a.w);
-                        const float Ta = T * al;
-                        C0 = fmaf(Ta, fmaf(wt, dab.x, a.x), C0);
-                        C1 = fmaf(Ta, fmaf(wt, dab.y, a.y), C1);
-                        C2 = fmaf(Ta, fmaf(wt, dab.z, a.z), C2);
-                        T = T * (1.0f - al);
-                        ++k;
-                        if (__fsub_rn(1.0f, T) >= et) fin = true;
-                    }
-                }
-                if (!fin && nvalid < kBatch && nvalid <= miss_at && nvalid <= empty_at) fin = true;  // left the volume
-                if (!fin && empty_at < kBatch && empty_at < miss_at && empty_at < nvalid) {
-                    // sample k is in a brick of zero opacity: every sample up to the brick's last
-                    // composites nothing, so continue after it
-                    const float o3[3] = {o0, o1, o2}, d3[3] = {d0, d1, d2};
-                    const int klast = brick_last_sample<LOD>(k, pti[empty_at], o3, d3, t0, t1, step, lodscale,
-                                                             P.lod_bias, nlev, s_lv, bshift, bmask, row, B1 - 1);
-                    if (GRAD)
-                        for (int kk = ((k + kCkptEvery - 1) / kCkptEvery) * kCkptEvery; kk <= klast; kk += kCkptEvery)
-                            if (kk > 0) P.ckpt[(long long)(kk / kCkptEvery - 1) * P.nrays + ray] = T;
-                    k = klast + 1;
-                } else if (fin) {
-                    const float4 bg = P.bg;
-                    P.out[ray] = make_float4(fmaf(T, bg.x, C0), fmaf(T, bg.y, C1), fmaf(T, bg.z, C2),
-                                             fmaf(T, bg.w, 1.0f - T));
-                    if (P.nsamp) P.nsamp[ray] = k;
-                    if (GRAD) P.ray_n[ray] = k;
-                    if (P.tile_cost && my_tile >= 0) atomicAdd(&P.tile_cost[my_tile], k);
-                    active = false;
-                } else if (miss_at < kBatch) {
-                    // wait for the missing brick: sample k (= the first missing one) resumes later
-                    if (P.req_table) {
-                        request_brick(P, miss_pti + 1u);
-                        suspend_ray(P, ray, k, C0, C1, C2, T);
-                    } else {
-                        atomicAdd(&P.counters[kDevError], 1u);
-                    }
-                    active = false;
-                }
-            }
-            act = __ballot_sync(kFull, active);
-        } while (__popc(act) >= thresh);
-    }
-}
 
 // ------------------------------------------------------------------ adjoint
 
@@ -946,8 +307,8 @@ __global__ void k_trace(const __grid_constant__ TraceDev P) {
 
 template <int DT, int BS, bool Q>
 const void* pick_render_b(bool lod, bool grad) {
-    if (grad) return (const void*)k_render<DT, false, true, BS, Q>;
-    return lod ? (const void*)k_render<DT, true, false, BS, Q> : (const void*)k_render<DT, false, false, BS, Q>;
+    if (grad) return (const void*)k_render<DT, false, kDvrGrad, BS, Q>;
+    return lod ? (const void*)k_render<DT, true, kDvr, BS, Q> : (const void*)k_render<DT, false, kDvr, BS, Q>;
 }
 
 // quad layout: specialised for bricks of 32 and 64; compact layout: any brick size
@@ -981,8 +342,10 @@ const void* pick_backward(int dtype) {
 
 }  // namespace
 
-cudaError_t launch_render(int dtype, bool grad, const RenderDev& p, int grid, cudaStream_t s) {
-    const void* fn = pick_render(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0, grad);
+cudaError_t launch_render(int dtype, int mode, const RenderDev& p, int grid, cudaStream_t s) {
+    const void* fn = (mode == kMop || mode == kMip)
+                         ? pick_render_projection(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0, mode)
+                         : pick_render(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0, mode == kDvrGrad);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&p};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kRenderThreads), args, 0, s);

@@ -342,6 +342,13 @@ int ensure_miss_buffers(vol_t v) {
     return VOL_OK;
 }
 
+int render_mode(const vol_params& p, bool grad) {
+    if (grad) return kDvrGrad;
+    if (p.composite == VOL_COMPOSITE_MOP) return kMop;
+    if (p.composite == VOL_COMPOSITE_MIP) return kMip;
+    return kDvr;
+}
+
 RenderDev render_args(vol_t v) {
     RenderDev p{};
     p.vol = vol_dev(v);
@@ -395,7 +402,7 @@ int run_pass(vol_t v, bool resume, bool may_miss) {
     p.tile_cost = v->tile_cost;
     CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
     const int grid = grid_for(v, v->dtype, v->grad, v->params.ctas_per_sm);
-    CK(v, launch_render(v->dtype, v->grad, p, grid, v->stream));
+    CK(v, launch_render(v->dtype, render_mode(v->params, v->grad), p, grid, v->stream));
     v->stats.passes++;
     return VOL_OK;
 }
@@ -789,8 +796,12 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be at most 4096");
     if (p.refill <= 0 || p.refill > 32) p.refill = 20;
     if (p.lod_mode != 0 && p.lod_mode != 1) return fail(v, VOL_ERR_INVALID_ARG, "lod_mode must be 0 or 1");
+    if (p.composite < VOL_COMPOSITE_DVR || p.composite > VOL_COMPOSITE_MIP)
+        return fail(v, VOL_ERR_INVALID_ARG, "composite must be VOL_COMPOSITE_DVR, _MOP or _MIP");
     const bool grad = (p.flags & VOL_RENDER_GRAD) != 0;
     if (grad && p.lod_mode != 0) return fail(v, VOL_ERR_UNSUPPORTED, "gradients need lod_mode 0");
+    if (grad && p.composite != VOL_COMPOSITE_DVR)
+        return fail(v, VOL_ERR_UNSUPPORTED, "gradients need emission/absorption compositing");
 
     // view table
     v->views_host.resize(nviews);
@@ -1054,6 +1065,8 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
         return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be at most 4096");
     if (p.refill <= 0 || p.refill > 32) p.refill = 20;
     if (p.lod_mode != 0 && p.lod_mode != 1) return fail(v, VOL_ERR_INVALID_ARG, "lod_mode must be 0 or 1");
+    if (p.composite < VOL_COMPOSITE_DVR || p.composite > VOL_COMPOSITE_MIP)
+        return fail(v, VOL_ERR_INVALID_ARG, "composite must be VOL_COMPOSITE_DVR, _MOP or _MIP");
     if (p.flags & VOL_RENDER_GRAD)
         return fail(v, VOL_ERR_UNSUPPORTED, "vol_render_noalloc keeps no gradient state; use vol_render");
     if (!all_resident(v, p.lod_mode != 0))
@@ -1108,11 +1121,12 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
     r.bg = make_float4(p.bg[0], p.bg[1], p.bg[2], p.bg[3]);
     r.lod_mode = p.lod_mode;
     r.lod_bias = p.lod_bias;
+    r.skip_empty = (p.flags & VOL_RENDER_SKIP_EMPTY) ? 1 : 0;
     r.out = (float4*)rgba_dev;
     r.nsamp = nsamples_dev;
     r.counters = counters;
     r.nrays = rays;  // no request table, no suspension buffers, no usage stamps, no checkpoints
     const int grid = grid_for(v, v->dtype, false, p.ctas_per_sm);
-    CK(v, launch_render(v->dtype, false, r, grid, v->stream));
+    CK(v, launch_render(v->dtype, render_mode(p, false), r, grid, v->stream));
     return VOL_OK;
 }

@@ -30,7 +30,7 @@ def camera_struct(cam: dict) -> C.vol_camera:
 
 
 def params_struct(step=0.5, et=0.99, bg=(0.0, 0.0, 0.0, 0.0), lod_mode=0, lod_bias=0, tile_w=0, tile_h=0,
-                  max_passes=0, flags=0, refill=0, ctas_per_sm=0, grad=False) -> C.vol_params:
+                  max_passes=0, flags=0, refill=0, ctas_per_sm=0, composite="dvr", grad=False) -> C.vol_params:
     p = C.vol_params()
     p.step, p.et_threshold = float(np.float32(step)), float(np.float32(et))
     p.bg[:] = [float(np.float32(b)) for b in bg]
@@ -38,6 +38,7 @@ def params_struct(step=0.5, et=0.99, bg=(0.0, 0.0, 0.0, 0.0), lod_mode=0, lod_bi
     p.tile_w, p.tile_h, p.max_passes = int(tile_w), int(tile_h), int(max_passes)
     p.flags = int(flags) | (C.VOL_RENDER_GRAD if grad else 0)
     p.refill, p.ctas_per_sm = int(refill), int(ctas_per_sm)
+    p.composite = C.COMPOSITES[composite] if isinstance(composite, str) else int(composite)
     return p
 
 

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes_match_header(lib):
     # sizes follow from the field lists in vol.h (natural alignment)
     assert ctypes.sizeof(lib.vol_camera) == 4 * 14 + 8
-    assert ctypes.sizeof(lib.vol_params) == 4 * 2 + 16 + 4 * 8
+    assert ctypes.sizeof(lib.vol_params) == 4 * 2 + 16 + 4 * 9
     assert ctypes.sizeof(lib.vol_trace_rec) == 56
 
 
