@@ -274,11 +274,13 @@ __device__ __forceinline__ bool entry_span(float x0, float x1, int& i0, int& i1)
 }
 
 // A brick whose stored values lie in [rng.x, rng.y] has zero opacity at every sample when no
-// TF entry that a lookup in that range can touch has non-zero alpha.
+// TF entry that a lookup in that range can touch (the same margin as entry_span) has non-zero
+// alpha.  tf_coord maps every stored value (floats clamped, +-inf included) into [0, 255], so
+// the indices stay within 0..256 even for the unordered range (+inf, -inf) of an all-NaN slot.
 template <int DT>
 __device__ __forceinline__ bool brick_empty(float2 rng, const int* s_apre) {
-    int ilo, ihi;
-    if (!entry_span(tf_coord<DT>(rng.x), tf_coord<DT>(rng.y), ilo, ihi)) return false;
+    const float xlo = tf_coord<DT>(rng.x), xhi = tf_coord<DT>(rng.y);
+    const int ilo = max((int)xlo - 1, 0), ihi = min((int)xhi + 2, 255);
     return s_apre[ihi + 1] - s_apre[ilo] == 0;
 }
 
