@@ -306,6 +306,7 @@ def run_ours(args, dist, rank, ws, local):
         wall0 = time.perf_counter()
         ms = time_frames(torch, vol, cams, tf, params, args.steps, args.warmup, flush)
         wall = time.perf_counter() - wall0
+    launches_per_frame = vol.stats()["launches"]  # library kernels of one render (the last timed one)
     clocks = clk.summary()
     t_mean = statistics.mean(ms)
     t_step = max_over_ranks(dist, t_mean)
@@ -423,7 +424,7 @@ def run_ours(args, dist, rank, ws, local):
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": 4096,
                     "d2h_bytes_per_step": npx * 16, "ms_per_step": e2e_step},
             # per step: the render kernel and the two heaviest-first scheduling kernels
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": launches_per_frame * args.steps,
             "clocks": clocks,
             "wall_s_timed": wall,
             "variants": variants,
@@ -454,21 +455,40 @@ def run_outofcore(args, dist, rank, ws, local):
     cams = wl["cams"]
     if ws > 1:
         cams = cams[rank::ws] * ws
-    frames = []
-    barrier(dist)
-    with Clocks(local) as clk:
-        for i, cam in enumerate(cams):
+    def flythrough(v, p):
+        fr = []
+        for cam in cams:
             torch.cuda.synchronize()
             t = time.perf_counter()
-            out, ns = vol.render(cam, tf, params, nsamples=True)
+            out, ns = v.render(cam, tf, p, nsamples=True)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t
-            st = vol.stats()
-            frames.append({"ms": 1e3 * dt, "samples": int(ns.sum().item()), "passes": st["passes"],
-                           "bricks_loaded": st["bricks_loaded"], "bytes_loaded": st["bytes_loaded"],
-                           "evicted": st["evicted"], "resident": st["resident"], "touched": st["touched"]})
+            st = v.stats()
+            fr.append({"ms": 1e3 * dt, "samples": int(ns.sum().item()), "passes": st["passes"],
+                       "bricks_loaded": st["bricks_loaded"], "bytes_loaded": st["bytes_loaded"],
+                       "evicted": st["evicted"], "resident": st["resident"], "touched": st["touched"],
+                       "load_wait_ms": st["load_wait_us"] * 1e-3, "launches": st["launches"]})
+        return fr
+
+    barrier(dist)
+    with Clocks(local) as clk:
+        frames = flythrough(vol, params)
     clocks = clk.summary()
+    vol.close()
     steady = frames[10:] if len(frames) > 10 else frames
+    variants = {}
+    if not args.quick:
+        # the same fly-through, cold cache: loading between passes only (no overlap), and with
+        # empty-space skipping
+        for name, flags in (("serial_loads", 4), ("skip_empty", 2)):
+            v2 = P.Volume(wl["D"], "u8", wl["brick"], wl["levels"], cache_bytes=wl["cache_bytes"], layout="compact")
+            v2.set_provider_batch(synth.brick_provider_address(), src, "u8")
+            fr2 = flythrough(v2, dict(params, flags=flags))
+            v2.close()
+            st2 = fr2[10:] if len(fr2) > 10 else fr2
+            variants[name] = {"ms_per_frame": statistics.mean(f["ms"] for f in st2), "first_frame_ms": fr2[0]["ms"],
+                              "load_wait_ms_per_frame": statistics.mean(f["load_wait_ms"] for f in st2),
+                              "passes_per_frame": statistics.mean(f["passes"] for f in st2)}
     ms = statistics.mean(f["ms"] for f in steady)
     samples = statistics.mean(f["samples"] for f in steady)
     t_step = max_over_ranks(dist, ms)
@@ -484,13 +504,15 @@ def run_outofcore(args, dist, rank, ws, local):
             "steady_state": {"ms_per_frame": ms,
                              "miss_bytes_per_frame": statistics.mean(f["bytes_loaded"] for f in steady),
                              "bricks_loaded_per_frame": statistics.mean(f["bricks_loaded"] for f in steady),
-                             "passes_per_frame": statistics.mean(f["passes"] for f in steady)},
+                             "passes_per_frame": statistics.mean(f["passes"] for f in steady),
+                             "load_wait_ms_per_frame": statistics.mean(f["load_wait_ms"] for f in steady),
+                             "first_frame_ms": frames[0]["ms"]},
+            "variants": variants,
             "frames": frames,
             "clocks": clocks,
-            "gpu_launches": None,
+            "gpu_launches": sum(f["launches"] for f in steady),
         }
         print(json.dumps(line), flush=True)
-    vol.close()
 
 
 def cpu_baseline(wl, raw, seconds):

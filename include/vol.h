@@ -76,6 +76,13 @@ typedef struct {
  * to the brick's last sample.  Those samples would composite nothing (alpha exactly 0), so
  * the image and the per-pixel sample counts are identical with or without it. */
 #define VOL_RENDER_SKIP_EMPTY 2u
+/* With a batch provider, vol_render overlaps brick loading with rendering: while a pass
+ * runs, the requests it appends are read and a library thread runs the provider on chunks
+ * of them (one call at a time, from that thread) into a pinned host ring, from which queued
+ * kernels upload the bricks after the pass; the next pass resumes the rays.  This flag
+ * loads all requested bricks between passes instead, on the calling thread.  The image is
+ * the same either way. */
+#define VOL_RENDER_SERIAL_LOADS 4u
 
 /* Compositing (vol_params.composite).
  * VOL_COMPOSITE_DVR: front-to-back emission/absorption with early termination (Sec. IV-A).
@@ -103,7 +110,7 @@ typedef struct {
     int32_t lod_bias;    /* added to the footprint level before clamping to [0, L-1] */
     int32_t tile_w;      /* ray tile (work item) width in pixels; 0 = default 4 */
     int32_t tile_h;      /* ray tile height (tile_w * tile_h <= 4096); 0 = 8 */
-    int32_t max_passes;  /* miss/refill passes per render when a provider is set; 0 = 64 */
+    int32_t max_passes;  /* miss/refill passes per render when a provider is set; 0 = 256 */
     uint32_t flags;      /* VOL_RENDER_* bits */
     int32_t refill;      /* a warp fetches new rays once fewer lanes than this are busy
                             (1..32; 0 = default 20); performance only, never the image */
@@ -151,6 +158,8 @@ typedef struct {
     int64_t frame;           /* frame counter (one per vol_render) */
     int64_t device_error;    /* device-side check failures (0 expected) */
     int64_t touched;         /* distinct bricks the last render sampled (usage stamps) */
+    int64_t load_wait_us;    /* host time the last render spent waiting for the provider (us) */
+    int64_t launches;        /* kernels the library launched since the last render began */
 } vol_stats;
 
 /* Provider of bricks that are not resident (procedural or out-of-core source).

@@ -6,12 +6,18 @@
 // used eviction policy driven by per-slot usage stamps written by the render kernel
 // (Sec. III-C/III-E: garbage collection frees down to a 10% target), the brick-request loop
 // (Sec. III-H), and the buffers of the last render needed by the adjoint.
+#include <sched.h>
+
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.cuh"
@@ -21,6 +27,18 @@ using namespace volrc;
 namespace {
 
 thread_local std::string g_create_error;
+
+// Cores this process may run on (its affinity mask), at least 1.
+int host_cores() {
+    cpu_set_t set;
+    if (sched_getaffinity(0, sizeof(set), &set) == 0) return std::max(1, CPU_COUNT(&set));
+    return (int)std::max(1u, std::thread::hardware_concurrency());
+}
+
+int64_t now_us() {
+    return std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
 
 int bpv_of(int dtype) {
     switch (dtype) {
@@ -97,6 +115,8 @@ struct vol_s {
     std::vector<uint32_t> pt_host;    // page tables (mirror)
     std::vector<uint32_t> owner;      // slot -> page-table index or invalid
     std::vector<uint32_t> protect;    // slot -> operation epoch that must not evict it
+    std::vector<uint8_t> reserved;    // slot -> 1 while a brick is being generated into it
+    std::vector<uint8_t> queued;      // page-table index -> 1 while waiting for or in generation
     std::vector<uint32_t> free_slots; // stack
     uint32_t op_epoch = 1;
     int64_t resident = 0;
@@ -148,6 +168,38 @@ struct vol_s {
     void* stage_dev = nullptr;
     uint32_t* stage_slots_dev = nullptr;
     int stage_bricks = 0;
+    // overlapped loading: a pinned host ring the batch provider fills and the upload kernels
+    // read directly, a stream for reading the request list while a pass runs, and one worker
+    // thread that runs the provider
+    struct Ring {
+        char* host = nullptr;        // cap bricks of `brick_bytes` (source type), pinned, mapped
+        uint32_t* slots = nullptr;   // cap: slot of each ring entry (pinned, mapped)
+        uint32_t* ptis = nullptr;    // cap: page-table index of each ring entry (pinned, mapped)
+        char* host_dev = nullptr;    // device-side addresses of the three arrays
+        uint32_t* slots_dev = nullptr;
+        uint32_t* ptis_dev = nullptr;
+        int cap = 0;
+        size_t brick_bytes = 0;
+        int head = 0, used = 0;      // next free entry; entries in use (gaps at the wrap included)
+        struct Region {
+            int start, n, gap;
+            cudaEvent_t ev;          // recorded after the region's upload kernels
+        };
+        std::deque<Region> inflight;
+        std::vector<cudaEvent_t> spare;
+    } ring;
+    cudaStream_t poll_stream = nullptr;
+    uint32_t* poll_host = nullptr;   // pinned: request count, then request keys
+    cudaEvent_t ev_pass_start = nullptr, ev_pass_end = nullptr;  // around each pass's launch
+    struct Loader {
+        std::thread th;
+        std::mutex m;
+        std::condition_variable cv;
+        bool quit = false, job = false, done = true;
+        int n = 0, rc = 0;
+        const int32_t* coords = nullptr;
+        void* dst = nullptr;
+    } loader;
 
     // heaviest-first scheduling from the previous frame's per-tile sample counts
     int* tile_cost = nullptr;
@@ -237,6 +289,7 @@ int flush_pt_updates(vol_t v) {
     std::copy(v->upd_val.begin(), v->upd_val.end(), packed.begin() + n);
     CK(v, cudaMemcpyAsync(v->upd_dev, packed.data(), sizeof(uint32_t) * 2 * n, cudaMemcpyHostToDevice, v->stream));
     CK(v, launch_pt_update(v->pt, v->upd_dev, v->upd_dev + n, (int)n, v->stream));
+    v->stats.launches += 1;
     v->upd_idx.clear();
     v->upd_val.clear();
     return VOL_OK;
@@ -264,7 +317,7 @@ int evict_lru(vol_t v, size_t need) {
     std::vector<uint32_t> cand;
     cand.reserve(ns);
     for (int64_t s = 0; s < ns; ++s)
-        if (v->owner[s] != kInvalidSlot && v->protect[s] != v->op_epoch) cand.push_back((uint32_t)s);
+        if (v->owner[s] != kInvalidSlot && v->protect[s] != v->op_epoch && !v->reserved[s]) cand.push_back((uint32_t)s);
     // age order: older frames first; the current frame last
     std::stable_sort(cand.begin(), cand.end(), [&](uint32_t a, uint32_t b) {
         const uint32_t fa = stamp[a] == v->frame ? 0xFFFFFFFFu : stamp[a];
@@ -386,6 +439,7 @@ int run_pass(vol_t v, bool resume, bool may_miss) {
         p.req_list = v->req_list;
         p.req_list_cap = v->req_list_cap;
         CK(v, cudaMemsetAsync(v->req_table, 0, sizeof(unsigned) * v->req_cap, v->stream));
+        CK(v, cudaMemsetAsync(v->req_list, 0, sizeof(unsigned) * v->req_list_cap, v->stream));
     }
     if (resume) {
         p.resume = 1;
@@ -402,7 +456,10 @@ int run_pass(vol_t v, bool resume, bool may_miss) {
     p.tile_cost = v->tile_cost;
     CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
     const int grid = grid_for(v, v->dtype, v->grad, v->params.ctas_per_sm);
+    if (v->ev_pass_start) CK(v, cudaEventRecord(v->ev_pass_start, v->stream));
     CK(v, launch_render(v->dtype, render_mode(v->params, v->grad), p, grid, v->stream));
+    if (v->ev_pass_end) CK(v, cudaEventRecord(v->ev_pass_end, v->stream));
+    v->stats.launches += 1;
     v->stats.passes++;
     return VOL_OK;
 }
@@ -484,6 +541,7 @@ int load_requests(vol_t v) {
         const size_t n = slots.size();
         if (!n) break;
         // fill the pinned stage from the source
+        const int64_t t_prov = now_us();
         if (v->prov_batch) {
             if (v->prov_batch(v->prov_user, (int)n, batch.data(), v->stage_host) != 0)
                 return fail(v, VOL_ERR_PROVIDER, "brick provider failed");
@@ -492,6 +550,7 @@ int load_requests(vol_t v) {
                 if (v->prov(v->prov_user, batch[4 * j], &batch[4 * j + 1], (char*)v->stage_host + j * src_bytes) != 0)
                     return fail(v, VOL_ERR_PROVIDER, "brick provider failed");
         }
+        v->stats.load_wait_us += now_us() - t_prov;
         v->stats.bricks_loaded += (int64_t)n;
         v->stats.bytes_loaded += (int64_t)(n * src_bytes);
         CK(v, cudaMemcpyAsync(v->stage_dev, v->stage_host, src_bytes * n, cudaMemcpyHostToDevice, v->stream));
@@ -499,16 +558,360 @@ int load_requests(vol_t v) {
         CK(v, launch_upload_bricks(v->dtype, v->prov_dtype, v->stage_dev, vol_dev(v), v->stage_slots_dev, (long long)n,
                                    v->stream));
         CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, v->stage_slots_dev, (long long)n, v->stream));
+        v->stats.launches += 2;
         if (int rc = flush_pt_updates(v)) return rc;
         CK(v, cudaStreamSynchronize(v->stream));  // the pinned stage is reused by the next batch
     }
     return VOL_OK;
 }
 
+// ---- overlapped loading (batch provider) ----------------------------------------------
+//
+// The paper interleaves brick loading with rendering (Sec. III-H; Sec. V-A: raycaster tasks
+// keep running while chunks load).  Here:
+//  * while a pass runs, the host reads the brick requests the kernel appends (a copy on a
+//    separate non-blocking stream) and hands them to one library thread that runs the batch
+//    provider into a pinned, device-mapped host ring;
+//  * a finished chunk is published without a blocking copy: its upload, value-range and
+//    page-table kernels read the ring directly and are queued on the volume's stream behind
+//    the pass in flight;
+//  * the next pass starts once at least half of the bricks known to be missing are published.
+// A page-table entry is inserted by a kernel queued after its brick's upload, so no pass ever
+// samples a slot that is being filled.
+
+void loader_main(vol_t v) {
+    auto& L = v->loader;
+    std::unique_lock<std::mutex> lk(L.m);
+    for (;;) {
+        L.cv.wait(lk, [&] { return L.quit || L.job; });
+        if (L.quit) return;
+        L.job = false;
+        const int n = L.n;
+        const int32_t* coords = L.coords;
+        void* dst = L.dst;
+        lk.unlock();
+        const int rc = v->prov_batch(v->prov_user, n, coords, dst);
+        lk.lock();
+        L.rc = rc;
+        L.done = true;
+        L.cv.notify_all();
+    }
+}
+
+int loader_submit(vol_t v, int n, const int32_t* coords, void* dst) {
+    auto& L = v->loader;
+    if (!L.th.joinable()) {
+        try {
+            L.th = std::thread(loader_main, v);
+        } catch (...) {
+            return fail(v, VOL_ERR_UNSUPPORTED, "cannot start the brick loader thread");
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(L.m);
+        L.n = n;
+        L.coords = coords;
+        L.dst = dst;
+        L.done = false;
+        L.job = true;
+    }
+    L.cv.notify_all();
+    return VOL_OK;
+}
+
+bool loader_done(vol_t v) {
+    std::lock_guard<std::mutex> lk(v->loader.m);
+    return v->loader.done;
+}
+
+int loader_wait(vol_t v) {
+    auto& L = v->loader;
+    const int64_t t = now_us();
+    std::unique_lock<std::mutex> lk(L.m);
+    L.cv.wait(lk, [&] { return L.done; });
+    v->stats.load_wait_us += now_us() - t;
+    return L.rc;
+}
+
+void ring_reclaim(vol_t v) {
+    auto& R = v->ring;
+    while (!R.inflight.empty() && cudaEventQuery(R.inflight.front().ev) == cudaSuccess) {
+        R.used -= R.inflight.front().n + R.inflight.front().gap;
+        R.spare.push_back(R.inflight.front().ev);
+        R.inflight.pop_front();
+    }
+}
+
+// Ring buffers, the polling stream and the pass events; called before the first pass of a
+// render whose misses will load through the overlapped path.
+int ensure_overlap(vol_t v) {
+    auto& R = v->ring;
+    const int64_t B1 = v->B + 1;
+    const size_t bb = (size_t)(B1 * B1 * B1) * bpv_of(v->prov_dtype);
+    if (!v->poll_stream) CK(v, cudaStreamCreateWithFlags(&v->poll_stream, cudaStreamNonBlocking));
+    if (!v->poll_host)
+        CK(v, cudaHostAlloc((void**)&v->poll_host, sizeof(uint32_t) * ((size_t)v->req_list_cap + 1), cudaHostAllocDefault));
+    for (cudaEvent_t* e : {&v->ev_pass_start, &v->ev_pass_end})
+        if (!*e) CK(v, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    if (R.host && R.brick_bytes == bb) return VOL_OK;
+    // (re)size for this provider's source type: nothing of the old ring may be in flight
+    CK(v, cudaStreamSynchronize(v->stream));
+    ring_reclaim(v);
+    for (void* b : {(void*)R.host, (void*)R.slots, (void*)R.ptis})
+        if (b) cudaFreeHost(b);
+    R.host = nullptr;
+    R.slots = R.ptis = nullptr;
+    R.brick_bytes = bb;
+    R.cap = (int)std::max<size_t>(64, std::min<size_t>(65536, (size_t(1) << 30) / bb));
+    const unsigned fl = cudaHostAllocMapped | cudaHostAllocPortable;
+    CK(v, cudaHostAlloc((void**)&R.host, bb * R.cap, fl));
+    CK(v, cudaHostAlloc((void**)&R.slots, sizeof(uint32_t) * R.cap, fl));
+    CK(v, cudaHostAlloc((void**)&R.ptis, sizeof(uint32_t) * R.cap, fl));
+    CK(v, cudaHostGetDevicePointer((void**)&R.host_dev, R.host, 0));
+    CK(v, cudaHostGetDevicePointer((void**)&R.slots_dev, R.slots, 0));
+    CK(v, cudaHostGetDevicePointer((void**)&R.ptis_dev, R.ptis, 0));
+    R.head = R.used = 0;
+    return VOL_OK;
+}
+
+// n contiguous ring entries (wrapping to the start when the tail is too short), or -1 when
+// the ring has no room until earlier uploads complete.
+int ring_alloc(vol_t v, int n, int* gap) {
+    auto& R = v->ring;
+    ring_reclaim(v);
+    const int g = R.head + n > R.cap ? R.cap - R.head : 0;
+    if (n > R.cap || R.used + g + n > R.cap) return -1;
+    const int start = g ? 0 : R.head;
+    R.head = start + n == R.cap ? 0 : start + n;
+    R.used += g + n;
+    *gap = g;
+    return start;
+}
+
+void ring_unalloc(vol_t v, int start, int n, int gap) {  // undo the newest allocation
+    auto& R = v->ring;
+    R.head = gap ? R.cap - gap : start;
+    R.used -= n + gap;
+}
+
+// Mirror-only page-table insert (the device entry is written by a queued kernel).
+void mirror_entry(vol_t v, uint32_t pti, uint32_t slot) {
+    const uint32_t old = v->pt_host[pti];
+    const int l = level_of_pti(v, pti);
+    if (old == kInvalidSlot && slot != kInvalidSlot) { ++v->resident; ++v->level_resident[l]; }
+    if (old != kInvalidSlot && slot == kInvalidSlot) { --v->resident; --v->level_resident[l]; }
+    v->pt_host[pti] = slot;
+}
+
+struct LoadJob {
+    int start = 0, nalloc = 0, gap = 0, n = 0;  // ring region, bricks in it
+    std::vector<int32_t> coords;                 // [n][4] level, bx, by, bz
+};
+
+// New request keys of the pass in flight: its count word, then the keys past `seen` that the
+// kernel has stored (keys are non-zero; a zero is a reserved place not yet written, read again
+// at the next poll).
+int poll_live(vol_t v, uint32_t& seen, std::vector<uint32_t>& out) {
+    CK(v, cudaMemcpyAsync(v->poll_host, v->counters + kReqCount, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                          v->poll_stream));
+    CK(v, cudaStreamSynchronize(v->poll_stream));
+    const uint32_t cnt = std::min<uint32_t>(v->poll_host[0], v->req_list_cap);
+    if (cnt <= seen) return VOL_OK;
+    CK(v, cudaMemcpyAsync(v->poll_host + 1, v->req_list + seen, sizeof(uint32_t) * (cnt - seen),
+                          cudaMemcpyDeviceToHost, v->poll_stream));
+    CK(v, cudaStreamSynchronize(v->poll_stream));
+    uint32_t i = 0;
+    for (; i < cnt - seen && v->poll_host[1 + i] != 0u; ++i) out.push_back(v->poll_host[1 + i]);
+    seen += i;
+    return VOL_OK;
+}
+
+int miss_loop_overlapped(vol_t v) {
+    auto& R = v->ring;
+    const size_t bb = R.brick_bytes;
+    const int max_passes = v->params.max_passes > 0 ? v->params.max_passes : 256;
+    const size_t min_chunk = std::min<size_t>(64, 2 * (size_t)host_cores());  // bricks for every host core
+    const size_t max_chunk = std::max<size_t>(min_chunk, std::min<size_t>(512, (size_t)R.cap / 4));
+    ++v->op_epoch;
+    std::deque<uint32_t> pending;
+    std::vector<uint32_t> keys;
+    auto take = [&](const std::vector<uint32_t>& ks) -> int {
+        // coarse levels first: one coarse brick serves the rays of many fine ones
+        std::vector<uint32_t> fresh;
+        for (const uint32_t key : ks) {
+            const uint32_t pti = key - 1u;
+            if (pti >= v->pt_host.size()) return fail(v, VOL_ERR_DEVICE, "corrupt brick request");
+            if (v->pt_host[pti] != kInvalidSlot) {
+                v->protect[v->pt_host[pti]] = v->op_epoch;
+                continue;
+            }
+            if (v->queued[pti]) continue;
+            v->queued[pti] = 1;
+            fresh.push_back(pti);
+        }
+        std::stable_sort(fresh.begin(), fresh.end(),
+                         [&](uint32_t a, uint32_t b) { return level_of_pti(v, a) > level_of_pti(v, b); });
+        pending.insert(pending.end(), fresh.begin(), fresh.end());
+        return VOL_OK;
+    };
+    LoadJob J;
+    bool running = false;
+    // take a chunk of the queue: ring entries, slots (evicting only when no pass is in flight)
+    auto start_job = [&](bool may_evict) -> int {
+        const int want = (int)std::min(pending.size(), max_chunk);
+        if (want == 0) return VOL_OK;
+        int gap = 0;
+        const int start = ring_alloc(v, want, &gap);
+        if (start < 0) return VOL_OK;  // the ring drains as queued uploads run
+        J.start = start;
+        J.nalloc = want;
+        J.gap = gap;
+        J.n = 0;
+        J.coords.clear();
+        while (J.n < want) {
+            const uint32_t pti = pending.front();
+            if (v->free_slots.empty()) {
+                if (!may_evict) break;
+                const int rc = evict_lru(v, 1);
+                if (rc == VOL_ERR_CACHE_FULL) break;  // retried after the next pass releases slots
+                if (rc) return rc;
+            }
+            const uint32_t s = v->free_slots.back();
+            v->free_slots.pop_back();
+            v->owner[s] = pti;
+            v->reserved[s] = 1;
+            v->protect[s] = v->op_epoch;
+            pending.pop_front();
+            R.slots[start + J.n] = s;
+            R.ptis[start + J.n] = pti;
+            const int l = level_of_pti(v, pti);
+            const int64_t id = (int64_t)pti - v->lay.level_pt_offset[l];
+            const int64_t nbx = v->lay.level_bricks[l][0], nby = v->lay.level_bricks[l][1];
+            J.coords.insert(J.coords.end(), {(int32_t)l, (int32_t)(id % nbx), (int32_t)((id / nbx) % nby),
+                                             (int32_t)(id / (nbx * nby))});
+            ++J.n;
+        }
+        if (J.n == 0) {
+            ring_unalloc(v, start, want, gap);
+            return VOL_OK;
+        }
+        if (int rc = loader_submit(v, J.n, J.coords.data(), R.host + (size_t)start * bb)) return rc;
+        running = true;
+        return VOL_OK;
+    };
+    auto drop_job = [&]() {
+        for (int j = 0; j < J.n; ++j) {
+            const uint32_t s = R.slots[J.start + j];
+            v->reserved[s] = 0;
+            v->owner[s] = kInvalidSlot;
+            v->free_slots.push_back(s);
+            v->queued[R.ptis[J.start + j]] = 0;
+        }
+        ring_unalloc(v, J.start, J.nalloc, J.gap);
+        J.n = 0;
+    };
+    // queue the chunk's upload, value ranges and page-table inserts (all reading the ring)
+    auto publish = [&]() -> int {
+        const int n = J.n, st = J.start;
+        CK(v, launch_upload_bricks(v->dtype, v->prov_dtype, R.host_dev + (size_t)st * bb, vol_dev(v), R.slots_dev + st,
+                                   (long long)n, v->stream));
+        CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, R.slots_dev + st, (long long)n, v->stream));
+        CK(v, launch_pt_update(v->pt, R.ptis_dev + st, R.slots_dev + st, n, v->stream));
+        v->stats.launches += 3;
+        cudaEvent_t ev = nullptr;
+        if (!R.spare.empty()) {
+            ev = R.spare.back();
+            R.spare.pop_back();
+        } else {
+            CK(v, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        }
+        CK(v, cudaEventRecord(ev, v->stream));
+        R.inflight.push_back({st, J.nalloc, J.gap, ev});
+        for (int j = 0; j < n; ++j) {
+            const uint32_t s = R.slots[st + j], pti = R.ptis[st + j];
+            v->reserved[s] = 0;
+            v->protect[s] = v->op_epoch;
+            v->queued[pti] = 0;
+            mirror_entry(v, pti, s);
+        }
+        v->stats.bricks_loaded += n;
+        v->stats.bytes_loaded += (int64_t)n * (int64_t)bb;
+        J.n = 0;
+        return VOL_OK;
+    };
+    auto finish_job = [&](bool keep, int* published) -> int {
+        if (!running) return VOL_OK;
+        running = false;
+        const int prc = loader_wait(v);
+        if (prc != 0 || !keep) {
+            drop_job();
+            return prc != 0 ? fail(v, VOL_ERR_PROVIDER, "brick provider failed") : VOL_OK;
+        }
+        if (published) *published += J.n;
+        return publish();
+    };
+
+    int rc = VOL_OK;
+    bool resumed = false;  // the pass in flight is the fresh one (launched by the caller)
+    int published = 0;     // bricks published since the pass in flight was launched
+    uint32_t seen = 0;
+    for (;;) {
+        // (1) while the pass runs: read its requests, publish finished chunks, start new ones
+        for (;;) {
+            bool progress = false;
+            if (cudaEventQuery(v->ev_pass_start) == cudaSuccess) {  // the pass's counters are reset
+                keys.clear();
+                if ((rc = poll_live(v, seen, keys)) || (rc = take(keys))) break;
+            }
+            if (running && loader_done(v)) {
+                if ((rc = finish_job(true, &published))) break;
+                progress = true;
+            }
+            if (!running && pending.size() >= min_chunk) {
+                if ((rc = start_job(false))) break;
+                progress = progress || running;
+            }
+            const cudaError_t q = cudaEventQuery(v->ev_pass_end);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) {
+                rc = cuda_fail(v, q, "render pass");
+                break;
+            }
+            if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+        if (rc) break;
+        // (2) the pass is over: all of its requests
+        if ((rc = collect_pass(v, resumed)) || (rc = take(v->last_requests))) break;
+        if (v->nsusp == 0) break;
+        if (v->stats.passes >= max_passes) {
+            rc = fail(v, VOL_ERR_INCOMPLETE, "max_passes reached");
+            break;
+        }
+        // (3) load until most of what is known to be missing is published
+        for (;;) {
+            if (!running && !pending.empty() && (rc = start_job(true))) break;
+            const size_t known = (size_t)published + (running ? (size_t)J.n : 0) + pending.size();
+            if (published > 0 && 2 * (size_t)published >= known) break;
+            if (!running) break;  // nothing loadable now: resume anyway (the rays ask again)
+            if ((rc = finish_job(true, &published))) break;
+        }
+        if (rc) break;
+        // (4) the next pass; the chunk in generation keeps going meanwhile
+        ++v->op_epoch;
+        published = 0;
+        seen = 0;
+        if ((rc = run_pass(v, true, true))) break;
+        resumed = true;
+    }
+    const int frc = finish_job(rc == VOL_OK, nullptr);
+    for (const uint32_t pti : pending) v->queued[pti] = 0;
+    return rc ? rc : frc;
+}
+
 // Miss loop: load and resume until no ray is suspended or passes run out.
 int miss_loop(vol_t v, bool first_resumed) {
     if (int rc = collect_pass(v, first_resumed)) return rc;
-    const int max_passes = v->params.max_passes > 0 ? v->params.max_passes : 64;
+    const int max_passes = v->params.max_passes > 0 ? v->params.max_passes : 256;
     while (v->nsusp > 0) {
         if (!v->prov && !v->prov_batch)
             return fail(v, VOL_ERR_INCOMPLETE, "rays wait for non-resident bricks (no provider)");
@@ -568,6 +971,8 @@ int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t
     v->pt_host.assign((size_t)lay.total_bricks, kInvalidSlot);
     v->owner.assign((size_t)lay.nslots, kInvalidSlot);
     v->protect.assign((size_t)lay.nslots, 0);
+    v->reserved.assign((size_t)lay.nslots, 0);
+    v->queued.assign((size_t)lay.total_bricks, 0);
     v->free_slots.resize((size_t)lay.nslots);
     for (int64_t s = 0; s < lay.nslots; ++s) v->free_slots[(size_t)s] = (uint32_t)(lay.nslots - 1 - s);
     v->level_resident.assign(levels, 0);
@@ -577,6 +982,14 @@ int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t
 
 void vol_destroy(vol_t v) {
     if (!v) return;
+    if (v->loader.th.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(v->loader.m);
+            v->loader.quit = true;
+        }
+        v->loader.cv.notify_all();
+        v->loader.th.join();
+    }
     if (v->stream) cudaStreamSynchronize(v->stream);
     else cudaDeviceSynchronize();
     void* bufs[] = {v->atlas, v->pt, v->last_used, v->counters, v->aux, v->upd_dev, v->views_dev, v->req_table,
@@ -584,7 +997,14 @@ void vol_destroy(vol_t v) {
                     v->tile_cost, v->tile_order, v->order_buckets, v->range};
     for (void* b : bufs)
         if (b) cudaFree(b);
-    if (v->stage_host) cudaFreeHost(v->stage_host);
+    void* hbufs[] = {v->stage_host, v->ring.host, v->ring.slots, v->ring.ptis, v->poll_host};
+    for (void* b : hbufs)
+        if (b) cudaFreeHost(b);
+    for (auto& r : v->ring.inflight) cudaEventDestroy(r.ev);
+    for (cudaEvent_t e : v->ring.spare) cudaEventDestroy(e);
+    if (v->poll_stream) cudaStreamDestroy(v->poll_stream);
+    for (cudaEvent_t e : {v->ev_pass_start, v->ev_pass_end})
+        if (e) cudaEventDestroy(e);
     delete v;
 }
 
@@ -675,6 +1095,7 @@ int vol_upload_brick(vol_t v, int level, const int32_t brick[3], const void* src
     CK(v, cudaMemcpyAsync(v->stage_slots_dev, &s, sizeof(uint32_t), cudaMemcpyHostToDevice, v->stream));
     CK(v, launch_upload_bricks(v->dtype, src_dtype, dsrc, vol_dev(v), v->stage_slots_dev, 1, v->stream));
     CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, v->stage_slots_dev, 1, v->stream));
+    v->stats.launches += 2;
     if (int rc = flush_pt_updates(v)) return rc;
     CK(v, cudaStreamSynchronize(v->stream));
     return VOL_OK;
@@ -883,13 +1304,18 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         }
     }
     const bool may_miss = !all_resident(v, p.lod_mode != 0);
+    const bool overlap = may_miss && v->prov_batch && !(p.flags & VOL_RENDER_SERIAL_LOADS);
     if (may_miss)
         if (int rc = ensure_miss_buffers(v)) return rc;
+    if (overlap)
+        if (int rc = ensure_overlap(v)) return rc;
     if (int rc = run_pass(v, false, may_miss)) return rc;
-    int rc = may_miss ? miss_loop(v, false) : VOL_OK;
+    int rc = VOL_OK;
+    if (may_miss) rc = overlap ? miss_loop_overlapped(v) : miss_loop(v, false);
     if (rc == VOL_OK) v->have_forward = true;
     if (rc == VOL_OK || rc == VOL_ERR_INCOMPLETE) {
         CK(v, launch_tile_order(v->tile_cost, v->tile_order, (int)tiles, v->order_buckets, v->stream));
+        v->stats.launches += 2;
         v->order_ready = true;
     }
     return rc;
@@ -951,6 +1377,7 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
     CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
     const int grid = backward_blocks_per_sm(v->dtype) * v->nsm;
     CK(v, launch_backward(v->dtype, b, grid, v->stream));
+    v->stats.launches += 1;
     return VOL_OK;
 }
 
@@ -1128,5 +1555,6 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
     r.nrays = rays;  // no request table, no suspension buffers, no usage stamps, no checkpoints
     const int grid = grid_for(v, v->dtype, false, p.ctas_per_sm);
     CK(v, launch_render(v->dtype, render_mode(p, false), r, grid, v->stream));
+    v->stats.launches += 1;
     return VOL_OK;
 }

@@ -76,3 +76,32 @@ def test_flythrough_independent_of_cache_size(P, layout):
         assert st["device_error"] == 0
         np.testing.assert_array_equal(got, want)
     assert evicted > 0 and loaded > 400
+
+
+@pytest.mark.parametrize("cache_slots", [0, 300])
+def test_overlapped_loading_equals_serial(P, cache_slots):
+    """Bricks generated on a library thread while the GPU resumes rays (the default with a batch
+    provider) give the image of loading everything between passes (VOL_RENDER_SERIAL_LOADS),
+    with room for every brick and with a cache that must evict during the frame."""
+    D, B, L, seed = (384, 320, 256), 32, 5, 13
+    tf = synth.tf_peaks(seed)
+    tfd = torch.from_numpy(tf).cuda()
+    cams = synth.flythrough(D, 256, 144, 4, seed)
+    slot = P.plan(D, "u8", B, L, layout="compact").slot_bytes
+    cache = cache_slots * slot
+    params = {"lod_mode": 1, "lod_bias": 0, "max_passes": 5000}
+    over = procedural_volume(P, D, B, L, seed, cache_bytes=cache)
+    serial = procedural_volume(P, D, B, L, seed, cache_bytes=cache)
+    loads = 0
+    for i, cam in enumerate(cams):
+        want = serial.render(cam, tfd, dict(params, flags=4)).cpu().numpy()
+        got, ns = over.render(cam, tfd, params, nsamples=True)
+        st = over.stats()
+        assert st["device_error"] == 0
+        loads += st["bricks_loaded"]
+        np.testing.assert_array_equal(got.cpu().numpy(), want)
+        if i == 0:
+            assert st["passes"] > 1 and st["bricks_loaded"] > 0
+    assert loads > 0
+    if cache_slots:
+        assert over.stats()["resident"] <= cache_slots
