@@ -100,8 +100,12 @@ def _load():
                                        ctypes.POINTER(_Params), vp, ctypes.c_int64, ctypes.c_double,
                                        vp, vp, vp, vp, vp, ctypes.c_int]
             lib.orc_render.restype = ctypes.c_int
+            lib.orc_render_preview.argtypes = [ctypes.POINTER(_Volume), ctypes.POINTER(_Camera), vp,
+                                               ctypes.POINTER(_Params), vp, vp, ctypes.c_int64, ctypes.c_double,
+                                               vp, vp, vp, vp, vp, ctypes.c_int]
+            lib.orc_render_preview.restype = ctypes.c_int
             lib.orc_render_max.argtypes = [ctypes.POINTER(_Volume), ctypes.POINTER(_Camera), vp,
-                                           ctypes.POINTER(_Params), ctypes.c_int, vp, ctypes.c_int64,
+                                           ctypes.POINTER(_Params), ctypes.c_int, vp, vp, ctypes.c_int64,
                                            ctypes.c_double, vp, vp, vp, vp, ctypes.c_int]
             lib.orc_render_max.restype = ctypes.c_int
             lib.orc_render_grad.argtypes = [ctypes.POINTER(_Volume), ctypes.POINTER(_Camera), vp,
@@ -260,17 +264,57 @@ def render(vol: Volume, cam: dict, tf: np.ndarray, params: dict, pixels=None, am
     return {"rgba": rgba, "n": n, "alt_rgba": alt, "alt_n": alt_n, "amb": flag.astype(bool)}
 
 
+def page_table_size(vol: Volume) -> int:
+    """Entries of the levels' page tables laid end to end (ceil(D_l / B) bricks per axis)."""
+    n = 0
+    for arr in vol.levels:
+        Dz, Dy, Dx = arr.shape
+        n += -(-Dx // vol.brick) * -(-Dy // vol.brick) * -(-Dz // vol.brick)
+    return n
+
+
+def render_preview(vol: Volume, cam: dict, tf: np.ndarray, params: dict, resident: np.ndarray, pixels=None,
+                   amb=1e-5, nthreads=0) -> dict:
+    """``render`` under a residency map (uint8 per page-table index, levels end to end, brick id
+    x fastest): a sample whose brick is absent uses the finest coarser resident level, or
+    composites nothing (progressive preview, Sec. IV-B)."""
+    tf = np.ascontiguousarray(tf, dtype=np.float32)
+    resident = np.ascontiguousarray(resident, dtype=np.uint8)
+    assert resident.shape == (page_table_size(vol),)
+    if pixels is None:
+        npix, pp = int(cam["w"]) * int(cam["h"]), None
+    else:
+        pixels = np.ascontiguousarray(pixels, dtype=np.int32)
+        npix, pp = pixels.shape[0], pixels.ctypes.data
+    rgba = np.zeros((npix, 4)); n = np.zeros(npix, dtype=np.int32)
+    alt = np.zeros((npix, 4)); alt_n = np.zeros(npix, dtype=np.int32)
+    flag = np.zeros(npix, dtype=np.int32)
+    rc = _load().orc_render_preview(ctypes.byref(vol._s), ctypes.byref(_cam(cam)), tf.ctypes.data,
+                                    ctypes.byref(_params(**params)), resident.ctypes.data, pp, npix, float(amb),
+                                    rgba.ctypes.data, n.ctypes.data, alt.ctypes.data, alt_n.ctypes.data,
+                                    flag.ctypes.data, int(nthreads))
+    if rc:
+        raise RuntimeError("orc_render_preview failed")
+    return {"rgba": rgba, "n": n, "alt_rgba": alt, "alt_n": alt_n, "amb": flag.astype(bool)}
+
+
 PROJECTIONS = {"mop": 1, "mip": 2}
 
 
 def render_max(vol: Volume, cam: dict, tf: np.ndarray, params: dict, mode: str, pixels=None, amb=1e-5,
-               nthreads=0) -> dict:
+               nthreads=0, resident=None) -> dict:
     """FP64 maximum-opacity ("mop") or maximum-intensity ("mip") projection (Sec. V-A).
 
     Returns rgba [n,4], n (samples on the ray) and lo/hi [n,4]: per channel the range of the
-    outputs over the samples whose opacity lies within ``amb`` of the maximum (MOP)."""
+    outputs over the samples whose opacity lies within ``amb`` of the maximum (MOP).  With a
+    residency map, the progressive preview of ``render_preview``."""
     tf = np.ascontiguousarray(tf, dtype=np.float32)
     assert tf.shape == (256, 4)
+    res_ptr = None
+    if resident is not None:
+        resident = np.ascontiguousarray(resident, dtype=np.uint8)
+        assert resident.shape == (page_table_size(vol),)
+        res_ptr = resident.ctypes.data
     if pixels is None:
         npix, pp = int(cam["w"]) * int(cam["h"]), None
     else:
@@ -279,7 +323,7 @@ def render_max(vol: Volume, cam: dict, tf: np.ndarray, params: dict, mode: str, 
     rgba = np.zeros((npix, 4)); lo = np.zeros((npix, 4)); hi = np.zeros((npix, 4))
     n = np.zeros(npix, dtype=np.int32)
     rc = _load().orc_render_max(ctypes.byref(vol._s), ctypes.byref(_cam(cam)), tf.ctypes.data,
-                                ctypes.byref(_params(**params)), PROJECTIONS[mode], pp, npix, float(amb),
+                                ctypes.byref(_params(**params)), PROJECTIONS[mode], res_ptr, pp, npix, float(amb),
                                 rgba.ctypes.data, lo.ctypes.data, hi.ctypes.data, n.ctypes.data,
                                 int(nthreads))
     if rc:

@@ -15,6 +15,8 @@
  *     transfer function                                         (Sec. IV-A; Fig. 1)
  *   - maximum-opacity projection (MOP), and maximum-intensity projection
  *     beside it                                                 (Sec. V-A; Table I)
+ *   - progressive preview: absent bricks replaced by coarser
+ *     resident levels                                           (Sec. IV-B)
  * The paper gives no formulas for ray setup, interpolation, LOD choice or
  * compositing; the readings used here are listed in the design notes and in
  * the comments of each function.
@@ -480,8 +482,42 @@ typedef struct {
     double C[3], T;
 } orc_state;
 
+/* Page-table index of (level, brick id): the levels' tables laid end to end, level 0
+ * first, each with ceil(D_l / B) bricks per axis (Sec. III-E). */
+static int64_t pt_index(const orc_volume *V, int level, int64_t brick_id)
+{
+    int64_t off = 0;
+    for (int l = 0; l < level; ++l) {
+        int64_t n = 1;
+        for (int a = 0; a < 3; ++a) n *= (V->dims[l][a] + V->brick - 1) / V->brick;
+        off += n;
+    }
+    return off + brick_id;
+}
+
+/*
+ * Progressive preview (Sec. IV-B, Rendering: a low-resolution image from coarser LOD levels
+ * first, refined as bricks arrive).  Reading: with a residency map (one byte per page-table
+ * index), a sample whose brick on its level l is not resident is taken on the finest coarser
+ * level l' > l whose brick at the same position is resident; when none is, the sample
+ * composites nothing.  Returns 0 when the sample is skipped, else 1 with R resolved on the
+ * level used.
+ */
+static int resolve_resident(const orc_volume *V, int level, const float p[3], const uint8_t *resident,
+                            orc_resolve *R)
+{
+    resolve(V, level, p, R);
+    if (!resident || resident[pt_index(V, level, R->brick_id)]) return 1;
+    for (int l = level + 1; l < V->nlevels; ++l) {
+        resolve(V, l, p, R);
+        if (resident[pt_index(V, l, R->brick_id)]) return 1;
+    }
+    return 0;
+}
+
 static int64_t march(const orc_volume *V, const orc_camera *c, const float *tf, const orc_params *P,
-                     const orc_ray *r, int64_t flip_k, double amb, int64_t *amb_k, orc_state *S)
+                     const uint8_t *resident, const orc_ray *r, int64_t flip_k, double amb, int64_t *amb_k,
+                     orc_state *S)
 {
     float scale = lod_scale(c);
     S->C[0] = S->C[1] = S->C[2] = 0.0;
@@ -496,7 +532,7 @@ static int64_t march(const orc_volume *V, const orc_camera *c, const float *tf, 
         for (int a = 0; a < 3; ++a) p[a] = r->o[a] + t * r->d[a];
         int l = lod_level(t, scale, P->lod_bias, V->nlevels, P->lod_mode);
         orc_resolve R;
-        resolve(V, l, p, &R);
+        if (!resolve_resident(V, l, p, resident, &R)) continue; /* preview: nothing resident here */
         orc_interp I;
         interp(V, &R, &I);
         orc_tflookup L;
@@ -527,9 +563,9 @@ static void finish(const orc_state *S, const orc_params *P, double *rgba)
  * out_rgba [npix][4], out_n [npix]; alt_rgba / alt_n receive the alternate
  * (flipped early-termination) result where amb_flag[i] = 1, else a copy.
  */
-int orc_render(const orc_volume *V, const orc_camera *c, const float *tf, const orc_params *P,
-               const int32_t *pix, int64_t npix, double amb, double *out_rgba, int32_t *out_n,
-               double *alt_rgba, int32_t *alt_n, int32_t *amb_flag, int nthreads)
+static int render_impl(const orc_volume *V, const orc_camera *c, const float *tf, const orc_params *P,
+                       const uint8_t *resident, const int32_t *pix, int64_t npix, double amb, double *out_rgba,
+                       int32_t *out_n, double *alt_rgba, int32_t *alt_n, int32_t *amb_flag, int nthreads)
 {
     if (V->nlevels < 1 || V->nlevels > ORC_MAX_LEVELS || V->brick < 1) return -1;
     if (!pix) npix = (int64_t)c->w * c->h;
@@ -544,13 +580,13 @@ int orc_render(const orc_volume *V, const orc_camera *c, const float *tf, const 
         orc_make_ray(c, V->dims[0], px, py, &r);
         orc_state S;
         int64_t ak;
-        int64_t n = march(V, c, tf, P, &r, -1, amb, &ak, &S);
+        int64_t n = march(V, c, tf, P, resident, &r, -1, amb, &ak, &S);
         finish(&S, P, &out_rgba[4 * i]);
         out_n[i] = (int32_t)n;
         if (alt_rgba) {
             if (ak >= 0) {
                 orc_state S2;
-                int64_t n2 = march(V, c, tf, P, &r, ak, amb, NULL, &S2);
+                int64_t n2 = march(V, c, tf, P, resident, &r, ak, amb, NULL, &S2);
                 finish(&S2, P, &alt_rgba[4 * i]);
                 alt_n[i] = (int32_t)n2;
                 amb_flag[i] = 1;
@@ -562,6 +598,24 @@ int orc_render(const orc_volume *V, const orc_camera *c, const float *tf, const 
         }
     }
     return 0;
+}
+
+int orc_render(const orc_volume *V, const orc_camera *c, const float *tf, const orc_params *P,
+               const int32_t *pix, int64_t npix, double amb, double *out_rgba, int32_t *out_n,
+               double *alt_rgba, int32_t *alt_n, int32_t *amb_flag, int nthreads)
+{
+    return render_impl(V, c, tf, P, NULL, pix, npix, amb, out_rgba, out_n, alt_rgba, alt_n, amb_flag, nthreads);
+}
+
+/* orc_render with a residency map (one byte per page-table index, levels end to end): the
+ * progressive preview of resolve_resident.  out_n counts every sample the ray passed,
+ * skipped ones included. */
+int orc_render_preview(const orc_volume *V, const orc_camera *c, const float *tf, const orc_params *P,
+                       const uint8_t *resident, const int32_t *pix, int64_t npix, double amb, double *out_rgba,
+                       int32_t *out_n, double *alt_rgba, int32_t *alt_n, int32_t *amb_flag, int nthreads)
+{
+    if (!resident) return -1;
+    return render_impl(V, c, tf, P, resident, pix, npix, amb, out_rgba, out_n, alt_rgba, alt_n, amb_flag, nthreads);
 }
 
 /* ----------------------------------------------- maximum projections */
@@ -589,9 +643,10 @@ static void composite_one(const double rgba[4], const orc_params *P, double *out
     out[3] = al + (1.0 - al) * (double)P->bg[3];
 }
 
-/* TF lookup of sample k of ray r (value layer); returns 0 past the exit. */
+/* TF lookup of sample k of ray r (value layer); returns 0 past the exit, 2 for a sample that
+ * a preview's residency map leaves out (nothing resident at its position). */
 static int sample_lookup(const orc_volume *V, const orc_camera *c, const float *tf, const orc_params *P,
-                         const orc_ray *r, int64_t k, orc_tflookup *L)
+                         const uint8_t *resident, const orc_ray *r, int64_t k, orc_tflookup *L)
 {
     float t = sample_t(r, P->step, k);
     if (!(t < r->t1)) return 0;
@@ -599,7 +654,7 @@ static int sample_lookup(const orc_volume *V, const orc_camera *c, const float *
     for (int a = 0; a < 3; ++a) p[a] = r->o[a] + t * r->d[a];
     int l = lod_level(t, lod_scale(c), P->lod_bias, V->nlevels, P->lod_mode);
     orc_resolve R;
-    resolve(V, l, p, &R);
+    if (!resolve_resident(V, l, p, resident, &R)) return 2;
     orc_interp I;
     interp(V, &R, &I);
     tf_lookup(tf, I.v, L);
@@ -616,8 +671,8 @@ static int sample_lookup(const orc_volume *V, const orc_camera *c, const float *
  * is continuous in the maximum, so there lo = hi = out.
  */
 int orc_render_max(const orc_volume *V, const orc_camera *c, const float *tf, const orc_params *P, int mode,
-                   const int32_t *pix, int64_t npix, double amb, double *out_rgba, double *lo, double *hi,
-                   int32_t *out_n, int nthreads)
+                   const uint8_t *resident, const int32_t *pix, int64_t npix, double amb, double *out_rgba,
+                   double *lo, double *hi, int32_t *out_n, int nthreads)
 {
     if (V->nlevels < 1 || V->nlevels > ORC_MAX_LEVELS || V->brick < 1) return -1;
     if (mode != ORC_MOP && mode != ORC_MIP) return -1;
@@ -636,7 +691,8 @@ int orc_render_max(const orc_volume *V, const orc_camera *c, const float *tf, co
         int64_t n = 0;
         orc_tflookup L;
         if (r.hit) {
-            for (; sample_lookup(V, c, tf, P, &r, n, &L); ++n) {
+            for (int got; (got = sample_lookup(V, c, tf, P, resident, &r, n, &L)); ++n) {
+                if (got == 2) continue;
                 if (mode == ORC_MOP && L.rgba[3] > best) {
                     best = L.rgba[3];
                     memcpy(kept, L.rgba, sizeof kept);
@@ -657,7 +713,7 @@ int orc_render_max(const orc_volume *V, const orc_camera *c, const float *tf, co
             memcpy(&hi[4 * i], o, 4 * sizeof(double));
             if (mode == ORC_MOP) {
                 for (int64_t k = 0; k < n; ++k) {
-                    sample_lookup(V, c, tf, P, &r, k, &L);
+                    if (sample_lookup(V, c, tf, P, resident, &r, k, &L) != 1) continue;
                     if (!(L.rgba[3] >= best - amb)) continue;
                     double cand[4];
                     composite_one(L.rgba, P, cand);
@@ -733,8 +789,8 @@ int orc_render_grad(const orc_volume *V, const orc_camera *c, const float *tf, c
             orc_make_ray(c, V->dims[0], px, py, &r);
             orc_state S;
             int64_t ak;
-            int64_t n = march(V, c, tf, P, &r, -1, amb, &ak, &S);
-            if (alt_select && alt_select[i] && ak >= 0) n = march(V, c, tf, P, &r, ak, amb, NULL, &S);
+            int64_t n = march(V, c, tf, P, NULL, &r, -1, amb, &ak, &S);
+            if (alt_select && alt_select[i] && ak >= 0) n = march(V, c, tf, P, NULL, &r, ak, amb, NULL, &S);
             if (n == 0) continue;
             if (n > cap) {
                 cap = n;
