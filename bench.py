@@ -467,7 +467,8 @@ def run_outofcore(args, dist, rank, ws, local):
             fr.append({"ms": 1e3 * dt, "samples": int(ns.sum().item()), "passes": st["passes"],
                        "bricks_loaded": st["bricks_loaded"], "bytes_loaded": st["bytes_loaded"],
                        "evicted": st["evicted"], "resident": st["resident"], "touched": st["touched"],
-                       "load_wait_ms": st["load_wait_us"] * 1e-3, "launches": st["launches"]})
+                       "load_wait_ms": st["load_wait_us"] * 1e-3, "launches": st["launches"],
+                       "preview_samples": st["preview_samples"]})
         return fr
 
     barrier(dist)
@@ -480,7 +481,7 @@ def run_outofcore(args, dist, rank, ws, local):
     if not args.quick:
         # the same fly-through, cold cache: loading between passes only (no overlap), and with
         # empty-space skipping
-        for name, flags in (("serial_loads", 4), ("skip_empty", 2)):
+        for name, flags in (("serial_loads", 4), ("skip_empty", 2), ("preview", 8)):
             v2 = P.Volume(wl["D"], "u8", wl["brick"], wl["levels"], cache_bytes=wl["cache_bytes"], layout="compact")
             v2.set_provider_batch(synth.brick_provider_address(), src, "u8")
             fr2 = flythrough(v2, dict(params, flags=flags))
@@ -489,6 +490,9 @@ def run_outofcore(args, dist, rank, ws, local):
             variants[name] = {"ms_per_frame": statistics.mean(f["ms"] for f in st2), "first_frame_ms": fr2[0]["ms"],
                               "load_wait_ms_per_frame": statistics.mean(f["load_wait_ms"] for f in st2),
                               "passes_per_frame": statistics.mean(f["passes"] for f in st2)}
+            if flags == 8:  # one pass per frame: samples on a coarser level than their own, or left out
+                variants[name]["preview_sample_fraction"] = statistics.mean(
+                    f["preview_samples"] / max(1, f["samples"]) for f in st2)
     ms = statistics.mean(f["ms"] for f in steady)
     samples = statistics.mean(f["samples"] for f in steady)
     t_step = max_over_ranks(dist, ms)

@@ -83,6 +83,15 @@ typedef struct {
  * loads all requested bricks between passes instead, on the calling thread.  The image is
  * the same either way. */
 #define VOL_RENDER_SERIAL_LOADS 4u
+/* Progressive preview (Sec. IV-B: a low-resolution image from coarser levels first, refined as
+ * bricks arrive).  One pass: a sample whose brick on its level is not resident is taken on the
+ * finest coarser level whose brick at that position is resident (left out when none is) instead
+ * of waiting, and the brick it wanted is requested.  With a provider the requested bricks start
+ * loading before the call returns (with a batch provider, overlapped with the pass; the chunk
+ * still in generation is published by the next call), so repeated preview renders refine the
+ * image; vol_stats.preview_samples counts the samples not on their own level (0: the image is
+ * the full render's).  Not with VOL_RENDER_GRAD. */
+#define VOL_RENDER_PREVIEW 8u
 
 /* Compositing (vol_params.composite).
  * VOL_COMPOSITE_DVR: front-to-back emission/absorption with early termination (Sec. IV-A).
@@ -160,6 +169,7 @@ typedef struct {
     int64_t touched;         /* distinct bricks the last render sampled (usage stamps) */
     int64_t load_wait_us;    /* host time the last render spent waiting for the provider (us) */
     int64_t launches;        /* kernels the library launched since the last render began */
+    int64_t preview_samples; /* preview: samples taken on a coarser level or left out */
 } vol_stats;
 
 /* Provider of bricks that are not resident (procedural or out-of-core source).

@@ -29,6 +29,7 @@ MAX_LEVELS = 16
 VOL_RENDER_GRAD = 1
 VOL_RENDER_SKIP_EMPTY = 2
 VOL_RENDER_SERIAL_LOADS = 4
+VOL_RENDER_PREVIEW = 8
 VOL_COMPOSITE_DVR, VOL_COMPOSITE_MOP, VOL_COMPOSITE_MIP = 0, 1, 2
 COMPOSITES = {"dvr": VOL_COMPOSITE_DVR, "mop": VOL_COMPOSITE_MOP, "mip": VOL_COMPOSITE_MIP}
 VOL_LAYOUT_COMPACT = 1
@@ -69,7 +70,8 @@ class vol_layout(ctypes.Structure):
 class vol_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("passes", "rays", "suspended", "requests", "request_overflow",
                                                "bricks_loaded", "bytes_loaded", "evicted", "resident", "frame",
-                                               "device_error", "touched", "load_wait_us", "launches")]
+                                               "device_error", "touched", "load_wait_us", "launches",
+                                               "preview_samples")]
 
 
 class vol_trace_rec(ctypes.Structure):

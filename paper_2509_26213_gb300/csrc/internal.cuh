@@ -27,6 +27,7 @@ enum Counter : int {
     kSuspCount = 2,  // rays suspended in this pass
     kReqOverflow = 3,
     kDevError = 4,
+    kPreview = 5,    // preview: samples taken from a coarser level, or left out
     kNumCounters = 8
 };
 
@@ -81,6 +82,7 @@ struct RenderDev {
     float4 bg;
     int lod_mode, lod_bias;
     int skip_empty;     // skip bricks whose value range the TF maps to zero opacity
+    int preview;        // a sample on a non-resident brick uses the finest coarser resident level
     float4* out;
     int* nsamp;
     unsigned* counters;

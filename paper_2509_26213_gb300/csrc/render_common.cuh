@@ -363,6 +363,46 @@ __device__ __noinline__ int brick_last_sample(int k_start, uint32_t pti_start, c
     return ke;
 }
 
+// Progressive preview (Sec. IV-B: a low-resolution image from coarser levels first): sample k,
+// whose brick on its level is not resident, on the finest coarser level whose brick at the
+// same position is resident.  ok = false when no level is.
+struct Fallback {
+    uint32_t slot, local;
+    float w[3];
+    bool ok;
+};
+
+template <bool LOD>
+__device__ __noinline__ Fallback preview_fallback(const uint32_t* __restrict__ pt, int k, float o0, float o1,
+                                                  float o2, float d0, float d1, float d2, float t0, float step,
+                                                  float lodscale, int bias, int nlev, const LevelDev* s_lv,
+                                                  int bshift, int bmask, int row) {
+    Fallback F;
+    F.ok = false;
+    F.slot = 0;
+    F.local = 0;
+    F.w[0] = F.w[1] = F.w[2] = 0.0f;
+    const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
+    const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
+                        __fadd_rn(o2, __fmul_rn(t, d2))};
+    const int l = LOD ? lod_level(t, lodscale, bias, nlev) : 0;
+    for (int m = l + 1; m < nlev; ++m) {
+        Resolved R;
+        resolve(s_lv[m], bshift, bmask, row, p, R);
+        const uint32_t s = __ldg(pt + R.pti);
+        if (s != kInvalidSlot) {
+            F.ok = true;
+            F.slot = s;
+            F.local = R.local;
+            F.w[0] = R.w[0];
+            F.w[1] = R.w[1];
+            F.w[2] = R.w[2];
+            break;
+        }
+    }
+    return F;
+}
+
 __device__ __forceinline__ int find_view_tile(const ViewDev* views, int nviews, int item) {
     int lo = 0, hi = nviews - 1;
     while (lo < hi) {
@@ -453,6 +493,37 @@ constexpr int kBatch = VOLRC_BATCH;
 #endif
 
 __host__ __device__ constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
+
+// One sample's compositing step for mode MODE (lane state C0..C2, T as k_render keeps it);
+// returns true when the ray may stop after it.
+template <int DT, int MODE>
+__device__ __forceinline__ bool composite_sample(float val, const float4* s_tf, const float4* s_tfd, float amax_tf,
+                                                 float et, float& T, float& C0, float& C1, float& C2) {
+    const float x = tf_coord<DT>(val);
+    if (MODE == kMip) {
+        if (x > T) T = x;
+        return T >= 255.0f;  // no coordinate lies above 255
+    }
+    const int i = min((int)x, 254);
+    const float wt = x - (float)i;
+    const float4 a = s_tf[i], dab = s_tfd[i];  // entry i and tf[i+1] - tf[i]
+    const float al = fmaf(wt, dab.w, a.w);
+    if (MODE == kMop) {
+        if (al > T) {  // the first sample of largest opacity is kept
+            T = al;
+            C0 = fmaf(wt, dab.x, a.x);
+            C1 = fmaf(wt, dab.y, a.y);
+            C2 = fmaf(wt, dab.z, a.z);
+        }
+        return T >= amax_tf;
+    }
+    const float Ta = T * al;
+    C0 = fmaf(Ta, fmaf(wt, dab.x, a.x), C0);
+    C1 = fmaf(Ta, fmaf(wt, dab.y, a.y), C1);
+    C2 = fmaf(Ta, fmaf(wt, dab.z, a.z), C2);
+    T = T * (1.0f - al);
+    return __fsub_rn(1.0f, T) >= et;
+}
 
 // BS: brick edge known at compile time (32 or 64), or 0 for any power of two read at run time.
 // MODE: kDvr, kDvrGrad, kMop or kMip.  Lane state (C0, C1, C2, T): emission/absorption keeps
@@ -670,39 +741,33 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     if (j < stop && !fin) {
                         if (GRAD && k > 0 && (k & (kCkptEvery - 1)) == 0)
                             P.ckpt[(long long)(k / kCkptEvery - 1) * P.nrays + ray] = T;
-                        const float x = tf_coord<DT>(val[j]);
-                        if (MODE == kMip) {
-                            if (x > T) T = x;
-                            ++k;
-                            if (T >= 255.0f) fin = true;  // no coordinate lies above 255
-                            continue;
-                        }
-                        const int i = min((int)x, 254);
-                        const float wt = x - (float)i;
-                        const float4 a = s_tf[i], dab = s_tfd[i];  // entry i and tf[i+1] - tf[i]
-                        const float al = fmaf(wt, dab.w, a.w);
-                        if (MODE == kMop) {
-                            if (al > T) {  // the first sample of largest opacity is kept
-                                T = al;
-                                C0 = fmaf(wt, dab.x, a.x);
-                                C1 = fmaf(wt, dab.y, a.y);
-                                C2 = fmaf(wt, dab.z, a.z);
-                            }
-                            ++k;
-                            if (T >= amax_tf) fin = true;
-                            continue;
-                        }
-                        const float Ta = T * al;
-                        C0 = fmaf(Ta, fmaf(wt, dab.x, a.x), C0);
-                        C1 = fmaf(Ta, fmaf(wt, dab.y, a.y), C1);
-                        C2 = fmaf(Ta, fmaf(wt, dab.z, a.z), C2);
-                        T = T * (1.0f - al);
+                        fin = composite_sample<DT, MODE>(val[j], s_tf, s_tfd, amax_tf, et, T, C0, C1, C2);
                         ++k;
-                        if (__fsub_rn(1.0f, T) >= et) fin = true;
                     }
                 }
-                if (!fin && nvalid < kBatch && nvalid <= miss_at && nvalid <= empty_at) fin = true;  // left the volume
-                if (!fin && empty_at < kBatch && empty_at < miss_at && empty_at < nvalid) {
+                bool fell = false;
+                if (!GRAD && P.preview && !fin && miss_at < kBatch && miss_at < empty_at) {
+                    // preview (Sec. IV-B): sample k lies in a brick that is not resident.  Request the
+                    // brick for the refinement and take the sample on the finest coarser resident
+                    // level (left out when none is).
+                    if (P.req_table && pti[miss_at] != cur_pti) request_brick(P, pti[miss_at] + 1u);
+                    cur_pti = pti[miss_at];
+                    cur_empty = false;
+                    const Fallback F = preview_fallback<LOD>(P.vol.pt, k, o0, o1, o2, d0, d1, d2, t0, step, lodscale,
+                                                             P.lod_bias, nlev, s_lv, bshift, bmask, row);
+                    if (F.ok) {
+                        if (P.last_used) P.last_used[F.slot] = P.frame;
+                        const float v = sample_value<DT, BS, Q>(
+                            P.vol.atlas, (unsigned long long)F.slot * slot_stride + F.local, B1, F.w);
+                        fin = composite_sample<DT, MODE>(v, s_tf, s_tfd, amax_tf, et, T, C0, C1, C2);
+                    }
+                    ++k;
+                    fell = true;
+                    const unsigned m = __activemask();
+                    if ((int)lane == __ffs(m) - 1) atomicAdd(&P.counters[kPreview], (unsigned)__popc(m));
+                }
+                if (!fin && !fell && nvalid < kBatch && nvalid <= miss_at && nvalid <= empty_at) fin = true;  // left the volume
+                if (!fin && !fell && empty_at < kBatch && empty_at < miss_at && empty_at < nvalid) {
                     // sample k is in a brick of zero opacity: every sample up to the brick's last
                     // composites nothing, so continue after it
                     const float o3[3] = {o0, o1, o2}, d3[3] = {d0, d1, d2};
@@ -739,7 +804,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     if (GRAD) P.ray_n[ray] = k;
                     if (P.tile_cost && my_tile >= 0) atomicAdd(&P.tile_cost[my_tile], k);
                     active = false;
-                } else if (miss_at < kBatch) {
+                } else if (!fell && miss_at < kBatch) {
                     // wait for the missing brick: sample k (= the first missing one) resumes later
                     if (P.req_table) {
                         request_brick(P, miss_pti + 1u);

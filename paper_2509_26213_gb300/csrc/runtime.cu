@@ -188,6 +188,15 @@ struct vol_s {
         std::deque<Region> inflight;
         std::vector<cudaEvent_t> spare;
     } ring;
+    struct LoadJob {
+        int start = 0, nalloc = 0, gap = 0, n = 0;  // ring region, bricks in it
+        std::vector<int32_t> coords;                 // [n][4] level, bx, by, bz
+    };
+    struct Ovl {
+        std::deque<uint32_t> pending;  // requested bricks (page-table indices) not yet in generation
+        LoadJob job;
+        bool running = false;          // job is in the loader thread
+    } ovl;
     cudaStream_t poll_stream = nullptr;
     uint32_t* poll_host = nullptr;   // pinned: request count, then request keys
     cudaEvent_t ev_pass_start = nullptr, ev_pass_end = nullptr;  // around each pass's launch
@@ -417,6 +426,7 @@ RenderDev render_args(vol_t v) {
     p.lod_mode = v->params.lod_mode;
     p.lod_bias = v->params.lod_bias;
     p.skip_empty = (v->params.flags & VOL_RENDER_SKIP_EMPTY) ? 1 : 0;
+    p.preview = (v->params.flags & VOL_RENDER_PREVIEW) ? 1 : 0;
     p.out = (float4*)v->out;
     p.nsamp = v->nsamp;
     p.counters = v->counters;
@@ -471,6 +481,7 @@ int collect_pass(vol_t v, bool resumed) {
     CK(v, cudaMemcpyAsync(c, v->counters, sizeof(c), cudaMemcpyDeviceToHost, v->stream));
     CK(v, cudaStreamSynchronize(v->stream));
     v->stats.device_error += c[kDevError];
+    v->stats.preview_samples += c[kPreview];
     v->stats.request_overflow += c[kReqOverflow];
     const uint32_t nreq = std::min<uint32_t>(c[kReqCount], v->req_list_cap);
     v->stats.requests += nreq;
@@ -703,11 +714,6 @@ void mirror_entry(vol_t v, uint32_t pti, uint32_t slot) {
     v->pt_host[pti] = slot;
 }
 
-struct LoadJob {
-    int start = 0, nalloc = 0, gap = 0, n = 0;  // ring region, bricks in it
-    std::vector<int32_t> coords;                 // [n][4] level, bx, by, bz
-};
-
 // New request keys of the pass in flight: its count word, then the keys past `seen` that the
 // kernel has stored (keys are non-zero; a zero is a reserved place not yet written, read again
 // at the next poll).
@@ -726,185 +732,217 @@ int poll_live(vol_t v, uint32_t& seen, std::vector<uint32_t>& out) {
     return VOL_OK;
 }
 
-int miss_loop_overlapped(vol_t v) {
-    auto& R = v->ring;
-    const size_t bb = R.brick_bytes;
-    const int max_passes = v->params.max_passes > 0 ? v->params.max_passes : 256;
-    const size_t min_chunk = std::min<size_t>(64, 2 * (size_t)host_cores());  // bricks for every host core
-    const size_t max_chunk = std::max<size_t>(min_chunk, std::min<size_t>(512, (size_t)R.cap / 4));
-    ++v->op_epoch;
-    std::deque<uint32_t> pending;
-    std::vector<uint32_t> keys;
-    auto take = [&](const std::vector<uint32_t>& ks) -> int {
-        // coarse levels first: one coarse brick serves the rays of many fine ones
-        std::vector<uint32_t> fresh;
-        for (const uint32_t key : ks) {
-            const uint32_t pti = key - 1u;
-            if (pti >= v->pt_host.size()) return fail(v, VOL_ERR_DEVICE, "corrupt brick request");
-            if (v->pt_host[pti] != kInvalidSlot) {
-                v->protect[v->pt_host[pti]] = v->op_epoch;
-                continue;
-            }
-            if (v->queued[pti]) continue;
-            v->queued[pti] = 1;
-            fresh.push_back(pti);
-        }
-        std::stable_sort(fresh.begin(), fresh.end(),
-                         [&](uint32_t a, uint32_t b) { return level_of_pti(v, a) > level_of_pti(v, b); });
-        pending.insert(pending.end(), fresh.begin(), fresh.end());
-        return VOL_OK;
-    };
-    LoadJob J;
-    bool running = false;
-    // take a chunk of the queue: ring entries, slots (evicting only when no pass is in flight)
-    auto start_job = [&](bool may_evict) -> int {
-        const int want = (int)std::min(pending.size(), max_chunk);
-        if (want == 0) return VOL_OK;
-        int gap = 0;
-        const int start = ring_alloc(v, want, &gap);
-        if (start < 0) return VOL_OK;  // the ring drains as queued uploads run
-        J.start = start;
-        J.nalloc = want;
-        J.gap = gap;
-        J.n = 0;
-        J.coords.clear();
-        while (J.n < want) {
-            const uint32_t pti = pending.front();
-            if (v->free_slots.empty()) {
-                if (!may_evict) break;
-                const int rc = evict_lru(v, 1);
-                if (rc == VOL_ERR_CACHE_FULL) break;  // retried after the next pass releases slots
-                if (rc) return rc;
-            }
-            const uint32_t s = v->free_slots.back();
-            v->free_slots.pop_back();
-            v->owner[s] = pti;
-            v->reserved[s] = 1;
-            v->protect[s] = v->op_epoch;
-            pending.pop_front();
-            R.slots[start + J.n] = s;
-            R.ptis[start + J.n] = pti;
-            const int l = level_of_pti(v, pti);
-            const int64_t id = (int64_t)pti - v->lay.level_pt_offset[l];
-            const int64_t nbx = v->lay.level_bricks[l][0], nby = v->lay.level_bricks[l][1];
-            J.coords.insert(J.coords.end(), {(int32_t)l, (int32_t)(id % nbx), (int32_t)((id / nbx) % nby),
-                                             (int32_t)(id / (nbx * nby))});
-            ++J.n;
-        }
-        if (J.n == 0) {
-            ring_unalloc(v, start, want, gap);
-            return VOL_OK;
-        }
-        if (int rc = loader_submit(v, J.n, J.coords.data(), R.host + (size_t)start * bb)) return rc;
-        running = true;
-        return VOL_OK;
-    };
-    auto drop_job = [&]() {
-        for (int j = 0; j < J.n; ++j) {
-            const uint32_t s = R.slots[J.start + j];
-            v->reserved[s] = 0;
-            v->owner[s] = kInvalidSlot;
-            v->free_slots.push_back(s);
-            v->queued[R.ptis[J.start + j]] = 0;
-        }
-        ring_unalloc(v, J.start, J.nalloc, J.gap);
-        J.n = 0;
-    };
-    // queue the chunk's upload, value ranges and page-table inserts (all reading the ring)
-    auto publish = [&]() -> int {
-        const int n = J.n, st = J.start;
-        CK(v, launch_upload_bricks(v->dtype, v->prov_dtype, R.host_dev + (size_t)st * bb, vol_dev(v), R.slots_dev + st,
-                                   (long long)n, v->stream));
-        CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, R.slots_dev + st, (long long)n, v->stream));
-        CK(v, launch_pt_update(v->pt, R.ptis_dev + st, R.slots_dev + st, n, v->stream));
-        v->stats.launches += 3;
-        cudaEvent_t ev = nullptr;
-        if (!R.spare.empty()) {
-            ev = R.spare.back();
-            R.spare.pop_back();
-        } else {
-            CK(v, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        }
-        CK(v, cudaEventRecord(ev, v->stream));
-        R.inflight.push_back({st, J.nalloc, J.gap, ev});
-        for (int j = 0; j < n; ++j) {
-            const uint32_t s = R.slots[st + j], pti = R.ptis[st + j];
-            v->reserved[s] = 0;
-            v->protect[s] = v->op_epoch;
-            v->queued[pti] = 0;
-            mirror_entry(v, pti, s);
-        }
-        v->stats.bricks_loaded += n;
-        v->stats.bytes_loaded += (int64_t)n * (int64_t)bb;
-        J.n = 0;
-        return VOL_OK;
-    };
-    auto finish_job = [&](bool keep, int* published) -> int {
-        if (!running) return VOL_OK;
-        running = false;
-        const int prc = loader_wait(v);
-        if (prc != 0 || !keep) {
-            drop_job();
-            return prc != 0 ? fail(v, VOL_ERR_PROVIDER, "brick provider failed") : VOL_OK;
-        }
-        if (published) *published += J.n;
-        return publish();
-    };
+size_t ovl_min_chunk() { return std::min<size_t>(64, 2 * (size_t)host_cores()); }  // bricks for every host core
+size_t ovl_max_chunk(vol_t v) { return std::max<size_t>(ovl_min_chunk(), std::min<size_t>(512, (size_t)v->ring.cap / 4)); }
 
+// Queue requested bricks (keys = page-table index + 1) that are neither resident nor queued;
+// coarse levels first, since one coarse brick serves the rays of many fine ones.
+int ovl_take(vol_t v, const std::vector<uint32_t>& keys) {
+    std::vector<uint32_t> fresh;
+    for (const uint32_t key : keys) {
+        const uint32_t pti = key - 1u;
+        if (pti >= v->pt_host.size()) return fail(v, VOL_ERR_DEVICE, "corrupt brick request");
+        if (v->pt_host[pti] != kInvalidSlot) {
+            v->protect[v->pt_host[pti]] = v->op_epoch;
+            continue;
+        }
+        if (v->queued[pti]) continue;
+        v->queued[pti] = 1;
+        fresh.push_back(pti);
+    }
+    std::stable_sort(fresh.begin(), fresh.end(),
+                     [&](uint32_t a, uint32_t b) { return level_of_pti(v, a) > level_of_pti(v, b); });
+    v->ovl.pending.insert(v->ovl.pending.end(), fresh.begin(), fresh.end());
+    return VOL_OK;
+}
+
+// Hand the next chunk of the queue to the loader thread when it is idle and at least min_n
+// bricks wait: ring entries, then slots (evicting only when no pass is in flight).
+int ovl_start(vol_t v, bool may_evict, size_t min_n) {
+    auto& O = v->ovl;
+    auto& R = v->ring;
+    auto& J = O.job;
+    if (O.running || O.pending.empty() || O.pending.size() < min_n) return VOL_OK;
+    const int want = (int)std::min(O.pending.size(), ovl_max_chunk(v));
+    int gap = 0;
+    const int start = ring_alloc(v, want, &gap);
+    if (start < 0) return VOL_OK;  // the ring drains as queued uploads run
+    J.start = start;
+    J.nalloc = want;
+    J.gap = gap;
+    J.n = 0;
+    J.coords.clear();
+    while (J.n < want) {
+        const uint32_t pti = O.pending.front();
+        if (v->free_slots.empty()) {
+            if (!may_evict) break;
+            const int rc = evict_lru(v, 1);
+            if (rc == VOL_ERR_CACHE_FULL) break;  // retried after the next pass releases slots
+            if (rc) return rc;
+        }
+        const uint32_t s = v->free_slots.back();
+        v->free_slots.pop_back();
+        v->owner[s] = pti;
+        v->reserved[s] = 1;
+        v->protect[s] = v->op_epoch;
+        O.pending.pop_front();
+        R.slots[start + J.n] = s;
+        R.ptis[start + J.n] = pti;
+        const int l = level_of_pti(v, pti);
+        const int64_t id = (int64_t)pti - v->lay.level_pt_offset[l];
+        const int64_t nbx = v->lay.level_bricks[l][0], nby = v->lay.level_bricks[l][1];
+        J.coords.insert(J.coords.end(), {(int32_t)l, (int32_t)(id % nbx), (int32_t)((id / nbx) % nby),
+                                         (int32_t)(id / (nbx * nby))});
+        ++J.n;
+    }
+    if (J.n == 0) {
+        ring_unalloc(v, start, want, gap);
+        return VOL_OK;
+    }
+    if (int rc = loader_submit(v, J.n, J.coords.data(), R.host + (size_t)start * R.brick_bytes)) return rc;
+    O.running = true;
+    return VOL_OK;
+}
+
+void ovl_drop(vol_t v) {  // free the chunk's reservations
+    auto& J = v->ovl.job;
+    auto& R = v->ring;
+    for (int j = 0; j < J.n; ++j) {
+        const uint32_t s = R.slots[J.start + j];
+        v->reserved[s] = 0;
+        v->owner[s] = kInvalidSlot;
+        v->free_slots.push_back(s);
+        v->queued[R.ptis[J.start + j]] = 0;
+    }
+    ring_unalloc(v, J.start, J.nalloc, J.gap);
+    J.n = 0;
+}
+
+// Queue the chunk's upload, value ranges and page-table inserts (all reading the ring) on the
+// volume's stream.
+int ovl_publish(vol_t v, int* published) {
+    auto& J = v->ovl.job;
+    auto& R = v->ring;
+    const int n = J.n, st = J.start;
+    const size_t bb = R.brick_bytes;
+    CK(v, launch_upload_bricks(v->dtype, v->prov_dtype, R.host_dev + (size_t)st * bb, vol_dev(v), R.slots_dev + st,
+                               (long long)n, v->stream));
+    CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, R.slots_dev + st, (long long)n, v->stream));
+    CK(v, launch_pt_update(v->pt, R.ptis_dev + st, R.slots_dev + st, n, v->stream));
+    v->stats.launches += 3;
+    cudaEvent_t ev = nullptr;
+    if (!R.spare.empty()) {
+        ev = R.spare.back();
+        R.spare.pop_back();
+    } else {
+        CK(v, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    CK(v, cudaEventRecord(ev, v->stream));
+    R.inflight.push_back({st, J.nalloc, J.gap, ev});
+    for (int j = 0; j < n; ++j) {
+        const uint32_t s = R.slots[st + j], pti = R.ptis[st + j];
+        v->reserved[s] = 0;
+        v->protect[s] = v->op_epoch;
+        v->queued[pti] = 0;
+        mirror_entry(v, pti, s);
+    }
+    v->stats.bricks_loaded += n;
+    v->stats.bytes_loaded += (int64_t)n * (int64_t)bb;
+    if (published) *published += n;
+    J.n = 0;
+    return VOL_OK;
+}
+
+// Wait for the chunk in the loader thread; publish it (keep) or free it.
+int ovl_finish(vol_t v, bool keep, int* published) {
+    auto& O = v->ovl;
+    if (!O.running) return VOL_OK;
+    O.running = false;
+    const int prc = loader_wait(v);
+    if (prc != 0 || !keep) {
+        ovl_drop(v);
+        return prc != 0 ? fail(v, VOL_ERR_PROVIDER, "brick provider failed") : VOL_OK;
+    }
+    return ovl_publish(v, published);
+}
+
+// Before anything else changes the cache: publish the chunk still in generation (a preview
+// render leaves it running) and forget the queue.
+int ovl_settle(vol_t v) {
+    int rc = ovl_finish(v, true, nullptr);
+    for (const uint32_t pti : v->ovl.pending) v->queued[pti] = 0;
+    v->ovl.pending.clear();
+    return rc;
+}
+
+// While the pass in flight runs: read its requests, publish finished chunks, start new ones.
+int ovl_poll_pass(vol_t v, int* published) {
+    uint32_t seen = 0;
+    std::vector<uint32_t> keys;
+    for (;;) {
+        bool progress = false;
+        if (cudaEventQuery(v->ev_pass_start) == cudaSuccess) {  // the pass's counters are reset
+            keys.clear();
+            if (int rc = poll_live(v, seen, keys)) return rc;
+            if (int rc = ovl_take(v, keys)) return rc;
+        }
+        if (v->ovl.running && loader_done(v)) {
+            if (int rc = ovl_finish(v, true, published)) return rc;
+            progress = true;
+        }
+        if (!v->ovl.running) {
+            if (int rc = ovl_start(v, false, ovl_min_chunk())) return rc;
+            progress = progress || v->ovl.running;
+        }
+        const cudaError_t q = cudaEventQuery(v->ev_pass_end);
+        if (q == cudaSuccess) return VOL_OK;
+        if (q != cudaErrorNotReady) return cuda_fail(v, q, "render pass");
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+}
+
+// Miss loop of the overlapped path for the pass the caller launched.  preview: that pass took
+// absent bricks from coarser levels, so no ray waits; its requests start loading and the
+// chunk in generation is left running for the next render to publish.
+int miss_loop_overlapped(vol_t v, bool preview) {
+    auto& O = v->ovl;
+    const int max_passes = v->params.max_passes > 0 ? v->params.max_passes : 256;
+    ++v->op_epoch;
     int rc = VOL_OK;
     bool resumed = false;  // the pass in flight is the fresh one (launched by the caller)
     int published = 0;     // bricks published since the pass in flight was launched
-    uint32_t seen = 0;
     for (;;) {
-        // (1) while the pass runs: read its requests, publish finished chunks, start new ones
-        for (;;) {
-            bool progress = false;
-            if (cudaEventQuery(v->ev_pass_start) == cudaSuccess) {  // the pass's counters are reset
-                keys.clear();
-                if ((rc = poll_live(v, seen, keys)) || (rc = take(keys))) break;
-            }
-            if (running && loader_done(v)) {
-                if ((rc = finish_job(true, &published))) break;
-                progress = true;
-            }
-            if (!running && pending.size() >= min_chunk) {
-                if ((rc = start_job(false))) break;
-                progress = progress || running;
-            }
-            const cudaError_t q = cudaEventQuery(v->ev_pass_end);
-            if (q == cudaSuccess) break;
-            if (q != cudaErrorNotReady) {
-                rc = cuda_fail(v, q, "render pass");
-                break;
-            }
-            if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(100));
-        }
-        if (rc) break;
+        // (1) while the pass runs
+        if ((rc = ovl_poll_pass(v, &published))) break;
         // (2) the pass is over: all of its requests
-        if ((rc = collect_pass(v, resumed)) || (rc = take(v->last_requests))) break;
+        if ((rc = collect_pass(v, resumed)) || (rc = ovl_take(v, v->last_requests))) break;
+        if (preview) {
+            rc = ovl_start(v, true, 1);
+            return rc;
+        }
         if (v->nsusp == 0) break;
         if (v->stats.passes >= max_passes) {
             rc = fail(v, VOL_ERR_INCOMPLETE, "max_passes reached");
             break;
         }
-        // (3) load until most of what is known to be missing is published
+        // (3) load until at least half of what is known to be missing is published
         for (;;) {
-            if (!running && !pending.empty() && (rc = start_job(true))) break;
-            const size_t known = (size_t)published + (running ? (size_t)J.n : 0) + pending.size();
+            if ((rc = ovl_start(v, true, 1))) break;
+            const size_t known = (size_t)published + (O.running ? (size_t)O.job.n : 0) + O.pending.size();
             if (published > 0 && 2 * (size_t)published >= known) break;
-            if (!running) break;  // nothing loadable now: resume anyway (the rays ask again)
-            if ((rc = finish_job(true, &published))) break;
+            if (!O.running) break;  // nothing loadable now: resume anyway (the rays ask again)
+            if ((rc = ovl_finish(v, true, &published))) break;
         }
         if (rc) break;
         // (4) the next pass; the chunk in generation keeps going meanwhile
         ++v->op_epoch;
         published = 0;
-        seen = 0;
         if ((rc = run_pass(v, true, true))) break;
         resumed = true;
     }
-    const int frc = finish_job(rc == VOL_OK, nullptr);
-    for (const uint32_t pti : pending) v->queued[pti] = 0;
+    const int frc = ovl_finish(v, rc == VOL_OK, nullptr);
+    for (const uint32_t pti : O.pending) v->queued[pti] = 0;
+    O.pending.clear();
     return rc ? rc : frc;
 }
 
@@ -1042,6 +1080,7 @@ int vol_get_stats(vol_t v, vol_stats* out) {
 
 int vol_upload_level(vol_t v, int level, const void* src, int src_dtype, int src_on_device) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     if (level < 0 || level >= v->L || !src) return fail(v, VOL_ERR_INVALID_ARG, "bad level or src");
     if (!bpv_of(src_dtype)) return fail(v, VOL_ERR_INVALID_ARG, "bad src dtype");
     if (!conversion_ok(src_dtype, v->dtype)) return fail(v, VOL_ERR_UNSUPPORTED, "unsupported conversion");
@@ -1078,6 +1117,7 @@ int vol_upload_level(vol_t v, int level, const void* src, int src_dtype, int src
 
 int vol_upload_brick(vol_t v, int level, const int32_t brick[3], const void* src, int src_dtype, int src_on_device) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     uint32_t pti;
     if (!src || brick_pti(v, level, brick, &pti)) return fail(v, VOL_ERR_INVALID_ARG, "bad level, brick or src");
     if (!conversion_ok(src_dtype, v->dtype)) return fail(v, VOL_ERR_UNSUPPORTED, "unsupported conversion");
@@ -1103,6 +1143,7 @@ int vol_upload_brick(vol_t v, int level, const int32_t brick[3], const void* src
 
 int vol_build_lod(vol_t v, int from_level) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     if (from_level < 0 || from_level >= v->L) return fail(v, VOL_ERR_INVALID_ARG, "bad from_level");
     for (int l = from_level + 1; l < v->L; ++l) {
         if (v->level_resident[l - 1] != level_nbricks(v, l - 1))
@@ -1138,6 +1179,7 @@ int vol_build_lod(vol_t v, int from_level) {
 
 int vol_download_brick(vol_t v, int level, const int32_t brick[3], void* dst) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     uint32_t pti;
     if (!dst || brick_pti(v, level, brick, &pti)) return fail(v, VOL_ERR_INVALID_ARG, "bad level, brick or dst");
     const uint32_t s = v->pt_host[pti];
@@ -1169,6 +1211,7 @@ int vol_download_brick(vol_t v, int level, const int32_t brick[3], void* dst) {
 
 int vol_evict_all(vol_t v) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     for (int64_t s = 0; s < v->lay.nslots; ++s)
         if (v->owner[(size_t)s] != kInvalidSlot) {
             v->owner[(size_t)s] = kInvalidSlot;
@@ -1186,6 +1229,7 @@ int vol_evict_all(vol_t v) {
 
 int vol_set_provider(vol_t v, vol_provider_fn fn, void* user, int src_dtype) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     if (fn && !conversion_ok(src_dtype, v->dtype)) return fail(v, VOL_ERR_UNSUPPORTED, "unsupported provider dtype");
     v->prov = fn;
     v->prov_batch = nullptr;
@@ -1196,6 +1240,7 @@ int vol_set_provider(vol_t v, vol_provider_fn fn, void* user, int src_dtype) {
 
 int vol_set_provider_batch(vol_t v, vol_provider_batch_fn fn, void* user, int src_dtype) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     if (fn && !conversion_ok(src_dtype, v->dtype)) return fail(v, VOL_ERR_UNSUPPORTED, "unsupported provider dtype");
     v->prov_batch = fn;
     v->prov = nullptr;
@@ -1223,6 +1268,8 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     if (grad && p.lod_mode != 0) return fail(v, VOL_ERR_UNSUPPORTED, "gradients need lod_mode 0");
     if (grad && p.composite != VOL_COMPOSITE_DVR)
         return fail(v, VOL_ERR_UNSUPPORTED, "gradients need emission/absorption compositing");
+    const bool preview = (p.flags & VOL_RENDER_PREVIEW) != 0;
+    if (grad && preview) return fail(v, VOL_ERR_UNSUPPORTED, "a preview keeps no gradient state");
 
     // view table
     v->views_host.resize(nviews);
@@ -1305,14 +1352,26 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     }
     const bool may_miss = !all_resident(v, p.lod_mode != 0);
     const bool overlap = may_miss && v->prov_batch && !(p.flags & VOL_RENDER_SERIAL_LOADS);
+    if (!overlap)
+        if (int rc = ovl_settle(v)) return rc;  // a chunk a preview left in generation
     if (may_miss)
         if (int rc = ensure_miss_buffers(v)) return rc;
     if (overlap)
         if (int rc = ensure_overlap(v)) return rc;
     if (int rc = run_pass(v, false, may_miss)) return rc;
     int rc = VOL_OK;
-    if (may_miss) rc = overlap ? miss_loop_overlapped(v) : miss_loop(v, false);
-    if (rc == VOL_OK) v->have_forward = true;
+    if (may_miss) {
+        if (overlap) {
+            rc = miss_loop_overlapped(v, preview);
+        } else if (preview) {
+            // one pass (no ray waited); load what it requested for the next render
+            rc = collect_pass(v, false);
+            if (!rc && (v->prov || v->prov_batch) && !v->last_requests.empty()) rc = load_requests(v);
+        } else {
+            rc = miss_loop(v, false);
+        }
+    }
+    if (rc == VOL_OK && !preview) v->have_forward = true;
     if (rc == VOL_OK || rc == VOL_ERR_INCOMPLETE) {
         CK(v, launch_tile_order(v->tile_cost, v->tile_order, (int)tiles, v->order_buckets, v->stream));
         v->stats.launches += 2;
@@ -1323,6 +1382,7 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
 
 int vol_render_resume(vol_t v) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     if (!v->out) return fail(v, VOL_ERR_NO_FORWARD_STATE, "no render to resume");
     if (v->nsusp == 0) return VOL_OK;
     if (int rc = run_pass(v, true, true)) return rc;
@@ -1349,6 +1409,7 @@ int vol_poll_requests(vol_t v, int32_t* out, int cap, int* n) {
 
 int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* dvoxel_dev) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     if (!drgba_dev) return fail(v, VOL_ERR_INVALID_ARG, "drgba is NULL");
     if (!v->have_forward || !v->grad) return fail(v, VOL_ERR_NO_FORWARD_STATE, "no gradient-mode render to differentiate");
     if (v->nsusp) return fail(v, VOL_ERR_NO_FORWARD_STATE, "last render is incomplete");
@@ -1384,6 +1445,7 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
 int vol_trace(vol_t v, const vol_camera* cam, const vol_params* params, const int32_t* pixels_host, int npix,
               int max_samples, vol_trace_rec* out_host, int32_t* counts_host) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     if (!cam || !params || !pixels_host || !out_host || !counts_host || npix < 0 || max_samples < 0)
         return fail(v, VOL_ERR_INVALID_ARG, "bad trace arguments");
     if (npix == 0) return VOL_OK;
@@ -1481,6 +1543,7 @@ int noalloc_scratch(vol_t v, unsigned char** out) {
 extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
                                   const vol_params* params, float* rgba_dev, int32_t* nsamples_dev) {
     if (!v) return VOL_ERR_INVALID_ARG;
+    if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
     if (!cams || !tf_dev || !params || !rgba_dev) return fail(v, VOL_ERR_INVALID_ARG, "null argument");
     if (nviews < 1 || nviews > VOL_NOALLOC_MAX_VIEWS)
         return fail(v, VOL_ERR_INVALID_ARG, "nviews must be 1..VOL_NOALLOC_MAX_VIEWS (64) for vol_render_noalloc");
