@@ -56,7 +56,7 @@ class _Camera(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("step", ctypes.c_float), ("et", ctypes.c_float), ("bg", ctypes.c_float * 4),
-                ("lod_mode", ctypes.c_int32), ("lod_bias", ctypes.c_int32)]
+                ("lod_mode", ctypes.c_int32), ("lod_bias", ctypes.c_int32), ("level_step", ctypes.c_int32)]
 
 
 class _Volume(ctypes.Structure):
@@ -140,11 +140,14 @@ def _cam(c: dict) -> _Camera:
     return s
 
 
-def _params(step=0.5, et=0.99, bg=(0, 0, 0, 0), lod_mode=0, lod_bias=0, **_ignored) -> _Params:
+def _params(step=0.5, et=0.99, bg=(0, 0, 0, 0), lod_mode=0, lod_bias=0, flags=0, level_step=False,
+            **_ignored) -> _Params:
+    """``flags`` is read for its level-step bit (16), as the library's render flags carry it."""
     p = _Params()
     p.step, p.et = float(np.float32(step)), float(np.float32(et))
     p.bg[:] = [float(np.float32(b)) for b in bg]
     p.lod_mode, p.lod_bias = int(lod_mode), int(lod_bias)
+    p.level_step = int(bool(level_step) or bool(int(flags) & 16))
     return p
 
 

@@ -57,6 +57,7 @@ typedef struct {
     float bg[4];        /* background RGBA behind the volume */
     int32_t lod_mode;   /* 0: every sample on level 0; 1: footprint LOD */
     int32_t lod_bias;   /* added to the footprint level before clamping */
+    int32_t level_step; /* 1: sample spacing and opacity scaled with the level (below) */
 } orc_params;
 
 typedef struct {
@@ -265,6 +266,17 @@ static inline float sample_t(const orc_ray *r, float dt, int64_t k)
     return r->t0 + (float)k * dt;
 }
 
+/*
+ * Level-scaled sampling (an extension: the paper fixes no step rule for coarse levels, Sec.
+ * V-C): a sample on level l stands for 2^l reference steps, so
+ *   t_0 = t0,  t_{k+1} = t_k + dt * 2^{l_k}   (binary32 sum; the scaling is exact),
+ * and its opacity is corrected to the longer step: a' = 1 - (1 - a)^(2^l).
+ */
+static inline float next_t_level_step(float t, float dt, int level)
+{
+    return t + ldexpf(dt, level);
+}
+
 /* Footprint scale: world size of one pixel at unit distance, in level-0
  * voxels: (2 * tan_half_fov) / h. */
 static inline float lod_scale(const orc_camera *c)
@@ -438,13 +450,15 @@ int64_t orc_trace(const orc_volume *V, const orc_camera *c, const orc_params *P,
     if (!r.hit) return 0;
     float scale = lod_scale(c);
     int64_t k = 0;
+    float t = r.t0;
+    int l = 0;
     for (;; ++k) {
-        float t = sample_t(&r, P->step, k);
+        t = P->level_step ? (k ? next_t_level_step(t, P->step, l) : r.t0) : sample_t(&r, P->step, k);
         if (!(t < r.t1)) break;
+        l = lod_level(t, scale, P->lod_bias, V->nlevels, P->lod_mode);
         if (k >= max_samples) continue;
         float p[3];
         for (int a = 0; a < 3; ++a) p[a] = r.o[a] + t * r.d[a];
-        int l = lod_level(t, scale, P->lod_bias, V->nlevels, P->lod_mode);
         orc_resolve R;
         resolve(V, l, p, &R);
         orc_trace_rec *q = &out[k];
@@ -525,12 +539,14 @@ static int64_t march(const orc_volume *V, const orc_camera *c, const float *tf, 
     if (amb_k) *amb_k = -1;
     if (!r->hit) return 0;
     int64_t k = 0;
+    float t = r->t0;
+    int l = 0;
     for (;; ++k) {
-        float t = sample_t(r, P->step, k);
+        t = P->level_step ? (k ? next_t_level_step(t, P->step, l) : r->t0) : sample_t(r, P->step, k);
         if (!(t < r->t1)) break;
         float p[3];
         for (int a = 0; a < 3; ++a) p[a] = r->o[a] + t * r->d[a];
-        int l = lod_level(t, scale, P->lod_bias, V->nlevels, P->lod_mode);
+        l = lod_level(t, scale, P->lod_bias, V->nlevels, P->lod_mode);
         orc_resolve R;
         if (!resolve_resident(V, l, p, resident, &R)) continue; /* preview: nothing resident here */
         orc_interp I;
@@ -538,6 +554,11 @@ static int64_t march(const orc_volume *V, const orc_camera *c, const float *tf, 
         orc_tflookup L;
         tf_lookup(tf, I.v, &L);
         double al = L.rgba[3];
+        if (P->level_step && l > 0) {
+            double om = 1.0 - al; /* (1 - a)^(2^l) by l squarings */
+            for (int q = 0; q < l; ++q) om *= om;
+            al = 1.0 - om;
+        }
         for (int ch = 0; ch < 3; ++ch) S->C[ch] += S->T * al * L.rgba[ch];
         S->T *= (1.0 - al);
         double margin = (1.0 - S->T) - (double)P->et;
@@ -676,6 +697,7 @@ int orc_render_max(const orc_volume *V, const orc_camera *c, const float *tf, co
 {
     if (V->nlevels < 1 || V->nlevels > ORC_MAX_LEVELS || V->brick < 1) return -1;
     if (mode != ORC_MOP && mode != ORC_MIP) return -1;
+    if (P->level_step) return -1;
     if (!pix) npix = (int64_t)c->w * c->h;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -750,7 +772,7 @@ int orc_render_grad(const orc_volume *V, const orc_camera *c, const float *tf, c
                     const int32_t *pix, int64_t npix, double amb, const double *dI,
                     const int32_t *alt_select, double *dtf, double *dvox, int nthreads)
 {
-    if (P->lod_mode != 0) return -1;
+    if (P->lod_mode != 0 || P->level_step) return -1;
     if (!pix) npix = (int64_t)c->w * c->h;
     const int64_t nvox = V->dims[0][0] * V->dims[0][1] * V->dims[0][2];
     int nt = 1;
