@@ -354,6 +354,15 @@ def run_ours(args, dist, rank, ws, local):
     ms_es = time_frames(torch, vol, cams, tf, dict(params, flags=2), max(5, args.steps // 4), args.warmup, flush)
     variants["skip_empty"] = {"ms_per_frame": statistics.mean(ms_es),
                               "samples_per_s": samples / (statistics.mean(ms_es) * 1e-3)}
+    if params.get("lod_mode"):
+        # level-scaled sampling: coarse levels take steps of dt 2^l with corrected opacity (a
+        # different, cheaper image of the same volume; reported beside the default line)
+        pl = dict(params, flags=16)
+        _, nsl = vol.render(cams, tf, pl, nsamples=True)
+        torch.cuda.synchronize()
+        sl = int(nsl.sum().item())
+        msl = statistics.mean(time_frames(torch, vol, cams, tf, pl, max(3, args.steps // 4), args.warmup, flush))
+        variants["level_step"] = {"ms_per_frame": msl, "samples_per_frame": sl, "samples_per_s": sl / (msl * 1e-3)}
     if not args.quick and args.workload in ("c2", "c3"):
         # maximum-opacity projection (the compositing of the paper's Kidney renderings) and
         # maximum-intensity projection: every ray runs to its exit unless it reaches the
@@ -481,7 +490,7 @@ def run_outofcore(args, dist, rank, ws, local):
     if not args.quick:
         # the same fly-through, cold cache: loading between passes only (no overlap), and with
         # empty-space skipping
-        for name, flags in (("serial_loads", 4), ("skip_empty", 2), ("preview", 8)):
+        for name, flags in (("serial_loads", 4), ("skip_empty", 2), ("preview", 8), ("level_step", 16)):
             v2 = P.Volume(wl["D"], "u8", wl["brick"], wl["levels"], cache_bytes=wl["cache_bytes"], layout="compact")
             v2.set_provider_batch(synth.brick_provider_address(), src, "u8")
             fr2 = flythrough(v2, dict(params, flags=flags))

@@ -92,6 +92,12 @@ typedef struct {
  * image; vol_stats.preview_samples counts the samples not on their own level (0: the image is
  * the full render's).  Not with VOL_RENDER_GRAD. */
 #define VOL_RENDER_PREVIEW 8u
+/* Level-scaled sampling (emission/absorption, no gradients): a sample on LOD level l stands
+ * for 2^l reference steps.  t_0 = t0, t_{k+1} = t_k + step * 2^{l_k} (binary32), and the
+ * sample's opacity is corrected to the longer step, a' = 1 - (1 - a)^(2^l), so a constant
+ * medium keeps its transmittance while coarse levels take fewer samples.  Empty-space
+ * skipping is not applied in this mode. */
+#define VOL_RENDER_LEVEL_STEP 16u
 
 /* Compositing (vol_params.composite).
  * VOL_COMPOSITE_DVR: front-to-back emission/absorption with early termination (Sec. IV-A).

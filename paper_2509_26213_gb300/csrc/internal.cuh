@@ -52,7 +52,7 @@ struct ViewDev {
 struct SuspRec {       // a ray waiting for a brick
     long long ray;     // packed pixel index
     int k;             // next sample
-    int pad;
+    int tk_bits;       // level-scaled sampling: depth of sample k (float bits)
     float C[3], T;     // partial colour and transmittance
 };
 
@@ -83,6 +83,7 @@ struct RenderDev {
     int lod_mode, lod_bias;
     int skip_empty;     // skip bricks whose value range the TF maps to zero opacity
     int preview;        // a sample on a non-resident brick uses the finest coarser resident level
+    int level_step;     // level-scaled sampling (chooses the kernel variant)
     float4* out;
     int* nsamp;
     unsigned* counters;
@@ -132,6 +133,7 @@ struct TraceDev {
     ViewDev view;
     float step;
     int lod_mode, lod_bias;
+    int level_step;     // samples dt * 2^l apart (level-scaled sampling)
     const int* pixels;
     int npix;
     int max_samples;
@@ -147,6 +149,8 @@ cudaError_t launch_trace(const TraceDev& p, cudaStream_t s);
 int render_blocks_per_sm(int dtype, bool grad);
 // Maximum projections (kernels_project.cu): the k_render variant for mode kMop or kMip.
 const void* pick_render_projection(int dtype, int brick, bool quad, bool lod, int mode);
+// Level-scaled sampling (kernels_lstep.cu): the emission/absorption variant.
+const void* pick_render_level_step(int dtype, int brick, bool quad, bool lod);
 // order[] = tiles sorted by descending log2 bucket of cost[] (heaviest first); zeroes cost[].
 // buckets: 64 ints of device scratch.
 cudaError_t launch_tile_order(int* cost, int* order, int ntiles, int* buckets, cudaStream_t s);

@@ -320,13 +320,15 @@ __global__ void k_trace(const __grid_constant__ TraceDev P) {
     make_ray(P.view, P.vol.D0f, P.pixels[2 * q], P.pixels[2 * q + 1], R);
     int k = 0;
     if (R.hit) {
+        float t = R.t0;
+        int l = 0;
         for (;; ++k) {
-            const float t = __fadd_rn(R.t0, __fmul_rn((float)k, P.step));
+            t = P.level_step ? (k ? next_t_level_step(t, P.step, l) : R.t0) : __fadd_rn(R.t0, __fmul_rn((float)k, P.step));
             if (!(t < R.t1)) break;
+            l = P.lod_mode ? lod_level(t, P.view.lodscale, P.lod_bias, P.vol.nlevels) : 0;
             if (k >= P.max_samples) continue;
             const float p[3] = {__fadd_rn(R.o[0], __fmul_rn(t, R.d[0])), __fadd_rn(R.o[1], __fmul_rn(t, R.d[1])),
                                 __fadd_rn(R.o[2], __fmul_rn(t, R.d[2]))};
-            const int l = P.lod_mode ? lod_level(t, P.view.lodscale, P.lod_bias, P.vol.nlevels) : 0;
             const LevelDev& L = P.vol.lv[l];
             Resolved Q;
             resolve(L, P.vol.bshift, P.vol.bmask, P.vol.quad ? P.vol.B1 - 1 : P.vol.B1, p, Q);
@@ -386,9 +388,13 @@ const void* pick_backward(int dtype) {
 }  // namespace
 
 cudaError_t launch_render(int dtype, int mode, const RenderDev& p, int grid, cudaStream_t s) {
-    const void* fn = (mode == kMop || mode == kMip)
-                         ? pick_render_projection(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0, mode)
-                         : pick_render(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0, mode == kDvrGrad);
+    const void* fn = nullptr;
+    if (mode == kMop || mode == kMip)
+        fn = pick_render_projection(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0, mode);
+    else if (p.level_step && mode == kDvr)
+        fn = pick_render_level_step(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0);
+    else if (!p.level_step)
+        fn = pick_render(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0, mode == kDvrGrad);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&p};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kRenderThreads), args, 0, s);

@@ -363,9 +363,9 @@ __device__ __noinline__ int brick_last_sample(int k_start, uint32_t pti_start, c
     return ke;
 }
 
-// Progressive preview (Sec. IV-B: a low-resolution image from coarser levels first): sample k,
-// whose brick on its level is not resident, on the finest coarser level whose brick at the
-// same position is resident.  ok = false when no level is.
+// Progressive preview (Sec. IV-B: a low-resolution image from coarser levels first): the
+// sample at depth t, whose brick on its level is not resident, on the finest coarser level
+// whose brick at the same position is resident.  ok = false when no level is.
 struct Fallback {
     uint32_t slot, local;
     float w[3];
@@ -373,16 +373,14 @@ struct Fallback {
 };
 
 template <bool LOD>
-__device__ __noinline__ Fallback preview_fallback(const uint32_t* __restrict__ pt, int k, float o0, float o1,
-                                                  float o2, float d0, float d1, float d2, float t0, float step,
-                                                  float lodscale, int bias, int nlev, const LevelDev* s_lv,
-                                                  int bshift, int bmask, int row) {
+__device__ __noinline__ Fallback preview_fallback(const uint32_t* __restrict__ pt, float t, float o0, float o1,
+                                                  float o2, float d0, float d1, float d2, float lodscale, int bias,
+                                                  int nlev, const LevelDev* s_lv, int bshift, int bmask, int row) {
     Fallback F;
     F.ok = false;
     F.slot = 0;
     F.local = 0;
     F.w[0] = F.w[1] = F.w[2] = 0.0f;
-    const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
     const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
                         __fadd_rn(o2, __fmul_rn(t, d2))};
     const int l = LOD ? lod_level(t, lodscale, bias, nlev) : 0;
@@ -458,7 +456,7 @@ __device__ __forceinline__ void request_brick(const RenderDev& P, uint32_t key) 
 }
 
 __device__ __forceinline__ void suspend_ray(const RenderDev& P, long long ray, int k, float C0, float C1, float C2,
-                                            float T) {
+                                            float T, float tk) {
     const unsigned m = __activemask();
     const int leader = __ffs(m) - 1;
     const unsigned lane = threadIdx.x & 31;
@@ -470,7 +468,7 @@ __device__ __forceinline__ void suspend_ray(const RenderDev& P, long long ray, i
         SuspRec r;
         r.ray = ray;
         r.k = k;
-        r.pad = 0;
+        r.tk_bits = __float_as_int(tk);
         r.C[0] = C0;
         r.C[1] = C1;
         r.C[2] = C2;
@@ -496,9 +494,9 @@ __host__ __device__ constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x
 
 // One sample's compositing step for mode MODE (lane state C0..C2, T as k_render keeps it);
 // returns true when the ray may stop after it.
-template <int DT, int MODE>
+template <int DT, int MODE, bool LS = false>
 __device__ __forceinline__ bool composite_sample(float val, const float4* s_tf, const float4* s_tfd, float amax_tf,
-                                                 float et, float& T, float& C0, float& C1, float& C2) {
+                                                 float et, float& T, float& C0, float& C1, float& C2, int l = 0) {
     const float x = tf_coord<DT>(val);
     if (MODE == kMip) {
         if (x > T) T = x;
@@ -517,6 +515,17 @@ __device__ __forceinline__ bool composite_sample(float val, const float4* s_tf, 
         }
         return T >= amax_tf;
     }
+    if (LS && l > 0) {
+        // level-scaled step: the sample stands for 2^l reference steps, 1 - a' = (1 - a)^(2^l)
+        float om = 1.0f - al;
+        for (int q = 0; q < l; ++q) om = om * om;
+        const float Ta = T * (1.0f - om);
+        C0 = fmaf(Ta, fmaf(wt, dab.x, a.x), C0);
+        C1 = fmaf(Ta, fmaf(wt, dab.y, a.y), C1);
+        C2 = fmaf(Ta, fmaf(wt, dab.z, a.z), C2);
+        T = T * om;
+        return __fsub_rn(1.0f, T) >= et;
+    }
     const float Ta = T * al;
     C0 = fmaf(Ta, fmaf(wt, dab.x, a.x), C0);
     C1 = fmaf(Ta, fmaf(wt, dab.y, a.y), C1);
@@ -525,12 +534,22 @@ __device__ __forceinline__ bool composite_sample(float val, const float4* s_tf, 
     return __fsub_rn(1.0f, T) >= et;
 }
 
+// Level-scaled sampling: the sample after one at t on level l lies dt * 2^l further (the
+// scaling by an exact power of two does not round).
+__device__ __forceinline__ float next_t_level_step(float t, float step, int l) {
+    return __fadd_rn(t, __fmul_rn(step, (float)(1 << l)));
+}
+
 // BS: brick edge known at compile time (32 or 64), or 0 for any power of two read at run time.
 // MODE: kDvr, kDvrGrad, kMop or kMip.  Lane state (C0, C1, C2, T): emission/absorption keeps
 // the partial colour and the transmittance; MOP the kept sample's colour and opacity (T,
 // starting at 0); MIP the largest TF coordinate so far (T, starting at -1).
-template <int DT, bool LOD, int MODE, int BS, bool Q>
+// LS: level-scaled sampling (emission/absorption only): sample k+1 lies dt * 2^l past sample k
+// on level l, whose opacity is corrected to that longer step; t of the lane's next sample is
+// kept in tcur (and in a suspended ray's record).
+template <int DT, bool LOD, int MODE, int BS, bool Q, bool LS = false>
 __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const __grid_constant__ RenderDev P) {
+    static_assert(!LS || MODE == kDvr, "level-scaled sampling is for emission/absorption without gradients");
     constexpr bool GRAD = MODE == kDvrGrad;
     constexpr float kT0 = MODE == kMop ? 0.0f : (MODE == kMip ? -1.0f : 1.0f);
     __shared__ float4 s_tf[256];
@@ -585,6 +604,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
     float o0 = 0, o1 = 0, o2 = 0, d0 = 0, d1 = 0, d2 = 0, t0 = 0, t1 = 0, lodscale = 0;
     int k = 0;
     float C0 = 0, C1 = 0, C2 = 0, T = kT0;
+    float tcur = 0.0f;  // LS: depth of sample k
     uint32_t cur_pti = kInvalidSlot;
     bool cur_empty = false;  // the brick of cur_pti has zero opacity everywhere
     const int nlev = P.vol.nlevels;
@@ -625,7 +645,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
             pool_next = min(pool_cnt, pool_next + __popc(need));
             if (!active && idx < pool_cnt) {
                 int view, px, py, k0 = 0;
-                float c0 = 0.f, c1 = 0.f, c2 = 0.f, tt = kT0;
+                float c0 = 0.f, c1 = 0.f, c2 = 0.f, tt = kT0, tk0 = 0.f;
                 bool ok;
                 if (!P.resume) {
                     view = pool_a;
@@ -641,6 +661,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     c1 = r.C[1];
                     c2 = r.C[2];
                     tt = r.T;
+                    tk0 = __int_as_float(r.tk_bits);
                     view = find_view_ray(P.views, P.nviews, ray);
                     const long long loc = ray - P.views[view].ray_off;
                     px = (int)(loc % P.views[view].w);
@@ -658,6 +679,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         t0 = R.t0; t1 = R.t1;
                         lodscale = P.views[view].lodscale;
                         k = k0; C0 = c0; C1 = c1; C2 = c2; T = tt;
+                        if (LS) tcur = P.resume ? tk0 : R.t0;
                         cur_pti = kInvalidSlot;
                     } else {
                         P.out[ray] = P.bg;
@@ -678,9 +700,12 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 uint32_t pti[kBatch], loc[kBatch];
                 float wgt[kBatch][3];
                 int nvalid = kBatch;
+                float tv[kBatch + 1];  // LS: depths of samples k .. k + kBatch
+                int lv[kBatch];        // LS: their levels
+                tv[0] = tcur;
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
-                    const float t = __fadd_rn(t0, __fmul_rn((float)(k + j), step));
+                    const float t = LS ? tv[j] : __fadd_rn(t0, __fmul_rn((float)(k + j), step));
                     if (!(t < t1) && nvalid == kBatch) nvalid = j;
                     const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
                                         __fadd_rn(o2, __fmul_rn(t, d2))};
@@ -690,6 +715,10 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                             cur_l = l;
                             L = load_lv(s_lv[l]);
                         }
+                    }
+                    if (LS) {
+                        lv[j] = LOD ? cur_l : 0;
+                        tv[j + 1] = next_t_level_step(t, step, lv[j]);
                     }
                     Resolved R;
                     resolve_reg(L, bshift, bmask, row, p, R);
@@ -716,7 +745,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         if (pti[j] != cur_pti) {
                             cur_pti = pti[j];
                             if (P.last_used) P.last_used[slot[j]] = P.frame;
-                            if (P.skip_empty) {
+                            if (!LS && P.skip_empty) {
                                 const float2 rng = __ldg(P.vol.range + slot[j]);
                                 if (MODE == kMop) cur_empty = brick_below_alpha<DT>(rng, s_amx, T);
                                 else if (MODE == kMip) cur_empty = brick_below_coord<DT>(rng, T);
@@ -741,8 +770,10 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     if (j < stop && !fin) {
                         if (GRAD && k > 0 && (k & (kCkptEvery - 1)) == 0)
                             P.ckpt[(long long)(k / kCkptEvery - 1) * P.nrays + ray] = T;
-                        fin = composite_sample<DT, MODE>(val[j], s_tf, s_tfd, amax_tf, et, T, C0, C1, C2);
+                        fin = composite_sample<DT, MODE, LS>(val[j], s_tf, s_tfd, amax_tf, et, T, C0, C1, C2,
+                                                             LS ? lv[j] : 0);
                         ++k;
+                        if (LS) tcur = tv[j + 1];
                     }
                 }
                 bool fell = false;
@@ -753,15 +784,18 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     if (P.req_table && pti[miss_at] != cur_pti) request_brick(P, pti[miss_at] + 1u);
                     cur_pti = pti[miss_at];
                     cur_empty = false;
-                    const Fallback F = preview_fallback<LOD>(P.vol.pt, k, o0, o1, o2, d0, d1, d2, t0, step, lodscale,
+                    const float tk = LS ? tcur : __fadd_rn(t0, __fmul_rn((float)k, step));
+                    const int lk = LOD ? lod_level(tk, lodscale, P.lod_bias, nlev) : 0;
+                    const Fallback F = preview_fallback<LOD>(P.vol.pt, tk, o0, o1, o2, d0, d1, d2, lodscale,
                                                              P.lod_bias, nlev, s_lv, bshift, bmask, row);
                     if (F.ok) {
                         if (P.last_used) P.last_used[F.slot] = P.frame;
                         const float v = sample_value<DT, BS, Q>(
                             P.vol.atlas, (unsigned long long)F.slot * slot_stride + F.local, B1, F.w);
-                        fin = composite_sample<DT, MODE>(v, s_tf, s_tfd, amax_tf, et, T, C0, C1, C2);
+                        fin = composite_sample<DT, MODE, LS>(v, s_tf, s_tfd, amax_tf, et, T, C0, C1, C2, lk);
                     }
                     ++k;
+                    if (LS) tcur = next_t_level_step(tk, step, lk);
                     fell = true;
                     const unsigned m = __activemask();
                     if ((int)lane == __ffs(m) - 1) atomicAdd(&P.counters[kPreview], (unsigned)__popc(m));
@@ -808,7 +842,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     // wait for the missing brick: sample k (= the first missing one) resumes later
                     if (P.req_table) {
                         request_brick(P, miss_pti + 1u);
-                        suspend_ray(P, ray, k, C0, C1, C2, T);
+                        suspend_ray(P, ray, k, C0, C1, C2, T, LS ? tcur : 0.0f);
                     } else {
                         atomicAdd(&P.counters[kDevError], 1u);
                     }

@@ -427,6 +427,7 @@ RenderDev render_args(vol_t v) {
     p.lod_bias = v->params.lod_bias;
     p.skip_empty = (v->params.flags & VOL_RENDER_SKIP_EMPTY) ? 1 : 0;
     p.preview = (v->params.flags & VOL_RENDER_PREVIEW) ? 1 : 0;
+    p.level_step = (v->params.flags & VOL_RENDER_LEVEL_STEP) ? 1 : 0;
     p.out = (float4*)v->out;
     p.nsamp = v->nsamp;
     p.counters = v->counters;
@@ -1270,6 +1271,8 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         return fail(v, VOL_ERR_UNSUPPORTED, "gradients need emission/absorption compositing");
     const bool preview = (p.flags & VOL_RENDER_PREVIEW) != 0;
     if (grad && preview) return fail(v, VOL_ERR_UNSUPPORTED, "a preview keeps no gradient state");
+    if ((p.flags & VOL_RENDER_LEVEL_STEP) && (grad || p.composite != VOL_COMPOSITE_DVR))
+        return fail(v, VOL_ERR_UNSUPPORTED, "level-scaled sampling is for emission/absorption without gradients");
 
     // view table
     v->views_host.resize(nviews);
@@ -1469,6 +1472,7 @@ int vol_trace(vol_t v, const vol_camera* cam, const vol_params* params, const in
     t.view.h = cam->h;
     t.step = params->step;
     t.lod_mode = params->lod_mode;
+    t.level_step = (params->flags & VOL_RENDER_LEVEL_STEP) ? 1 : 0;
     t.lod_bias = params->lod_bias;
     t.npix = npix;
     t.max_samples = max_samples;
@@ -1559,6 +1563,8 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
         return fail(v, VOL_ERR_INVALID_ARG, "composite must be VOL_COMPOSITE_DVR, _MOP or _MIP");
     if (p.flags & VOL_RENDER_GRAD)
         return fail(v, VOL_ERR_UNSUPPORTED, "vol_render_noalloc keeps no gradient state; use vol_render");
+    if ((p.flags & VOL_RENDER_LEVEL_STEP) && p.composite != VOL_COMPOSITE_DVR)
+        return fail(v, VOL_ERR_UNSUPPORTED, "level-scaled sampling is for emission/absorption");
     if (!all_resident(v, p.lod_mode != 0))
         return fail(v, VOL_ERR_UNSUPPORTED, "vol_render_noalloc needs every brick of the used levels resident");
 
@@ -1612,6 +1618,7 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
     r.lod_mode = p.lod_mode;
     r.lod_bias = p.lod_bias;
     r.skip_empty = (p.flags & VOL_RENDER_SKIP_EMPTY) ? 1 : 0;
+    r.level_step = (p.flags & VOL_RENDER_LEVEL_STEP) ? 1 : 0;
     r.out = (float4*)rgba_dev;
     r.nsamp = nsamples_dev;
     r.counters = counters;
