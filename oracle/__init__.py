@@ -108,6 +108,7 @@ def _load():
                                            ctypes.POINTER(_Params), ctypes.c_int, vp, vp, ctypes.c_int64,
                                            ctypes.c_double, vp, vp, vp, vp, ctypes.c_int]
             lib.orc_render_max.restype = ctypes.c_int
+            lib.orc_downsample_transpose.argtypes = [i64p, vp, vp]
             lib.orc_render_grad.argtypes = [ctypes.POINTER(_Volume), ctypes.POINTER(_Camera), vp,
                                             ctypes.POINTER(_Params), vp, ctypes.c_int64,
                                             ctypes.c_double, vp, vp, vp, vp, ctypes.c_int]
@@ -189,6 +190,16 @@ def downsample(a: np.ndarray, dtype: str) -> np.ndarray:
     rc = _load().orc_downsample(code, _dims((Dx, Dy, Dz)), a.ctypes.data, out.ctypes.data)
     if rc:
         raise RuntimeError("orc_downsample failed")
+    return out
+
+
+def downsample_transpose(g_coarse: np.ndarray, fine_shape) -> np.ndarray:
+    """Adjoint of one box-filter level: float64 gradient on the finer level (Dz, Dy, Dx)."""
+    g_coarse = np.ascontiguousarray(g_coarse, dtype=np.float64)
+    Dz, Dy, Dx = fine_shape
+    assert g_coarse.shape == ((Dz + 1) // 2, (Dy + 1) // 2, (Dx + 1) // 2)
+    out = np.zeros(fine_shape)
+    _load().orc_downsample_transpose(_dims((Dx, Dy, Dz)), g_coarse.ctypes.data, out.ctypes.data)
     return out
 
 
@@ -336,7 +347,8 @@ def render_max(vol: Volume, cam: dict, tf: np.ndarray, params: dict, mode: str, 
 
 def render_grad(vol: Volume, cam: dict, tf: np.ndarray, params: dict, dI: np.ndarray, pixels=None,
                 alt_select=None, amb=1e-5, nthreads=0):
-    """FP64 gradients (dL/dtf [256,4], dL/dvoxel level-0 shaped (Dz,Dy,Dx)) for dL/dI [n,4]."""
+    """FP64 gradients (dL/dtf [256,4], dL/dvoxel level-0 shaped (Dz,Dy,Dx)) for dL/dI [n,4]; with
+    footprint LOD the coarser levels' gradients reach level 0 through the box filter's adjoint."""
     tf = np.ascontiguousarray(tf, dtype=np.float32)
     if pixels is None:
         npix, pp = int(cam["w"]) * int(cam["h"]), None

@@ -753,6 +753,34 @@ int orc_render_max(const orc_volume *V, const orc_camera *c, const float *tf, co
 /* --------------------------------------------------------- adjoint */
 
 /*
+ * Adjoint of one level of the box filter (orc_downsample), for gradients with respect to
+ * the finer level: each coarse voxel c hands g_coarse[c] / 8 to each of its 8 children
+ * 2c + d, d in {0,1}^3, a child index beyond the fine edge replaced by the last fine voxel
+ * exactly as the filter replaces it (so an edge voxel can receive several shares).  The
+ * filter is the mean of the children; for integer storage its rounding is taken as the mean
+ * (its derivative is 1/8 per child almost everywhere).  Accumulates into g_fine.
+ */
+void orc_downsample_transpose(const int64_t Dfine[3], const double *g_coarse, double *g_fine)
+{
+    int64_t Dc[3];
+    for (int a = 0; a < 3; ++a) Dc[a] = (Dfine[a] + 1) / 2;
+    for (int64_t z = 0; z < Dc[2]; ++z)
+        for (int64_t y = 0; y < Dc[1]; ++y)
+            for (int64_t x = 0; x < Dc[0]; ++x) {
+                const double share = g_coarse[x + Dc[0] * (y + Dc[1] * z)] / 8.0;
+                for (int dz = 0; dz < 2; ++dz)
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) {
+                            int64_t cx = 2 * x + dx, cy = 2 * y + dy, cz = 2 * z + dz;
+                            if (cx > Dfine[0] - 1) cx = Dfine[0] - 1;
+                            if (cy > Dfine[1] - 1) cy = Dfine[1] - 1;
+                            if (cz > Dfine[2] - 1) cz = Dfine[2] - 1;
+                            g_fine[cx + Dfine[0] * (cy + Dfine[1] * cz)] += share;
+                        }
+            }
+}
+
+/*
  * Gradient of L with respect to the transfer function and to the normalised
  * voxel values of level 0, given dL/dI per pixel (I = output RGBA).  Not in
  * the paper (which does not differentiate); it is the exact derivative of the
@@ -765,16 +793,23 @@ int orc_render_max(const orc_volume *V, const orc_camera *c, const float *tf, co
  * d, zero when the clamp is active) and the trilinear weights to the voxels.
  * The early-termination index n is held fixed (alt_select[i] = 1 flips the
  * ambiguous decision as in orc_render).  T_k here are plain float64 products.
- * Only every sample on level 0 is supported (lod_mode 0).  dtf [256][4] and
- * dvox [level-0 voxels] are float64 and are accumulated into (+=).
+ * With footprint LOD a sample on level l contributes to the voxels of level l,
+ * and each level's gradient reaches level 0 through the adjoint of the box filter
+ * that made the level (orc_downsample_transpose), coarsest level first.
+ * dtf [256][4] and dvox [level-0 voxels] are float64 and are accumulated into (+=).
  */
 int orc_render_grad(const orc_volume *V, const orc_camera *c, const float *tf, const orc_params *P,
                     const int32_t *pix, int64_t npix, double amb, const double *dI,
                     const int32_t *alt_select, double *dtf, double *dvox, int nthreads)
 {
-    if (P->lod_mode != 0 || P->level_step) return -1;
+    if (P->level_step) return -1;
     if (!pix) npix = (int64_t)c->w * c->h;
-    const int64_t nvox = V->dims[0][0] * V->dims[0][1] * V->dims[0][2];
+    /* per-level gradients, levels laid end to end */
+    int64_t lvoff[ORC_MAX_LEVELS + 1];
+    lvoff[0] = 0;
+    for (int l = 0; l < V->nlevels; ++l) lvoff[l + 1] = lvoff[l] + V->dims[l][0] * V->dims[l][1] * V->dims[l][2];
+    const int64_t nvox = lvoff[V->nlevels];
+    const float scale = lod_scale(c);
     int nt = 1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -799,6 +834,7 @@ int orc_render_grad(const orc_volume *V, const orc_camera *c, const float *tf, c
         orc_interp *Is = NULL;
         orc_tflookup *Ls = NULL;
         double *Ts = NULL;
+        int *Lv = NULL;
         if (!myvox) err = 1;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 16)
@@ -819,15 +855,17 @@ int orc_render_grad(const orc_volume *V, const orc_camera *c, const float *tf, c
                 Is = realloc(Is, sizeof(orc_interp) * cap);
                 Ls = realloc(Ls, sizeof(orc_tflookup) * cap);
                 Ts = realloc(Ts, sizeof(double) * cap);
+                Lv = realloc(Lv, sizeof(int) * cap);
             }
-            /* forward again, keeping every sample (level 0 only) */
+            /* forward again, keeping every sample */
             double T = 1.0;
             for (int64_t k = 0; k < n; ++k) {
                 float t = sample_t(&r, P->step, k);
                 float p[3];
                 for (int a = 0; a < 3; ++a) p[a] = r.o[a] + t * r.d[a];
+                Lv[k] = lod_level(t, scale, P->lod_bias, V->nlevels, P->lod_mode);
                 orc_resolve R;
-                resolve(V, 0, p, &R);
+                resolve(V, Lv[k], p, &R);
                 interp(V, &R, &Is[k]);
                 tf_lookup(tf, Is[k].v, &Ls[k]);
                 Ts[k] = T;
@@ -852,20 +890,31 @@ int orc_render_grad(const orc_volume *V, const orc_camera *c, const float *tf, c
                     dv += drgba[ch] * ((double)tf[4 * (L->i + 1) + ch] - (double)tf[4 * L->i + ch]);
                 }
                 dv = L->inside ? 255.0 * dv : 0.0;
-                for (int q = 0; q < 8; ++q) myvox[Is[k].corner[q]] += Is[k].cw[q] * dv;
+                for (int q = 0; q < 8; ++q) myvox[lvoff[Lv[k]] + Is[k].corner[q]] += Is[k].cw[q] * dv;
                 for (int ch = 0; ch < 4; ++ch) Rr[ch] = al * c4[ch] + (1.0 - al) * Rr[ch];
             }
         }
         free(Is);
         free(Ls);
         free(Ts);
+        free(Lv);
     }
+    double *gsum = calloc((size_t)nvox, sizeof(double));
+    if (!gsum) err = 1;
     for (int t = 0; t < nt; ++t) {
         for (int j = 0; j < 1024; ++j) dtf[j] += pdtf[1024 * t + j];
         if (pvox[t]) {
-            for (int64_t j = 0; j < nvox; ++j) dvox[j] += pvox[t][j];
+            if (gsum)
+                for (int64_t j = 0; j < nvox; ++j) gsum[j] += pvox[t][j];
             free(pvox[t]);
         }
+    }
+    if (gsum) {
+        /* coarsest level first: each level's gradient onto the level it was filtered from */
+        for (int l = V->nlevels - 1; l >= 1; --l)
+            orc_downsample_transpose(V->dims[l - 1], gsum + lvoff[l], gsum + lvoff[l - 1]);
+        for (int64_t j = 0; j < lvoff[1]; ++j) dvox[j] += gsum[j];
+        free(gsum);
     }
     free(pvox);
     free(pdtf);
