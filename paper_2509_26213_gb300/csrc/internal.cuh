@@ -119,8 +119,9 @@ struct BackwardDev {
     float4 bg;
     const float4* drgba;
     float* dtf;
-    float* dvox;
-    int D0[3];
+    float* dvox;                // level-0 gradient (NULL: none)
+    float* dlev[kMaxLevels];    // gradient of each level's voxels; dlev[0] = dvox
+    int lod_mode, lod_bias;
     unsigned* counters;
     const float* ckpt;
     long long nrays;
@@ -154,7 +155,7 @@ const void* pick_render_level_step(int dtype, int brick, bool quad, bool lod);
 // order[] = tiles sorted by descending log2 bucket of cost[] (heaviest first); zeroes cost[].
 // buckets: 64 ints of device scratch.
 cudaError_t launch_tile_order(int* cost, int* order, int ntiles, int* buckets, cudaStream_t s);
-int backward_blocks_per_sm(int dtype);
+int backward_blocks_per_sm(int dtype, bool lod);
 
 // ---- launchers (kernels_volume.cu) ----
 // Write every brick of a dense level (src of src_dtype) into atlas slots.
@@ -167,6 +168,10 @@ cudaError_t launch_upload_bricks(int dst_dtype, int src_dtype, const void* src, 
 // Build level `level` (all bricks; slots_of_bricks indexed by brick id) from level-1.
 cudaError_t launch_downsample(int dtype, const VolDev& vol, int level, const uint32_t* slots_of_bricks,
                               long long nbricks, unsigned* err, cudaStream_t s);
+// Adjoint of one box-filter level: fine[i] += coarse[parent(i)] * (shares of i) / 8, for the
+// level of dims Dfine filtered into the level of coarse (a child index past the edge counts as
+// the last voxel, as in the filter).
+cudaError_t launch_downsample_transpose(const float* coarse, float* fine, const int Dfine[3], cudaStream_t s);
 // range[slots[i]] = (min, max) of the stored values of each listed slot (one CTA per slot).
 cudaError_t launch_slot_range(int dtype, const VolDev& vol, float2* range, const uint32_t* slots, long long n,
                               cudaStream_t s);

@@ -64,14 +64,18 @@ constexpr int kBwdMinBlocks = VOLRC_BWD_MINB;
 // forward -- transmittance from the segment's checkpoint and the sample values into shared
 // memory, kBwdBatch samples at a time -- then in reverse, accumulating dL/dtf and dL/dvoxel.
 // Lanes take a new ray between rounds, so a warp waits only on segments, not on whole rays.
-template <int DT>
+// LOD: samples on footprint levels; the gradient of a level-l voxel goes to P.dlev[l], which
+// the host then carries down to level 0 through the box filter's adjoint.
+template <int DT, bool LOD>
 __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const __grid_constant__ BackwardDev P) {
     __shared__ float4 s_tf[256];
     __shared__ float s_dtf[1024];
     __shared__ float s_T[kCkptEvery][kBwdThreads];
     __shared__ float s_V[kCkptEvery][kBwdThreads];
+    __shared__ LevelDev s_lv[LOD ? kMaxLevels : 1];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = P.tf[i];
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) s_dtf[i] = 0.0f;
+    if (LOD && threadIdx.x < P.vol.nlevels) s_lv[threadIdx.x] = P.vol.lv[threadIdx.x];
     __syncthreads();
 
     using VT = typename Voxel<DT>::T;
@@ -83,15 +87,19 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
     const bool quad = P.vol.quad != 0;
     const int row = quad ? B1 - 1 : B1;
     const unsigned long long slot_stride = quad ? P.vol.slot_entries : P.vol.slot_elems;
-    const LvReg L0 = load_lv(P.vol.lv[0]);
-    const int Dx = P.D0[0], Dy = P.D0[1];
+    LvReg L0 = load_lv(P.vol.lv[0]);  // LOD: the level of the last resolved sample
+    // voxels along x and y of level l (the shared level table when LOD)
+    auto dim_x = [&](int l) { return LOD ? s_lv[l].D[0] : P.vol.lv[0].D[0]; };
+    auto dim_y = [&](int l) { return LOD ? s_lv[l].D[1] : P.vol.lv[0].D[1]; };
+    int cur_l = 0;
+    const int nlev = P.vol.nlevels;
     const float step = P.step;
     // per-lane accumulators: dL/dtf for entries acc_i, acc_i + 1; dL/dvoxel for the 8 corners
-    // of cell cell_cur (cell_mask: which +1 corners exist)
+    // of cell cell_cur on level cell_lvl (cell_mask: which +1 corners exist)
     int acc_i = -1;
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     long long cell_cur = -1;
-    int cell_mask = 0;
+    int cell_mask = 0, cell_lvl = 0;
     float cacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 
     // warp-uniform tile pool
@@ -100,7 +108,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
     // lane state
     bool has = false;
     long long ray = 0;
-    float o0 = 0, o1 = 0, o2 = 0, d0 = 0, d1 = 0, d2 = 0, t0 = 0;
+    float o0 = 0, o1 = 0, o2 = 0, d0 = 0, d1 = 0, d2 = 0, t0 = 0, lodscale = 0;
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     float R0 = 0, R1 = 0, R2 = 0, R3 = 0;
     int n = 0, s = 0;
@@ -141,6 +149,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                         o0 = R.o[0]; o1 = R.o[1]; o2 = R.o[2];
                         d0 = R.d[0]; d1 = R.d[1]; d2 = R.d[2];
                         t0 = R.t0;
+                        lodscale = V.lodscale;
                         g = P.drgba[ray];
                         R0 = P.bg.x; R1 = P.bg.y; R2 = P.bg.z; R3 = P.bg.w;
                         s = (n - 1) / kCkptEvery;
@@ -165,6 +174,13 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                 const float t = __fadd_rn(t0, __fmul_rn((float)(k0 + jb + u), step));
                 const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
                                     __fadd_rn(o2, __fmul_rn(t, d2))};
+                if (LOD) {
+                    const int l = lod_level(t, lodscale, P.lod_bias, nlev);
+                    if (l != cur_l) {
+                        cur_l = l;
+                        L0 = load_lv(s_lv[l]);
+                    }
+                }
                 Resolved Q;
                 resolve_reg(L0, bshift, bmask, row, p, Q);
                 pti[u] = Q.pti;
@@ -204,6 +220,13 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                 const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
                 const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
                                     __fadd_rn(o2, __fmul_rn(t, d2))};
+                if (LOD) {
+                    const int l = lod_level(t, lodscale, P.lod_bias, nlev);
+                    if (l != cur_l) {
+                        cur_l = l;
+                        L0 = load_lv(s_lv[l]);
+                    }
+                }
                 Resolved Q;
                 resolve_reg(L0, bshift, bmask, row, p, Q);
                 const float val = s_V[j][tid];
@@ -236,12 +259,15 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                 if (P.dvox && tf_inside<DT>(val)) {
                     const float dv = 255.0f * (dr * (b.x - a.x) + dg * (b.y - a.y) + db * (b.z - a.z) + dal * (b.w - a.w));
                     if (dv != 0.0f) {
-                        // register accumulation while the trilinear cell stays the same
+                        // register accumulation while the trilinear cell (and level) stays the same
+                        const int lq = LOD ? cur_l : 0;
+                        const int Dx = L0.Dm[0] + 1, Dy = L0.Dm[1] + 1;
                         const long long cell = (long long)Q.i0[0] + (long long)Dx * ((long long)Q.i0[1] + (long long)Dy * Q.i0[2]);
-                        if (cell != cell_cur) {
-                            flush_vox(P.dvox, cell_cur, cell_mask, Dx, Dy, cacc);
+                        if (cell != cell_cur || lq != cell_lvl) {
+                            flush_vox(P.dlev[cell_lvl], cell_cur, cell_mask, dim_x(cell_lvl), dim_y(cell_lvl), cacc);
                             cell_cur = cell;
-                            cell_mask = (Q.i0[0] < Dx - 1 ? 1 : 0) | (Q.i0[1] < Dy - 1 ? 2 : 0) | (Q.i0[2] < P.D0[2] - 1 ? 4 : 0);
+                            cell_lvl = lq;
+                            cell_mask = (Q.i0[0] < L0.Dm[0] ? 1 : 0) | (Q.i0[1] < L0.Dm[1] ? 2 : 0) | (Q.i0[2] < L0.Dm[2] ? 4 : 0);
                         }
                         const float wx = Q.w[0], wy = Q.w[1], wz = Q.w[2];
 #pragma unroll
@@ -261,7 +287,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
         if (has && --s < 0) has = false;
     }
     if (P.dtf) flush_dtf(s_dtf, acc_i, acc);
-    if (P.dvox) flush_vox(P.dvox, cell_cur, cell_mask, Dx, Dy, cacc);
+    if (P.dvox) flush_vox(P.dlev[cell_lvl], cell_cur, cell_mask, dim_x(cell_lvl), dim_y(cell_lvl), cacc);
     __syncthreads();
     if (P.dtf)
         for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
@@ -352,7 +378,7 @@ __global__ void k_trace(const __grid_constant__ TraceDev P) {
 
 template <int DT, int BS, bool Q>
 const void* pick_render_b(bool lod, bool grad) {
-    if (grad) return (const void*)k_render<DT, false, kDvrGrad, BS, Q>;
+    if (grad) return lod ? (const void*)k_render<DT, true, kDvrGrad, BS, Q> : (const void*)k_render<DT, false, kDvrGrad, BS, Q>;
     return lod ? (const void*)k_render<DT, true, kDvr, BS, Q> : (const void*)k_render<DT, false, kDvr, BS, Q>;
 }
 
@@ -375,15 +401,18 @@ const void* pick_render(int dtype, int brick, bool quad, bool lod, bool grad) {
     return nullptr;
 }
 
-const void* pick_backward(int dtype) {
+template <bool LOD>
+const void* pick_backward_l(int dtype) {
     switch (dtype) {
-    case VOL_U8: return (const void*)k_backward<VOL_U8>;
-    case VOL_U16: return (const void*)k_backward<VOL_U16>;
-    case VOL_F16: return (const void*)k_backward<VOL_F16>;
-    case VOL_F32: return (const void*)k_backward<VOL_F32>;
+    case VOL_U8: return (const void*)k_backward<VOL_U8, LOD>;
+    case VOL_U16: return (const void*)k_backward<VOL_U16, LOD>;
+    case VOL_F16: return (const void*)k_backward<VOL_F16, LOD>;
+    case VOL_F32: return (const void*)k_backward<VOL_F32, LOD>;
     }
     return nullptr;
 }
+
+const void* pick_backward(int dtype, bool lod) { return lod ? pick_backward_l<true>(dtype) : pick_backward_l<false>(dtype); }
 
 }  // namespace
 
@@ -401,7 +430,7 @@ cudaError_t launch_render(int dtype, int mode, const RenderDev& p, int grid, cud
 }
 
 cudaError_t launch_backward(int dtype, const BackwardDev& p, int grid, cudaStream_t s) {
-    const void* fn = pick_backward(dtype);
+    const void* fn = pick_backward(dtype, p.lod_mode != 0);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&p};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kBwdThreads), args, 0, s);
@@ -430,9 +459,9 @@ int render_blocks_per_sm(int dtype, bool grad) {
     return n > 0 ? n : 1;
 }
 
-int backward_blocks_per_sm(int dtype) {
+int backward_blocks_per_sm(int dtype, bool lod) {
     int n = 0;
-    const void* fn = pick_backward(dtype);
+    const void* fn = pick_backward(dtype, lod);
     if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBwdThreads, 0) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }

@@ -3,6 +3,8 @@
 // Slot layouts (include/vol.h): compact slots hold the (B+1)^3 voxels of a brick and its
 // +x/+y/+z apron; quad slots hold B x B x (B+1) entries of four voxels each, entry (x, y, z)
 // = voxels (x, y), (x+1, y), (x, y+1), (x+1, y+1) of slice z of that region.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace volrc {
@@ -242,6 +244,21 @@ __global__ void __launch_bounds__(kThreads) k_slot_range(const typename Stored<D
     }
 }
 
+// Adjoint of one box-filter level (k_downsample): fine voxel i has the single parent i >> 1 per
+// axis, and along an axis of odd size the last fine voxel fills both child places of its
+// parent (the filter replaces the missing child by it), so it takes 2 shares there.
+__global__ void k_downsample_transpose(const float* __restrict__ coarse, float* __restrict__ fine, int Fx, int Fy,
+                                       int Fz) {
+    const long long n = (long long)Fx * Fy * Fz;
+    const int Cx = (Fx + 1) / 2, Cy = (Fy + 1) / 2;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % Fx), y = (int)((i / Fx) % Fy), z = (int)(i / ((long long)Fx * Fy));
+        const int m = ((Fx & 1) && x == Fx - 1 ? 2 : 1) * ((Fy & 1) && y == Fy - 1 ? 2 : 1) * ((Fz & 1) && z == Fz - 1 ? 2 : 1);
+        const float g = coarse[(x >> 1) + (long long)Cx * ((y >> 1) + (long long)Cy * (z >> 1))];
+        if (g != 0.0f) fine[i] += g * (0.125f * (float)m);
+    }
+}
+
 __global__ void k_pt_update(uint32_t* pt, const uint32_t* idx, const uint32_t* val, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicExch(&pt[idx[i]], val[i]);
@@ -327,6 +344,14 @@ cudaError_t launch_slot_range(int dtype, const VolDev& vol, float2* range, const
         default: return cudaErrorInvalidValue;
         }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_downsample_transpose(const float* coarse, float* fine, const int Dfine[3], cudaStream_t s) {
+    const long long n = (long long)Dfine[0] * Dfine[1] * Dfine[2];
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((n + 255) / 256, 65536);
+    k_downsample_transpose<<<(unsigned)blocks, 256, 0, s>>>(coarse, fine, Dfine[0], Dfine[1], Dfine[2]);
     return cudaGetLastError();
 }
 

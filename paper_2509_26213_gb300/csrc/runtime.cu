@@ -158,6 +158,8 @@ struct vol_s {
     size_t ckpt_cap = 0;
     int* ray_n = nullptr;
     size_t ray_n_cap = 0;
+    float* dlev_buf = nullptr;  // adjoint with LOD: gradients of levels 1..L-1
+    size_t dlev_cap = 0;
 
     // provider
     vol_provider_fn prov = nullptr;
@@ -1033,7 +1035,7 @@ void vol_destroy(vol_t v) {
     else cudaDeviceSynchronize();
     void* bufs[] = {v->atlas, v->pt, v->last_used, v->counters, v->aux, v->upd_dev, v->views_dev, v->req_table,
                     v->req_list, v->susp[0], v->susp[1], v->ckpt, v->ray_n, v->stage_dev, v->stage_slots_dev,
-                    v->tile_cost, v->tile_order, v->order_buckets, v->range};
+                    v->tile_cost, v->tile_order, v->order_buckets, v->range, v->dlev_buf};
     for (void* b : bufs)
         if (b) cudaFree(b);
     void* hbufs[] = {v->stage_host, v->ring.host, v->ring.slots, v->ring.ptis, v->poll_host};
@@ -1266,7 +1268,6 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     if (p.composite < VOL_COMPOSITE_DVR || p.composite > VOL_COMPOSITE_MIP)
         return fail(v, VOL_ERR_INVALID_ARG, "composite must be VOL_COMPOSITE_DVR, _MOP or _MIP");
     const bool grad = (p.flags & VOL_RENDER_GRAD) != 0;
-    if (grad && p.lod_mode != 0) return fail(v, VOL_ERR_UNSUPPORTED, "gradients need lod_mode 0");
     if (grad && p.composite != VOL_COMPOSITE_DVR)
         return fail(v, VOL_ERR_UNSUPPORTED, "gradients need emission/absorption compositing");
     const bool preview = (p.flags & VOL_RENDER_PREVIEW) != 0;
@@ -1416,7 +1417,9 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
     if (!drgba_dev) return fail(v, VOL_ERR_INVALID_ARG, "drgba is NULL");
     if (!v->have_forward || !v->grad) return fail(v, VOL_ERR_NO_FORWARD_STATE, "no gradient-mode render to differentiate");
     if (v->nsusp) return fail(v, VOL_ERR_NO_FORWARD_STATE, "last render is incomplete");
-    if (!all_resident(v, false)) return fail(v, VOL_ERR_NO_FORWARD_STATE, "level 0 changed since the render");
+    const bool lod = v->params.lod_mode != 0;
+    if (!all_resident(v, lod))
+        return fail(v, VOL_ERR_NO_FORWARD_STATE, lod ? "a level is no longer fully resident" : "level 0 changed since the render");
     if (!dtf_dev && !dvoxel_dev) return VOL_OK;
     BackwardDev b{};
     b.vol = vol_dev(v);
@@ -1431,7 +1434,22 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
     b.drgba = (const float4*)drgba_dev;
     b.dtf = dtf_dev;
     b.dvox = dvoxel_dev;
-    for (int a = 0; a < 3; ++a) b.D0[a] = (int)v->lay.dims[a];
+    b.lod_mode = v->params.lod_mode;
+    b.lod_bias = v->params.lod_bias;
+    b.dlev[0] = dvoxel_dev;
+    if (lod && dvoxel_dev) {
+        // gradient buffers for levels 1..L-1, zeroed; carried down to level 0 after the kernel
+        size_t tot = 0;
+        for (int l = 1; l < v->L; ++l)
+            tot += (size_t)(v->lay.level_dims[l][0] * v->lay.level_dims[l][1] * v->lay.level_dims[l][2]);
+        if (int rc = ensure(v, v->dlev_buf, v->dlev_cap, tot, "level gradient buffers")) return rc;
+        CK(v, cudaMemsetAsync(v->dlev_buf, 0, sizeof(float) * tot, v->stream));
+        size_t off = 0;
+        for (int l = 1; l < v->L; ++l) {
+            b.dlev[l] = v->dlev_buf + off;
+            off += (size_t)(v->lay.level_dims[l][0] * v->lay.level_dims[l][1] * v->lay.level_dims[l][2]);
+        }
+    }
     b.counters = v->counters;
     b.ckpt = v->ckpt;
     b.nrays = v->nrays;
@@ -1439,9 +1457,18 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
     // the order built from this forward's per-tile sample counts: the heaviest tiles first
     b.tile_order = v->order_ready ? v->tile_order : nullptr;
     CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
-    const int grid = backward_blocks_per_sm(v->dtype) * v->nsm;
+    const int grid = backward_blocks_per_sm(v->dtype, lod) * v->nsm;
     CK(v, launch_backward(v->dtype, b, grid, v->stream));
     v->stats.launches += 1;
+    if (lod && dvoxel_dev) {
+        // each level's gradient onto the level it was filtered from, coarsest first (Sec. III-D)
+        for (int l = v->L - 1; l >= 1; --l) {
+            const int Df[3] = {(int)v->lay.level_dims[l - 1][0], (int)v->lay.level_dims[l - 1][1],
+                               (int)v->lay.level_dims[l - 1][2]};
+            CK(v, launch_downsample_transpose(b.dlev[l], b.dlev[l - 1], Df, v->stream));
+            v->stats.launches += 1;
+        }
+    }
     return VOL_OK;
 }
 

@@ -244,13 +244,16 @@ class RaycastFn(torch.autograd.Function):
     """rgba = RaycastFn.apply(density, tf, volume, cams, params).
 
     density: float32 CUDA tensor (Dz, Dy, Dx) of normalised level-0 values, uploaded into
-    ``volume`` (an f32 Volume) on every forward; tf: float32 CUDA (256, 4).  Backward gives
-    dL/d(density) and dL/d(tf) through the adjoint kernel.  The backward must run before the
-    next render on the same volume."""
+    ``volume`` (an f32 Volume) on every forward, its coarser levels rebuilt when the render
+    uses footprint LOD; tf: float32 CUDA (256, 4).  Backward gives dL/d(density) (through the
+    box filter's adjoint for samples on coarser levels) and dL/d(tf) through the adjoint
+    kernel.  The backward must run before the next render on the same volume."""
 
     @staticmethod
     def forward(ctx, density, tf, volume, cams, params):
         volume.upload_level(0, density.detach(), "f32")
+        if (params or {}).get("lod_mode") and volume.levels > 1:
+            volume.build_lod(0)
         out = volume.render(cams, tf.detach(), params, grad=True)
         ctx.volume = volume
         ctx.frame = volume.stats()["frame"]
