@@ -490,8 +490,11 @@ def run_outofcore(args, dist, rank, ws, local):
     if not args.quick:
         # the same fly-through, cold cache: loading between passes only (no overlap), and with
         # empty-space skipping
-        for name, flags in (("serial_loads", 4), ("skip_empty", 2), ("preview", 8), ("level_step", 16)):
-            v2 = P.Volume(wl["D"], "u8", wl["brick"], wl["levels"], cache_bytes=wl["cache_bytes"], layout="compact")
+        for name, flags in (("serial_loads", 4), ("skip_empty", 2), ("preview", 8), ("level_step", 16),
+                            ("sparse_pt", 0)):
+            # sparse_pt: the same volume addressed through the three-level sparse page table
+            v2 = P.Volume(wl["D"], "u8", wl["brick"], wl["levels"], cache_bytes=wl["cache_bytes"], layout="compact",
+                          sparse_pt=name == "sparse_pt")
             v2.set_provider_batch(synth.brick_provider_address(), src, "u8")
             fr2 = flythrough(v2, dict(params, flags=flags))
             v2.close()

@@ -142,6 +142,17 @@ typedef struct {
  * VOL_LAYOUT_COMPACT: a slot holds the (B+1)^3 voxels of the brick and its
  * +x/+y/+z apron; a sample reads eight scalars.  Both give identical images. */
 #define VOL_LAYOUT_COMPACT 1u
+/* Sparse page table (the paper's three-level page table, Sec. III-E and Sec. V-C's virtual
+ * zettabyte volume): instead of one entry per brick of every level, each level has a dense top
+ * grid with one entry per 256^3 bricks, pointing to a middle page (16^3 entries, one per 16^3
+ * bricks), pointing to a leaf page (16^3 entries: the slots); pages are allocated as bricks
+ * arrive and are never freed.  The volume may then hold more bricks than 32-bit indices can
+ * count (up to 2^20 bricks per axis and level), e.g. a virtual volume whose bricks a
+ * provider generates.  Needs cache_bytes > 0.  Bricks arrive through vol_upload_brick or a
+ * provider (vol_upload_level and vol_build_lod are not available), brick loads are serial,
+ * and rendering is emission/absorption without gradients, level-scaled sampling or empty-
+ * space skipping.  Images equal those of the flat table. */
+#define VOL_LAYOUT_SPARSE_PT 2u
 
 /* Brick-and-level layout that vol_create() would use (pure host computation). */
 typedef struct {
@@ -152,11 +163,14 @@ typedef struct {
     int32_t entry_voxels;  /* voxels stored per addressable entry: 4 (quad) or 1 */
     int64_t level_dims[VOL_MAX_LEVELS][3];
     int64_t level_bricks[VOL_MAX_LEVELS][3];  /* ceil(D_l / B) per axis */
-    int64_t level_pt_offset[VOL_MAX_LEVELS];  /* first page-table entry of each level */
-    int64_t total_bricks;                     /* page-table entries over all levels */
+    int64_t level_pt_offset[VOL_MAX_LEVELS];  /* first page-table entry of each level (sparse: of
+                                                 its top grid) */
+    int64_t total_bricks;                     /* bricks over all levels (flat: page-table entries) */
     int64_t slot_bytes;   /* one atlas slot: (B+1)^3 voxels, padded to 256 bytes */
     int64_t nslots;       /* atlas capacity in bricks */
     int64_t atlas_bytes;
+    int64_t sparse_pt;      /* 1: VOL_LAYOUT_SPARSE_PT */
+    int64_t pt_top_entries; /* sparse: entries of the levels' top grids */
 } vol_layout;
 
 /* Per-render counters (vol_get_stats). */

@@ -233,6 +233,29 @@ class Volume:
         return (Dx, Dy, Dz)
 
 
+class VirtualVolume(Volume):
+    """Level dims only, no voxels: for decision-layer traces (``trace``) of volumes too large to
+    hold, e.g. the virtual volumes a procedural source serves.  Rendering one is an error."""
+
+    def __init__(self, D0, nlevels: int, dtype: str, brick: int):
+        if not 1 <= nlevels <= MAX_LEVELS:
+            raise ValueError("1..16 levels")
+        self.levels = []
+        self.dtype = dtype
+        self.brick = int(brick)
+        s = _Volume()
+        s.nlevels, s.dtype, s.brick = nlevels, DTYPES[dtype], self.brick
+        for l, (Dx, Dy, Dz) in enumerate(level_dims(D0, nlevels)):
+            s.dims[l][:] = [Dx, Dy, Dz]
+            s.data[l] = None
+        self._s = s
+        self._D0 = tuple(int(v) for v in D0)
+
+    @property
+    def dims0(self):
+        return self._D0
+
+
 def ray_info(cam: dict, D0, px: int, py: int):
     out = np.zeros(8, dtype=np.float32)
     hit = ctypes.c_int32()

@@ -35,6 +35,7 @@ VOL_COMPOSITE_DVR, VOL_COMPOSITE_MOP, VOL_COMPOSITE_MIP = 0, 1, 2
 COMPOSITES = {"dvr": VOL_COMPOSITE_DVR, "mop": VOL_COMPOSITE_MOP, "mip": VOL_COMPOSITE_MIP}
 VOL_LAYOUT_COMPACT = 1
 LAYOUTS = {"quad": 0, "compact": VOL_LAYOUT_COMPACT}
+VOL_LAYOUT_SPARSE_PT = 2
 
 # every entry point include/vol.h declares
 EXPORTS = ["vol_plan", "vol_create", "vol_destroy", "vol_last_error", "vol_set_stream", "vol_get_layout",
@@ -65,7 +66,8 @@ class vol_layout(ctypes.Structure):
                 ("level_dims", (ctypes.c_int64 * 3) * MAX_LEVELS),
                 ("level_bricks", (ctypes.c_int64 * 3) * MAX_LEVELS),
                 ("level_pt_offset", ctypes.c_int64 * MAX_LEVELS), ("total_bricks", ctypes.c_int64),
-                ("slot_bytes", ctypes.c_int64), ("nslots", ctypes.c_int64), ("atlas_bytes", ctypes.c_int64)]
+                ("slot_bytes", ctypes.c_int64), ("nslots", ctypes.c_int64), ("atlas_bytes", ctypes.c_int64),
+                ("sparse_pt", ctypes.c_int64), ("pt_top_entries", ctypes.c_int64)]
 
 
 class vol_stats(ctypes.Structure):

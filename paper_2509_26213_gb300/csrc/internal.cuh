@@ -35,8 +35,15 @@ struct LevelDev {
     int D[3];        // voxels per axis
     int nb[3];       // bricks per axis
     float r[3];      // D_l / D_0 per axis, binary32
-    uint32_t pt_off; // first page-table entry
+    uint32_t pt_off; // first page-table entry (sparse table: of the level's top grid)
+    int tn[3];       // sparse table: top-grid entries per axis, ceil(nb / 256)
 };
+
+// Sparse page table: a dense top grid per level (one entry per 256^3 bricks) -> middle page
+// (16^3 entries) -> leaf page (16^3 entries, the slots).  Entries of the top grid and of
+// middle pages hold the pool index of the child page's first entry, or kInvalidSlot.
+constexpr int kPageShift = 4;  // 16 entries per axis and page
+constexpr int kPageEntries = 1 << (3 * kPageShift);
 
 struct ViewDev {
     float eye[3], right[3], up[3], fwd[3];
@@ -63,7 +70,8 @@ struct VolDev {
     int quad;                      // 1: quad layout, 0: compact (B+1)^3
     int bshift, bmask, B1;         // log2 B, B - 1, B + 1
     int nlevels;
-    const uint32_t* pt;
+    const uint32_t* pt;            // flat page table, or the sparse table's pool
+    int sparse;                    // 1: three-level sparse page table
     const float2* range;           // per slot: min and max stored value (stored units)
     LevelDev lv[kMaxLevels];
     float D0f[3];
@@ -95,6 +103,8 @@ struct RenderDev {
     unsigned req_cap_mask;
     unsigned* req_list;
     unsigned req_list_cap;
+    unsigned long long* req_table64;  // sparse page table: requests keyed by (level, brick)
+    unsigned long long* req_list64;
     unsigned* last_used;
     unsigned frame;
     // gradient checkpoints
@@ -152,6 +162,8 @@ int render_blocks_per_sm(int dtype, bool grad);
 const void* pick_render_projection(int dtype, int brick, bool quad, bool lod, int mode);
 // Level-scaled sampling (kernels_lstep.cu): the emission/absorption variant.
 const void* pick_render_level_step(int dtype, int brick, bool quad, bool lod);
+// Sparse page table (kernels_sparse.cu): the emission/absorption variant.
+const void* pick_render_sparse(int dtype, int brick, bool quad, bool lod);
 // order[] = tiles sorted by descending log2 bucket of cost[] (heaviest first); zeroes cost[].
 // buckets: 64 ints of device scratch.
 cudaError_t launch_tile_order(int* cost, int* order, int ntiles, int* buckets, cudaStream_t s);

@@ -367,8 +367,15 @@ __global__ void k_trace(const __grid_constant__ TraceDev P) {
                 rec.local[a] = Q.i0[a] & P.vol.bmask;
             }
             rec.pad = 0;
-            rec.brick_id = (int64_t)(Q.pti - L.pt_off);
-            rec.slot = P.vol.pt[Q.pti];
+            if (P.vol.sparse) {
+                const int h0 = Q.i0[0] >> P.vol.bshift, h1 = Q.i0[1] >> P.vol.bshift, h2 = Q.i0[2] >> P.vol.bshift;
+                rec.brick_id = (int64_t)h0 + (int64_t)L.nb[0] * ((int64_t)h1 + (int64_t)L.nb[1] * h2);
+                uint32_t leaf;
+                rec.slot = sparse_walk(P.vol.pt, load_lv(L), h0, h1, h2, leaf);
+            } else {
+                rec.brick_id = (int64_t)(Q.pti - L.pt_off);
+                rec.slot = P.vol.pt[Q.pti];
+            }
             rec.pad2 = 0;
             P.out[(long long)q * P.max_samples + k] = rec;
         }
@@ -420,6 +427,10 @@ cudaError_t launch_render(int dtype, int mode, const RenderDev& p, int grid, cud
     const void* fn = nullptr;
     if (mode == kMop || mode == kMip)
         fn = pick_render_projection(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0, mode);
+    else if (p.vol.sparse && mode == kDvr && !p.level_step)
+        fn = pick_render_sparse(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0);
+    else if (p.vol.sparse)
+        fn = nullptr;  // the sparse table has only the emission/absorption variant
     else if (p.level_step && mode == kDvr)
         fn = pick_render_level_step(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0);
     else if (!p.level_step)

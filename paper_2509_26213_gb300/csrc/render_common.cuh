@@ -123,7 +123,8 @@ struct LvReg {
     float r[3];     // D_l / D_0 per axis (binary32)
     int Dm[3];      // D_l - 1 per axis
     int nb0, nb1;   // bricks along x and y
-    uint32_t off;   // first page-table entry of the level
+    uint32_t off;   // first page-table entry of the level (sparse table: of its top grid)
+    int tn0, tn1;   // sparse table: top-grid entries along x and y
 };
 
 __device__ __forceinline__ LvReg load_lv(const LevelDev& L) {
@@ -136,7 +137,40 @@ __device__ __forceinline__ LvReg load_lv(const LevelDev& L) {
     R.nb0 = L.nb[0];
     R.nb1 = L.nb[1];
     R.off = L.pt_off;
+    R.tn0 = L.tn[0];
+    R.tn1 = L.tn[1];
     return R;
+}
+
+// Sparse page table: the top-grid entry of brick (h0, h1, h2) on a level, and its position
+// inside the middle and leaf pages (packed: 8 low bits per axis).
+__device__ __forceinline__ uint32_t sparse_top(const LvReg& L, int h0, int h1, int h2) {
+    constexpr int s = 2 * kPageShift;
+    return L.off + (uint32_t)(((h2 >> s) * L.tn1 + (h1 >> s)) * L.tn0 + (h0 >> s));
+}
+__device__ __forceinline__ uint32_t sparse_sub(int h0, int h1, int h2) {
+    return ((uint32_t)(h2 & 255) << 16) | ((uint32_t)(h1 & 255) << 8) | (uint32_t)(h0 & 255);
+}
+__device__ __forceinline__ uint32_t sparse_mid_local(uint32_t sub) {
+    constexpr int p = kPageShift, m = (1 << kPageShift) - 1;
+    return (((sub >> (16 + p)) & m) << (2 * p)) | (((sub >> (8 + p)) & m) << p) | ((sub >> p) & m);
+}
+__device__ __forceinline__ uint32_t sparse_leaf_local(uint32_t sub) {
+    constexpr int p = kPageShift, m = (1 << kPageShift) - 1;
+    return (((sub >> 16) & m) << (2 * p)) | (((sub >> 8) & m) << p) | (sub & m);
+}
+// Slot of the brick through the three levels (kInvalidSlot when a page or the brick is
+// absent); leaf receives the leaf entry's pool index (the brick's identity) or kInvalidSlot.
+__device__ __forceinline__ uint32_t sparse_walk(const uint32_t* __restrict__ pool, const LvReg& L, int h0, int h1, int h2,
+                                                uint32_t& leaf) {
+    leaf = kInvalidSlot;
+    const uint32_t sub = sparse_sub(h0, h1, h2);
+    const uint32_t m = __ldg(pool + sparse_top(L, h0, h1, h2));
+    if (m == kInvalidSlot) return kInvalidSlot;
+    const uint32_t f = __ldg(pool + m + sparse_mid_local(sub));
+    if (f == kInvalidSlot) return kInvalidSlot;
+    leaf = f + sparse_leaf_local(sub);
+    return __ldg(pool + leaf);
 }
 
 // Grid position on a level, clamp to edge, chunk addressing (Sec. III-A).
@@ -372,7 +406,7 @@ struct Fallback {
     bool ok;
 };
 
-template <bool LOD>
+template <bool LOD, bool SP>
 __device__ __noinline__ Fallback preview_fallback(const uint32_t* __restrict__ pt, float t, float o0, float o1,
                                                   float o2, float d0, float d1, float d2, float lodscale, int bias,
                                                   int nlev, const LevelDev* s_lv, int bshift, int bmask, int row) {
@@ -387,7 +421,10 @@ __device__ __noinline__ Fallback preview_fallback(const uint32_t* __restrict__ p
     for (int m = l + 1; m < nlev; ++m) {
         Resolved R;
         resolve(s_lv[m], bshift, bmask, row, p, R);
-        const uint32_t s = __ldg(pt + R.pti);
+        uint32_t leaf;
+        const uint32_t s = SP ? sparse_walk(pt, load_lv(s_lv[m]), R.i0[0] >> bshift, R.i0[1] >> bshift,
+                                            R.i0[2] >> bshift, leaf)
+                              : __ldg(pt + R.pti);
         if (s != kInvalidSlot) {
             F.ok = true;
             F.slot = s;
@@ -453,6 +490,44 @@ __device__ __forceinline__ void request_brick(const RenderDev& P, uint32_t key) 
         if (pos < P.req_list_cap) P.req_list[pos] = key;
         else atomicAdd(&P.counters[kReqOverflow], 1u);
     }
+}
+
+// request_brick for the sparse page table: the key is (level << 60 | bz << 40 | by << 20 | bx) + 1.
+__device__ __forceinline__ void request_brick64(const RenderDev& P, unsigned long long key) {
+    uint32_t h = hash_key((uint32_t)key ^ hash_key((uint32_t)(key >> 32))) & P.req_cap_mask;
+    int state = 2;  // 0 new, 1 present, 2 overflow
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        const unsigned long long prev = atomicCAS(&P.req_table64[h], 0ull, key);
+        if (prev == 0ull) { state = 0; break; }
+        if (prev == key) { state = 1; break; }
+        h = (h + 1) & P.req_cap_mask;
+    }
+    if (state == 2) atomicAdd(&P.counters[kReqOverflow], 1u);
+    const unsigned m = __activemask();
+    const unsigned mnew = __ballot_sync(m, state == 0);
+    if (state == 0) {
+        const int leader = __ffs(mnew) - 1;
+        const unsigned lane = threadIdx.x & 31;
+        unsigned base = 0;
+        if ((int)lane == leader) base = atomicAdd(&P.counters[kReqCount], (unsigned)__popc(mnew));
+        base = __shfl_sync(mnew, base, leader);
+        const unsigned pos = base + __popc(mnew & ((1u << lane) - 1));
+        if (pos < P.req_list_cap) P.req_list64[pos] = key;
+        else atomicAdd(&P.counters[kReqOverflow], 1u);
+    }
+}
+
+// Sparse page table: the request key of the sample at depth t (its level and brick).
+template <bool LOD>
+__device__ __noinline__ unsigned long long sparse_request_key(float t, float o0, float o1, float o2, float d0, float d1,
+                                                             float d2, float lodscale, int bias, int nlev,
+                                                             const LevelDev* s_lv, int bshift, int bmask, int row) {
+    const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)), __fadd_rn(o2, __fmul_rn(t, d2))};
+    const int l = LOD ? lod_level(t, lodscale, bias, nlev) : 0;
+    Resolved R;
+    resolve(s_lv[l], bshift, bmask, row, p, R);
+    return (((unsigned long long)l << 60) | ((unsigned long long)(R.i0[2] >> bshift) << 40) |
+            ((unsigned long long)(R.i0[1] >> bshift) << 20) | (unsigned long long)(R.i0[0] >> bshift)) + 1ull;
 }
 
 __device__ __forceinline__ void suspend_ray(const RenderDev& P, long long ray, int k, float C0, float C1, float C2,
@@ -534,6 +609,11 @@ __device__ __forceinline__ bool composite_sample(float val, const float4* s_tf, 
     return __fsub_rn(1.0f, T) >= et;
 }
 
+// Depth of sample k: the kept depth under level-scaled sampling, else t0 + k dt.
+__device__ __forceinline__ float tcur_or_t(bool ls, float tcur, float t0, int k, float step) {
+    return ls ? tcur : __fadd_rn(t0, __fmul_rn((float)k, step));
+}
+
 // Level-scaled sampling: the sample after one at t on level l lies dt * 2^l further (the
 // scaling by an exact power of two does not round).
 __device__ __forceinline__ float next_t_level_step(float t, float step, int l) {
@@ -547,9 +627,11 @@ __device__ __forceinline__ float next_t_level_step(float t, float step, int l) {
 // LS: level-scaled sampling (emission/absorption only): sample k+1 lies dt * 2^l past sample k
 // on level l, whose opacity is corrected to that longer step; t of the lane's next sample is
 // kept in tcur (and in a suspended ray's record).
-template <int DT, bool LOD, int MODE, int BS, bool Q, bool LS = false>
+// SP: three-level sparse page table (emission/absorption, uniform steps, no empty-space jumps).
+template <int DT, bool LOD, int MODE, int BS, bool Q, bool LS = false, bool SP = false>
 __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const __grid_constant__ RenderDev P) {
     static_assert(!LS || MODE == kDvr, "level-scaled sampling is for emission/absorption without gradients");
+    static_assert(!SP || (MODE == kDvr && !LS), "the sparse page table variant is for emission/absorption");
     constexpr bool GRAD = MODE == kDvrGrad;
     constexpr float kT0 = MODE == kMop ? 0.0f : (MODE == kMip ? -1.0f : 1.0f);
     __shared__ float4 s_tf[256];
@@ -702,6 +784,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 int nvalid = kBatch;
                 float tv[kBatch + 1];  // LS: depths of samples k .. k + kBatch
                 int lv[kBatch];        // LS: their levels
+                uint32_t sub[kBatch];  // SP: brick position inside the middle and leaf pages
                 tv[0] = tcur;
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
@@ -723,6 +806,11 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     Resolved R;
                     resolve_reg(L, bshift, bmask, row, p, R);
                     pti[j] = R.pti;
+                    if (SP) {
+                        const int h0 = R.i0[0] >> bshift, h1 = R.i0[1] >> bshift, h2 = R.i0[2] >> bshift;
+                        pti[j] = sparse_top(L, h0, h1, h2);
+                        sub[j] = sparse_sub(h0, h1, h2);
+                    }
                     loc[j] = R.local;
                     wgt[j][0] = R.w[0];
                     wgt[j][1] = R.w[1];
@@ -730,8 +818,24 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 }
                 // (b) page-table lookups, all issued together (samples past the exit read entry 0)
                 uint32_t slot[kBatch];
+                if (SP) {
+                    // three dependent lookups, each issued for the whole batch; pti becomes the leaf
+                    // entry (the brick's identity) of resident bricks
+                    uint32_t e[kBatch];
 #pragma unroll
-                for (int j = 0; j < kBatch; ++j) slot[j] = __ldg(P.vol.pt + (j < nvalid ? pti[j] : 0u));
+                    for (int j = 0; j < kBatch; ++j) e[j] = j < nvalid ? __ldg(P.vol.pt + pti[j]) : kInvalidSlot;
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j)
+                        e[j] = e[j] != kInvalidSlot ? __ldg(P.vol.pt + e[j] + sparse_mid_local(sub[j])) : kInvalidSlot;
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        pti[j] = e[j] != kInvalidSlot ? e[j] + sparse_leaf_local(sub[j]) : kInvalidSlot;
+                        slot[j] = e[j] != kInvalidSlot ? __ldg(P.vol.pt + pti[j]) : kInvalidSlot;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) slot[j] = __ldg(P.vol.pt + (j < nvalid ? pti[j] : 0u));
+                }
                 int miss_at = kBatch;
 #pragma unroll
                 for (int j = kBatch - 1; j >= 0; --j)
@@ -745,7 +849,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         if (pti[j] != cur_pti) {
                             cur_pti = pti[j];
                             if (P.last_used) P.last_used[slot[j]] = P.frame;
-                            if (!LS && P.skip_empty) {
+                            if (!LS && !SP && P.skip_empty) {
                                 const float2 rng = __ldg(P.vol.range + slot[j]);
                                 if (MODE == kMop) cur_empty = brick_below_alpha<DT>(rng, s_amx, T);
                                 else if (MODE == kMip) cur_empty = brick_below_coord<DT>(rng, T);
@@ -781,13 +885,20 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     // preview (Sec. IV-B): sample k lies in a brick that is not resident.  Request the
                     // brick for the refinement and take the sample on the finest coarser resident
                     // level (left out when none is).
-                    if (P.req_table && pti[miss_at] != cur_pti) request_brick(P, pti[miss_at] + 1u);
-                    cur_pti = pti[miss_at];
+                    if (SP) {
+                        if (P.req_table64)
+                            request_brick64(P, sparse_request_key<LOD>(tcur_or_t(LS, tcur, t0, k, step), o0, o1, o2, d0,
+                                                                       d1, d2, lodscale, P.lod_bias, nlev, s_lv,
+                                                                       bshift, bmask, row));
+                    } else if (P.req_table && pti[miss_at] != cur_pti) {
+                        request_brick(P, pti[miss_at] + 1u);
+                    }
+                    cur_pti = SP ? kInvalidSlot : pti[miss_at];
                     cur_empty = false;
                     const float tk = LS ? tcur : __fadd_rn(t0, __fmul_rn((float)k, step));
                     const int lk = LOD ? lod_level(tk, lodscale, P.lod_bias, nlev) : 0;
-                    const Fallback F = preview_fallback<LOD>(P.vol.pt, tk, o0, o1, o2, d0, d1, d2, lodscale,
-                                                             P.lod_bias, nlev, s_lv, bshift, bmask, row);
+                    const Fallback F = preview_fallback<LOD, SP>(P.vol.pt, tk, o0, o1, o2, d0, d1, d2, lodscale,
+                                                                 P.lod_bias, nlev, s_lv, bshift, bmask, row);
                     if (F.ok) {
                         if (P.last_used) P.last_used[F.slot] = P.frame;
                         const float v = sample_value<DT, BS, Q>(
@@ -840,7 +951,12 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     active = false;
                 } else if (!fell && miss_at < kBatch) {
                     // wait for the missing brick: sample k (= the first missing one) resumes later
-                    if (P.req_table) {
+                    if (SP && P.req_table64) {
+                        request_brick64(P, sparse_request_key<LOD>(__fadd_rn(t0, __fmul_rn((float)k, step)), o0, o1, o2,
+                                                                   d0, d1, d2, lodscale, P.lod_bias, nlev, s_lv, bshift,
+                                                                   bmask, row));
+                        suspend_ray(P, ray, k, C0, C1, C2, T, 0.0f);
+                    } else if (!SP && P.req_table) {
                         request_brick(P, miss_pti + 1u);
                         suspend_ray(P, ray, k, C0, C1, C2, T, LS ? tcur : 0.0f);
                     } else {

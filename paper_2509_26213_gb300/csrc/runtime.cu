@@ -18,6 +18,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.cuh"
@@ -69,8 +70,10 @@ int plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache
     o->brick = brick;
     o->levels = levels;
     o->bytes_per_voxel = bpv;
-    if (flags & ~VOL_LAYOUT_COMPACT) { err = "unknown flags"; return VOL_ERR_INVALID_ARG; }
+    if (flags & ~(VOL_LAYOUT_COMPACT | VOL_LAYOUT_SPARSE_PT)) { err = "unknown flags"; return VOL_ERR_INVALID_ARG; }
     o->layout = (flags & VOL_LAYOUT_COMPACT) ? 1 : 0;
+    const bool sparse = (flags & VOL_LAYOUT_SPARSE_PT) != 0;
+    o->sparse_pt = sparse ? 1 : 0;
     o->entry_voxels = o->layout ? 1 : 4;
     int64_t off = 0;
     for (int l = 0; l < levels; ++l) {
@@ -79,11 +82,33 @@ int plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache
             o->level_dims[l][a] = l == 0 ? dims[a] : (o->level_dims[l - 1][a] + 1) / 2;
             o->level_bricks[l][a] = (o->level_dims[l][a] + brick - 1) / brick;
         }
-        o->level_pt_offset[l] = off;
+        if (!sparse) o->level_pt_offset[l] = off;
         off += o->level_bricks[l][0] * o->level_bricks[l][1] * o->level_bricks[l][2];
     }
-    if (off >= (int64_t)0xFFFFFFF0ll) { err = "too many bricks for 32-bit page-table indices"; return VOL_ERR_UNSUPPORTED; }
     o->total_bricks = off;
+    if (sparse) {
+        // top grids, one entry per 256^3 bricks, laid end to end
+        const int64_t span = int64_t(1) << (2 * kPageShift);
+        int64_t top = 0;
+        for (int l = 0; l < levels; ++l) {
+            int64_t n = 1;
+            for (int a = 0; a < 3; ++a) {
+                if (o->level_bricks[l][a] > (int64_t(1) << 20)) {
+                    err = "sparse page table: at most 2^20 bricks per axis";
+                    return VOL_ERR_UNSUPPORTED;
+                }
+                n *= (o->level_bricks[l][a] + span - 1) / span;
+            }
+            o->level_pt_offset[l] = top;
+            top += n;
+        }
+        if (top >= (int64_t(1) << 30)) { err = "sparse page table: top grids too large"; return VOL_ERR_UNSUPPORTED; }
+        o->pt_top_entries = top;
+        if (cache_bytes == 0) { err = "a sparse page table needs cache_bytes > 0"; return VOL_ERR_INVALID_ARG; }
+    } else if (off >= (int64_t)0xFFFFFFF0ll) {
+        err = "too many bricks for 32-bit page-table indices (VOL_LAYOUT_SPARSE_PT takes more)";
+        return VOL_ERR_UNSUPPORTED;
+    }
     const int64_t B1 = brick + 1;
     const int64_t slot_voxels = o->layout ? B1 * B1 * B1 : 4 * (int64_t)brick * brick * B1;
     o->slot_bytes = ((slot_voxels * bpv + 255) / 256) * 256;
@@ -116,6 +141,15 @@ struct vol_s {
     std::vector<uint32_t> owner;      // slot -> page-table index or invalid
     std::vector<uint32_t> protect;    // slot -> operation epoch that must not evict it
     std::vector<uint8_t> reserved;    // slot -> 1 while a brick is being generated into it
+    // sparse page table: bricks get handles (the index the flat table would use) on first use;
+    // `pt` is then the pool (top grids, then 16^3-entry pages) and pool_host its mirror
+    bool sparse = false;
+    std::unordered_map<uint64_t, uint32_t> handle_of;  // (level, brick) key -> handle
+    std::vector<uint64_t> key_of;                      // handle -> key
+    std::vector<uint32_t> pool_host;
+    size_t pool_used = 0, pool_cap = 0;                // entries in use / allocated on the device
+    unsigned long long* req_table64 = nullptr;
+    unsigned long long* req_list64 = nullptr;
     std::vector<uint8_t> queued;      // page-table index -> 1 while waiting for or in generation
     std::vector<uint32_t> free_slots; // stack
     uint32_t op_epoch = 1;
@@ -264,9 +298,86 @@ VolDev vol_dev(const vol_t v) {
             d.lv[l].r[a] = (float)v->lay.level_dims[l][a] / (float)v->lay.level_dims[0][a];
         }
         d.lv[l].pt_off = (uint32_t)v->lay.level_pt_offset[l];
+        for (int a = 0; a < 3; ++a) {
+            const int64_t span = int64_t(1) << (2 * kPageShift);
+            d.lv[l].tn[a] = (int)((v->lay.level_bricks[l][a] + span - 1) / span);
+        }
     }
     for (int a = 0; a < 3; ++a) d.D0f[a] = (float)v->lay.dims[a];
+    d.sparse = v->sparse ? 1 : 0;
     return d;
+}
+
+// ---- sparse page table: brick keys and handles, pages ------------------------------------
+
+uint64_t brick_key(int l, int64_t bx, int64_t by, int64_t bz) {
+    return ((uint64_t)l << 60) | ((uint64_t)bz << 40) | ((uint64_t)by << 20) | (uint64_t)bx;
+}
+
+// Handle of brick key `key`, assigned on first use.
+uint32_t handle_for(vol_t v, uint64_t key) {
+    auto it = v->handle_of.find(key);
+    if (it != v->handle_of.end()) return it->second;
+    const uint32_t h = (uint32_t)v->key_of.size();
+    v->handle_of.emplace(key, h);
+    v->key_of.push_back(key);
+    v->pt_host.push_back(kInvalidSlot);
+    v->queued.push_back(0);
+    return h;
+}
+
+// A zeroed (all kInvalidSlot) page of the pool, growing the device pool when it is full.  Only
+// between passes: growing synchronises the stream.
+int pool_page(vol_t v, uint32_t* base) {
+    if (v->pool_used + kPageEntries > v->pool_cap) {
+        const size_t cap = std::max(v->pool_cap * 2, v->pool_used + kPageEntries);
+        if (cap >= (size_t(1) << 32) - 16) return fail(v, VOL_ERR_OOM, "sparse page table: pool full");
+        uint32_t* np = nullptr;
+        CK(v, cudaStreamSynchronize(v->stream));
+        CK(v, cudaMalloc((void**)&np, sizeof(uint32_t) * cap));
+        CK(v, cudaMemcpyAsync(np, v->pt, sizeof(uint32_t) * v->pool_used, cudaMemcpyDeviceToDevice, v->stream));
+        CK(v, cudaMemsetAsync(np + v->pool_used, 0xFF, sizeof(uint32_t) * (cap - v->pool_used), v->stream));
+        CK(v, cudaStreamSynchronize(v->stream));
+        cudaFree(v->pt);
+        v->pt = np;
+        v->pool_cap = cap;
+        v->pool_host.resize(cap, kInvalidSlot);
+    }
+    *base = (uint32_t)v->pool_used;
+    v->pool_used += kPageEntries;
+    return VOL_OK;
+}
+
+// Pool index of the leaf entry of brick handle h; with create, allocates the missing middle
+// and leaf pages (their parent entries are queued as page-table updates).  kInvalidSlot when
+// absent and not created.
+int sparse_leaf(vol_t v, uint32_t h, bool create, uint32_t* out) {
+    const uint64_t key = v->key_of[h];
+    const int l = (int)(key >> 60);
+    const int64_t b[3] = {(int64_t)(key & 0xFFFFF), (int64_t)((key >> 20) & 0xFFFFF), (int64_t)((key >> 40) & 0xFFFFF)};
+    const int64_t span = int64_t(1) << (2 * kPageShift), pm = (int64_t(1) << kPageShift) - 1;
+    int64_t tn[3];
+    for (int a = 0; a < 3; ++a) tn[a] = (v->lay.level_bricks[l][a] + span - 1) / span;
+    const size_t top = (size_t)(v->lay.level_pt_offset[l] + ((b[2] / span) * tn[1] + b[1] / span) * tn[0] + b[0] / span);
+    auto local = [&](int shift) {
+        return (uint32_t)((((b[2] >> shift) & pm) << (2 * kPageShift)) | (((b[1] >> shift) & pm) << kPageShift) |
+                          ((b[0] >> shift) & pm));
+    };
+    *out = kInvalidSlot;
+    size_t at = top;
+    for (int shift : {kPageShift, 0}) {
+        uint32_t child = v->pool_host[at];
+        if (child == kInvalidSlot) {
+            if (!create) return VOL_OK;
+            if (int rc = pool_page(v, &child)) return rc;
+            v->pool_host[at] = child;
+            v->upd_idx.push_back((uint32_t)at);
+            v->upd_val.push_back(child);
+        }
+        at = (size_t)child + local(shift);
+    }
+    *out = (uint32_t)at;
+    return VOL_OK;
 }
 
 int64_t level_nbricks(const vol_t v, int l) {
@@ -274,6 +385,7 @@ int64_t level_nbricks(const vol_t v, int l) {
 }
 
 int level_of_pti(const vol_t v, uint32_t pti) {
+    if (v->sparse) return (int)(v->key_of[pti] >> 60);
     int l = 0;
     while (l + 1 < v->L && (int64_t)pti >= v->lay.level_pt_offset[l + 1]) ++l;
     return l;
@@ -312,8 +424,31 @@ void set_entry(vol_t v, uint32_t pti, uint32_t slot) {
     if (old == kInvalidSlot && slot != kInvalidSlot) { ++v->resident; ++v->level_resident[l]; }
     if (old != kInvalidSlot && slot == kInvalidSlot) { --v->resident; --v->level_resident[l]; }
     v->pt_host[pti] = slot;
-    v->upd_idx.push_back(pti);
+    uint32_t idx = pti;
+    if (v->sparse) {
+        sparse_leaf(v, pti, false, &idx);  // the pages exist: slot_for created them
+        if (idx == kInvalidSlot) return;
+    }
+    v->upd_idx.push_back(idx);
     v->upd_val.push_back(slot);
+}
+
+// Level and brick coordinates of page-table index (flat) or handle (sparse) pti.
+void pti_brick(const vol_t v, uint32_t pti, int* l, int32_t b[3]) {
+    if (v->sparse) {
+        const uint64_t key = v->key_of[pti];
+        *l = (int)(key >> 60);
+        b[0] = (int32_t)(key & 0xFFFFF);
+        b[1] = (int32_t)((key >> 20) & 0xFFFFF);
+        b[2] = (int32_t)((key >> 40) & 0xFFFFF);
+        return;
+    }
+    *l = level_of_pti(v, pti);
+    const int64_t id = (int64_t)pti - v->lay.level_pt_offset[*l];
+    const int64_t nbx = v->lay.level_bricks[*l][0], nby = v->lay.level_bricks[*l][1];
+    b[0] = (int32_t)(id % nbx);
+    b[1] = (int32_t)((id / nbx) % nby);
+    b[2] = (int32_t)(id / (nbx * nby));
 }
 
 // Least-recently-used eviction (usage stamps written by the render kernel).  Frees slots
@@ -352,6 +487,10 @@ int evict_lru(vol_t v, size_t need) {
 int slot_for(vol_t v, uint32_t pti, uint32_t* out) {
     uint32_t s = v->pt_host[pti];
     if (s == kInvalidSlot) {
+        if (v->sparse) {
+            uint32_t leaf;
+            if (int rc = sparse_leaf(v, pti, true, &leaf)) return rc;
+        }
         if (v->free_slots.empty())
             if (int rc = evict_lru(v, 1)) return rc;
         s = v->free_slots.back();
@@ -364,10 +503,14 @@ int slot_for(vol_t v, uint32_t pti, uint32_t* out) {
     return VOL_OK;
 }
 
-int brick_pti(const vol_t v, int level, const int32_t b[3], uint32_t* pti) {
+int brick_pti(vol_t v, int level, const int32_t b[3], uint32_t* pti) {
     if (level < 0 || level >= v->L || !b) return VOL_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
         if (b[a] < 0 || b[a] >= v->lay.level_bricks[level][a]) return VOL_ERR_INVALID_ARG;
+    if (v->sparse) {
+        *pti = handle_for(v, brick_key(level, b[0], b[1], b[2]));
+        return VOL_OK;
+    }
     *pti = (uint32_t)(v->lay.level_pt_offset[level] + b[0] +
                       v->lay.level_bricks[level][0] * (b[1] + v->lay.level_bricks[level][1] * (int64_t)b[2]));
     return VOL_OK;
@@ -393,6 +536,10 @@ int ensure_miss_buffers(vol_t v) {
         v->req_list_cap = 1u << 16;
         CK(v, cudaMalloc((void**)&v->req_table, sizeof(unsigned) * v->req_cap));
         CK(v, cudaMalloc((void**)&v->req_list, sizeof(unsigned) * v->req_list_cap));
+    }
+    if (v->sparse && !v->req_table64) {
+        CK(v, cudaMalloc((void**)&v->req_table64, sizeof(unsigned long long) * v->req_cap));
+        CK(v, cudaMalloc((void**)&v->req_list64, sizeof(unsigned long long) * v->req_list_cap));
     }
     if (v->susp_cap < v->nrays) {
         for (int i = 0; i < 2; ++i) {
@@ -453,6 +600,11 @@ int run_pass(vol_t v, bool resume, bool may_miss) {
         p.req_list_cap = v->req_list_cap;
         CK(v, cudaMemsetAsync(v->req_table, 0, sizeof(unsigned) * v->req_cap, v->stream));
         CK(v, cudaMemsetAsync(v->req_list, 0, sizeof(unsigned) * v->req_list_cap, v->stream));
+        if (v->sparse) {
+            p.req_table64 = v->req_table64;
+            p.req_list64 = v->req_list64;
+            CK(v, cudaMemsetAsync(v->req_table64, 0, sizeof(unsigned long long) * v->req_cap, v->stream));
+        }
     }
     if (resume) {
         p.resume = 1;
@@ -490,8 +642,21 @@ int collect_pass(vol_t v, bool resumed) {
     v->stats.requests += nreq;
     v->stats.suspended += c[kSuspCount];
     v->last_requests.resize(nreq);
-    if (nreq)
+    if (nreq && v->sparse) {
+        std::vector<unsigned long long> keys(nreq);
+        CK(v, cudaMemcpy(keys.data(), v->req_list64, sizeof(unsigned long long) * nreq, cudaMemcpyDeviceToHost));
+        for (uint32_t i = 0; i < nreq; ++i) {
+            const uint64_t key = keys[i] - 1ull;
+            const int l = (int)(key >> 60);
+            const int64_t b[3] = {(int64_t)(key & 0xFFFFF), (int64_t)((key >> 20) & 0xFFFFF), (int64_t)((key >> 40) & 0xFFFFF)};
+            bool ok = keys[i] != 0ull && l < v->L;
+            for (int a = 0; a < 3 && ok; ++a) ok = b[a] < v->lay.level_bricks[l][a];
+            if (!ok) return fail(v, VOL_ERR_DEVICE, "corrupt brick request");
+            v->last_requests[i] = handle_for(v, key) + 1u;
+        }
+    } else if (nreq) {
         CK(v, cudaMemcpy(v->last_requests.data(), v->req_list, sizeof(uint32_t) * nreq, cudaMemcpyDeviceToHost));
+    }
     v->nsusp = c[kSuspCount];
     if (resumed) v->susp_cur ^= 1;
     if (c[kDevError]) return fail(v, VOL_ERR_DEVICE, "device-side check failed during render");
@@ -545,12 +710,11 @@ int load_requests(vol_t v) {
                 return rc;
             }
             ++next;
-            const int l = level_of_pti(v, pti);
-            const int64_t id = (int64_t)pti - v->lay.level_pt_offset[l];
-            const int64_t nbx = v->lay.level_bricks[l][0], nby = v->lay.level_bricks[l][1];
+            int l;
+            int32_t b[3];
+            pti_brick(v, pti, &l, b);
             slots.push_back(s);
-            batch.insert(batch.end(), {(int32_t)l, (int32_t)(id % nbx), (int32_t)((id / nbx) % nby),
-                                       (int32_t)(id / (nbx * nby))});
+            batch.insert(batch.end(), {(int32_t)l, b[0], b[1], b[2]});
         }
         const size_t n = slots.size();
         if (!n) break;
@@ -990,16 +1154,19 @@ int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t
     while ((1 << v->bshift) < brick) ++v->bshift;
     v->L = levels;
     v->stream = (cudaStream_t)stream;
+    v->sparse = lay.sparse_pt != 0;
+    // flat: one entry per brick; sparse: the top grids plus room for 256 pages to start with
+    const size_t pt_entries = v->sparse ? (size_t)lay.pt_top_entries + 256 * (size_t)kPageEntries : (size_t)lay.total_bricks;
     cudaError_t e = cudaGetDevice(&v->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v->nsm, cudaDevAttrMultiProcessorCount, v->device);
     if (e == cudaSuccess) e = cudaMalloc(&v->atlas, (size_t)lay.atlas_bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v->pt, sizeof(uint32_t) * (size_t)lay.total_bricks);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v->pt, sizeof(uint32_t) * pt_entries);
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->last_used, sizeof(unsigned) * (size_t)lay.nslots);
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->counters, sizeof(unsigned) * kNumCounters);
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->aux, sizeof(unsigned) * 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->order_buckets, sizeof(int) * 64);
     if (e == cudaSuccess) e = cudaMalloc((void**)&v->range, sizeof(float2) * (size_t)lay.nslots);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * (size_t)lay.total_bricks, v->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * pt_entries, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->last_used, 0, sizeof(unsigned) * (size_t)lay.nslots, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->aux, 0, sizeof(unsigned) * 4, v->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(v->stream);
@@ -1009,11 +1176,17 @@ int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t
         vol_destroy(v);
         return fail(nullptr, code, msg);
     }
-    v->pt_host.assign((size_t)lay.total_bricks, kInvalidSlot);
+    if (v->sparse) {  // per-brick vectors grow with the handles
+        v->pool_host.assign(pt_entries, kInvalidSlot);
+        v->pool_cap = pt_entries;
+        v->pool_used = (size_t)lay.pt_top_entries;
+    } else {
+        v->pt_host.assign((size_t)lay.total_bricks, kInvalidSlot);
+        v->queued.assign((size_t)lay.total_bricks, 0);
+    }
     v->owner.assign((size_t)lay.nslots, kInvalidSlot);
     v->protect.assign((size_t)lay.nslots, 0);
     v->reserved.assign((size_t)lay.nslots, 0);
-    v->queued.assign((size_t)lay.total_bricks, 0);
     v->free_slots.resize((size_t)lay.nslots);
     for (int64_t s = 0; s < lay.nslots; ++s) v->free_slots[(size_t)s] = (uint32_t)(lay.nslots - 1 - s);
     v->level_resident.assign(levels, 0);
@@ -1035,7 +1208,8 @@ void vol_destroy(vol_t v) {
     else cudaDeviceSynchronize();
     void* bufs[] = {v->atlas, v->pt, v->last_used, v->counters, v->aux, v->upd_dev, v->views_dev, v->req_table,
                     v->req_list, v->susp[0], v->susp[1], v->ckpt, v->ray_n, v->stage_dev, v->stage_slots_dev,
-                    v->tile_cost, v->tile_order, v->order_buckets, v->range, v->dlev_buf};
+                    v->tile_cost, v->tile_order, v->order_buckets, v->range, v->dlev_buf, v->req_table64,
+                    v->req_list64};
     for (void* b : bufs)
         if (b) cudaFree(b);
     void* hbufs[] = {v->stage_host, v->ring.host, v->ring.slots, v->ring.ptis, v->poll_host};
@@ -1084,6 +1258,7 @@ int vol_get_stats(vol_t v, vol_stats* out) {
 int vol_upload_level(vol_t v, int level, const void* src, int src_dtype, int src_on_device) {
     if (!v) return VOL_ERR_INVALID_ARG;
     if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
+    if (v->sparse) return fail(v, VOL_ERR_UNSUPPORTED, "sparse page table: load bricks one by one or by a provider");
     if (level < 0 || level >= v->L || !src) return fail(v, VOL_ERR_INVALID_ARG, "bad level or src");
     if (!bpv_of(src_dtype)) return fail(v, VOL_ERR_INVALID_ARG, "bad src dtype");
     if (!conversion_ok(src_dtype, v->dtype)) return fail(v, VOL_ERR_UNSUPPORTED, "unsupported conversion");
@@ -1147,6 +1322,7 @@ int vol_upload_brick(vol_t v, int level, const int32_t brick[3], const void* src
 int vol_build_lod(vol_t v, int from_level) {
     if (!v) return VOL_ERR_INVALID_ARG;
     if (int rc = ovl_settle(v)) return rc;  // no chunk of a preview still in generation
+    if (v->sparse) return fail(v, VOL_ERR_UNSUPPORTED, "sparse page table: coarser levels come from the provider");
     if (from_level < 0 || from_level >= v->L) return fail(v, VOL_ERR_INVALID_ARG, "bad from_level");
     for (int l = from_level + 1; l < v->L; ++l) {
         if (v->level_resident[l - 1] != level_nbricks(v, l - 1))
@@ -1225,7 +1401,13 @@ int vol_evict_all(vol_t v) {
     v->resident = 0;
     v->upd_idx.clear();
     v->upd_val.clear();
-    CK(v, cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * (size_t)v->lay.total_bricks, v->stream));
+    if (v->sparse) {  // every page back to the pool
+        std::fill(v->pool_host.begin(), v->pool_host.end(), kInvalidSlot);
+        v->pool_used = (size_t)v->lay.pt_top_entries;
+        CK(v, cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * v->pool_cap, v->stream));
+    } else {
+        CK(v, cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * (size_t)v->lay.total_bricks, v->stream));
+    }
     v->have_forward = false;
     return VOL_OK;
 }
@@ -1274,6 +1456,9 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     if (grad && preview) return fail(v, VOL_ERR_UNSUPPORTED, "a preview keeps no gradient state");
     if ((p.flags & VOL_RENDER_LEVEL_STEP) && (grad || p.composite != VOL_COMPOSITE_DVR))
         return fail(v, VOL_ERR_UNSUPPORTED, "level-scaled sampling is for emission/absorption without gradients");
+    if (v->sparse && (grad || p.composite != VOL_COMPOSITE_DVR || (p.flags & VOL_RENDER_LEVEL_STEP)))
+        return fail(v, VOL_ERR_UNSUPPORTED, "the sparse page table renders emission/absorption without gradients "
+                                            "or level-scaled sampling");
 
     // view table
     v->views_host.resize(nviews);
@@ -1355,7 +1540,7 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         }
     }
     const bool may_miss = !all_resident(v, p.lod_mode != 0);
-    const bool overlap = may_miss && v->prov_batch && !(p.flags & VOL_RENDER_SERIAL_LOADS);
+    const bool overlap = may_miss && v->prov_batch && !(p.flags & VOL_RENDER_SERIAL_LOADS) && !v->sparse;
     if (!overlap)
         if (int rc = ovl_settle(v)) return rc;  // a chunk a preview left in generation
     if (may_miss)
@@ -1400,13 +1585,13 @@ int vol_poll_requests(vol_t v, int32_t* out, int cap, int* n) {
     *n = (int)v->last_requests.size();
     for (int i = 0; i < cap && i < *n; ++i) {
         const uint32_t pti = v->last_requests[i] - 1u;
-        const int l = level_of_pti(v, pti);
-        const int64_t id = (int64_t)pti - v->lay.level_pt_offset[l];
-        const int64_t nbx = v->lay.level_bricks[l][0], nby = v->lay.level_bricks[l][1];
+        int l;
+        int32_t b[3];
+        pti_brick(v, pti, &l, b);
         out[4 * i + 0] = l;
-        out[4 * i + 1] = (int32_t)(id % nbx);
-        out[4 * i + 2] = (int32_t)((id / nbx) % nby);
-        out[4 * i + 3] = (int32_t)(id / (nbx * nby));
+        out[4 * i + 1] = b[0];
+        out[4 * i + 2] = b[1];
+        out[4 * i + 3] = b[2];
     }
     return VOL_OK;
 }

@@ -42,10 +42,12 @@ def params_struct(step=0.5, et=0.99, bg=(0.0, 0.0, 0.0, 0.0), lod_mode=0, lod_bi
     return p
 
 
-def plan(dims, dtype: str, brick: int, levels: int, cache_bytes: int = 0, layout: str = "quad") -> C.vol_layout:
+def plan(dims, dtype: str, brick: int, levels: int, cache_bytes: int = 0, layout: str = "quad",
+         sparse_pt: bool = False) -> C.vol_layout:
     lay = C.vol_layout()
     d = (ctypes.c_int64 * 3)(*[int(x) for x in dims])
-    C.check(C.load().vol_plan(d, C.DTYPES[dtype], int(brick), int(levels), int(cache_bytes), C.LAYOUTS[layout],
+    C.check(C.load().vol_plan(d, C.DTYPES[dtype], int(brick), int(levels), int(cache_bytes),
+                              C.LAYOUTS[layout] | (C.VOL_LAYOUT_SPARSE_PT if sparse_pt else 0),
                               ctypes.byref(lay)))
     return lay
 
@@ -60,9 +62,12 @@ class Volume:
     dims = (Dx, Dy, Dz) level-0 voxels; dtype in {"u8", "u16", "f16", "f32"} (storage);
     brick = brick edge B (power of two); levels = LOD levels; cache_bytes = atlas size
     (0 = room for every brick of every level); layout = "quad" (four-voxel entries, two
-    loads per sample, about 4x memory) or "compact" ((B+1)^3 voxels per brick)."""
+    loads per sample, about 4x memory) or "compact" ((B+1)^3 voxels per brick); sparse_pt =
+    three-level sparse page table (bricks beyond what a flat table can index; needs
+    cache_bytes > 0 and bricks from vol_upload_brick or a provider)."""
 
-    def __init__(self, dims, dtype: str, brick: int, levels: int, cache_bytes: int = 0, layout: str = "quad"):
+    def __init__(self, dims, dtype: str, brick: int, levels: int, cache_bytes: int = 0, layout: str = "quad",
+                 sparse_pt: bool = False):
         self.lib = C.load()
         self.dims = tuple(int(x) for x in dims)
         self.dtype = dtype
@@ -71,7 +76,8 @@ class Volume:
         h = ctypes.c_void_p()
         d = (ctypes.c_int64 * 3)(*self.dims)
         C.check(self.lib.vol_create(d, C.DTYPES[dtype], self.brick, self.levels, int(cache_bytes),
-                                    C.LAYOUTS[layout], _stream_ptr(), ctypes.byref(h)))
+                                    C.LAYOUTS[layout] | (C.VOL_LAYOUT_SPARSE_PT if sparse_pt else 0), _stream_ptr(),
+                                    ctypes.byref(h)))
         self.h = h
         self._provider = None
         lay = C.vol_layout()

@@ -69,6 +69,24 @@ def test_plan_rejects(lib, bad):
     assert rc == lib.VOL_ERR_INVALID_ARG
 
 
+def test_plan_sparse_page_table(lib):
+    """The paper's virtual 2 ZB volume (8,000,000^3 voxels, 128^3 bricks): too many bricks for a
+    flat table, a few hundred MB of top grids for the sparse one."""
+    from paper_2509_26213_gb300.volume import plan
+    D = (8_000_000,) * 3
+    with pytest.raises(RuntimeError):
+        plan(D, "f32", 128, 8, cache_bytes=16 << 30)
+    with pytest.raises(RuntimeError):  # a sparse table needs a cache budget
+        plan(D, "f32", 128, 8, sparse_pt=True)
+    lay = plan(D, "f32", 128, 8, cache_bytes=16 << 30, sparse_pt=True)
+    assert lay.sparse_pt == 1
+    assert lay.level_bricks[0][0] == 62500 and lay.total_bricks > 2 ** 47
+    tops = [(-(-lay.level_bricks[l][0] // 256)) ** 3 for l in range(8)]
+    assert list(lay.level_pt_offset[:8]) == [sum(tops[:l]) for l in range(8)]
+    assert lay.pt_top_entries == sum(tops) and lay.pt_top_entries * 4 < (1 << 30)
+    assert lay.nslots == (16 << 30) // lay.slot_bytes
+
+
 def test_missing_library_fails_loudly(lib, monkeypatch, tmp_path):
     import importlib
     from paper_2509_26213_gb300 import _capi

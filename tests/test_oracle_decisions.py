@@ -148,3 +148,24 @@ def test_resolve_coarse_level(orc):
         assert rec["i0"][0] == min(max(x1, 0), 49)
         assert rec["i0"][1] == 30 and rec["i0"][2] == 8   # 61*0.5-0.5 = 30.0, 17*0.5-0.5 = 8.0
         assert rec["brick_id"] == rec["i0"][0] // 8 + 7 * (3 + 7 * 1)
+
+
+def test_virtual_volume_traces_like_a_dense_one(orc):
+    """The decision layer reads level dims only: a dims-only volume traces exactly like a dense
+    one, so traces of volumes too large to hold are pinned by the same rules."""
+    D = (40, 36, 30)
+    shapes = [(30, 36, 40), (15, 18, 20), (8, 9, 10)]
+    dense = orc.Volume([np.zeros(s, np.uint8) for s in shapes], "u8", 8)
+    virt = orc.VirtualVolume(D, 3, "u8", 8)
+    cam = dict(synth.seeded_orbit(D, 9, 7, 13, fit=0.7), h=3)
+    for params in ({"lod_mode": 1, "lod_bias": -1}, {"lod_mode": 0}):
+        for px, py in ((0, 0), (4, 1), (8, 2)):
+            a, na = orc.trace(dense, cam, params, px, py)
+            b, nb = orc.trace(virt, cam, params, px, py)
+            assert na == nb
+            np.testing.assert_array_equal(a, b)
+    # and at coordinates no dense array could hold: a 2^20-voxel cube, level-0 brick ids past 2^32
+    big = orc.VirtualVolume((1 << 20,) * 3, 7, "u8", 64)
+    cam = synth.look_at((524288.0, 524300.0, 524310.0), (600000.0, 700000.0, 520000.0), 8, 6, fov_deg=50.0)
+    recs, n = orc.trace(big, cam, {"lod_mode": 1, "lod_bias": 0}, 3, 2, max_samples=4000)
+    assert n > 4000 and recs["brick_id"].max() > 2 ** 32
