@@ -47,7 +47,10 @@ __device__ __forceinline__ void flush_vox(float* dvox, long long cell, int mask,
 
 // Samples per lane whose page-table lookups and gathers the adjoint's forward recompute issues
 // together.
-constexpr int kBwdBatch = 4;
+#ifndef VOLRC_BWD_BATCH
+#define VOLRC_BWD_BATCH 4
+#endif
+constexpr int kBwdBatch = VOLRC_BWD_BATCH;
 // Adjoint CTA size and the resident CTAs per SM its register allocation must allow (shared
 // memory per CTA: 8 KiB + 256 B per thread).
 #ifndef VOLRC_BWD_THREADS
