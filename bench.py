@@ -377,6 +377,35 @@ def run_ours(args, dist, rank, ws, local):
             msk = statistics.mean(time_frames(torch, vol, cams, tf, dict(pm, flags=2), nrep, args.warmup, flush))
             variants[mode] = {"ms_per_frame": msm, "samples_per_frame": sm, "samples_per_s": sm / (msm * 1e-3),
                               "ms_per_frame_skip_empty": msk}
+    if not args.quick and args.workload == "c3":
+        # the plain form at matched rays: the same views rendered one launch each from a float32
+        # store of the same volume (converted on the GPU; compact slots keep it to ~41 GB)
+        vol.close()
+        torch.cuda.empty_cache()
+        v32 = P.Volume(wl["D"], "f32", wl["brick"], wl["levels"], layout="compact")
+        v32.upload_level(0, raw, wl["src"])
+        v32.build_lod(0)
+        s32 = 0
+        for cam in cams:
+            _, nsv = v32.render(cam, tf, params, nsamples=True)
+            s32 += int(nsv.sum().item())
+        torch.cuda.synchronize()
+        per_view = []
+        for _ in range(max(2, args.steps // 4)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for cam in cams:
+                v32.render(cam, tf, params)
+            b.record()
+            torch.cuda.synchronize()
+            per_view.append(a.elapsed_time(b))
+        ms32 = statistics.mean(per_view)
+        variants["single_view_f32"] = {"ms_per_frame": ms32, "samples_per_frame": s32,
+                                       "samples_per_s": s32 / (ms32 * 1e-3), "launches": len(cams),
+                                       "store": "f32 compact"}
+        v32.close()
+        torch.cuda.empty_cache()
     if not args.quick and args.workload == "c2":
         for st2 in ("f16", "f32"):
             v2 = build_volume(P, wl, st2, raw)
