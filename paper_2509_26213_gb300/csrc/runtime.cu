@@ -403,13 +403,29 @@ int ensure(vol_t v, T*& ptr, size_t& cap, size_t n, const char* what) {
     return VOL_OK;
 }
 
+// Publishes the queued page-table writes.  The update kernel writes them in parallel, so an
+// entry written twice since the last flush (assigned, then given back) keeps only its last value.
 int flush_pt_updates(vol_t v) {
-    const size_t n = v->upd_idx.size();
-    if (!n) return VOL_OK;
+    if (v->upd_idx.empty()) return VOL_OK;
+    std::unordered_map<uint32_t, uint32_t> last;
+    last.reserve(v->upd_idx.size());
+    std::vector<uint32_t> order;
+    for (size_t i = 0; i < v->upd_idx.size(); ++i) {
+        auto it = last.find(v->upd_idx[i]);
+        if (it == last.end()) {
+            last.emplace(v->upd_idx[i], v->upd_val[i]);
+            order.push_back(v->upd_idx[i]);
+        } else {
+            it->second = v->upd_val[i];
+        }
+    }
+    const size_t n = order.size();
     if (int rc = ensure(v, v->upd_dev, v->upd_cap, 2 * n, "page-table update buffer")) return rc;
     std::vector<uint32_t> packed(2 * n);
-    std::copy(v->upd_idx.begin(), v->upd_idx.end(), packed.begin());
-    std::copy(v->upd_val.begin(), v->upd_val.end(), packed.begin() + n);
+    for (size_t i = 0; i < n; ++i) {
+        packed[i] = order[i];
+        packed[n + i] = last[order[i]];
+    }
     CK(v, cudaMemcpyAsync(v->upd_dev, packed.data(), sizeof(uint32_t) * 2 * n, cudaMemcpyHostToDevice, v->stream));
     CK(v, launch_pt_update(v->pt, v->upd_dev, v->upd_dev + n, (int)n, v->stream));
     v->stats.launches += 1;
@@ -682,7 +698,7 @@ int load_requests(vol_t v) {
     const size_t src_bytes = nvox * bpv_of(v->prov_dtype);
     ++v->op_epoch;
     const std::vector<uint32_t> reqs = v->last_requests;
-    std::vector<uint32_t> slots;
+    std::vector<uint32_t> slots, ptis;
     std::vector<int32_t> batch;  // [n][4] level, bx, by, bz of the bricks to load
     const int64_t loaded0 = v->stats.bricks_loaded;
     bool full = false;
@@ -690,6 +706,7 @@ int load_requests(vol_t v) {
     while (next < reqs.size() && !full) {
         // collect up to stage_bricks bricks that need a slot
         slots.clear();
+        ptis.clear();
         batch.clear();
         while (next < reqs.size() && slots.size() < (size_t)v->stage_bricks) {
             const uint32_t pti = reqs[next] - 1u;
@@ -714,19 +731,31 @@ int load_requests(vol_t v) {
             int32_t b[3];
             pti_brick(v, pti, &l, b);
             slots.push_back(s);
+            ptis.push_back(pti);
             batch.insert(batch.end(), {(int32_t)l, b[0], b[1], b[2]});
         }
         const size_t n = slots.size();
         if (!n) break;
         // fill the pinned stage from the source
         const int64_t t_prov = now_us();
+        bool ok = true;
         if (v->prov_batch) {
-            if (v->prov_batch(v->prov_user, (int)n, batch.data(), v->stage_host) != 0)
-                return fail(v, VOL_ERR_PROVIDER, "brick provider failed");
+            ok = v->prov_batch(v->prov_user, (int)n, batch.data(), v->stage_host) == 0;
         } else {
-            for (size_t j = 0; j < n; ++j)
-                if (v->prov(v->prov_user, batch[4 * j], &batch[4 * j + 1], (char*)v->stage_host + j * src_bytes) != 0)
-                    return fail(v, VOL_ERR_PROVIDER, "brick provider failed");
+            for (size_t j = 0; j < n && ok; ++j)
+                ok = v->prov(v->prov_user, batch[4 * j], &batch[4 * j + 1], (char*)v->stage_host + j * src_bytes) == 0;
+        }
+        if (!ok) {
+            // the batch's slots were assigned but never filled: give them back, so that the bricks
+            // count as absent (and are requested again) rather than resident with stale data
+            for (size_t j = 0; j < n; ++j) {
+                set_entry(v, ptis[j], kInvalidSlot);
+                v->owner[slots[j]] = kInvalidSlot;
+                v->free_slots.push_back(slots[j]);
+            }
+            // an eviction may already have published some of these entries: unpublish them now
+            if (int rc = flush_pt_updates(v)) return rc;
+            return fail(v, VOL_ERR_PROVIDER, "brick provider failed");
         }
         v->stats.load_wait_us += now_us() - t_prov;
         v->stats.bricks_loaded += (int64_t)n;
