@@ -31,6 +31,7 @@ VOL_RENDER_SKIP_EMPTY = 2
 VOL_RENDER_SERIAL_LOADS = 4
 VOL_RENDER_PREVIEW = 8
 VOL_RENDER_LEVEL_STEP = 16
+VOL_RENDER_NO_PREFETCH = 32
 VOL_COMPOSITE_DVR, VOL_COMPOSITE_MOP, VOL_COMPOSITE_MIP = 0, 1, 2
 COMPOSITES = {"dvr": VOL_COMPOSITE_DVR, "mop": VOL_COMPOSITE_MOP, "mip": VOL_COMPOSITE_MIP}
 VOL_LAYOUT_COMPACT = 1

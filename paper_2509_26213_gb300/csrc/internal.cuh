@@ -13,6 +13,10 @@ constexpr int kMaxLevels = VOL_MAX_LEVELS;
 constexpr int kCkptEvery = 32;      // transmittance checkpoint spacing (samples)
 constexpr int kRenderThreads = 128; // threads per CTA of the render kernels
 constexpr int kMaxProbe = 64;       // bounded linear probing of the request table
+#ifndef VOLRC_PREFETCH_BRICKS
+#define VOLRC_PREFETCH_BRICKS 4
+#endif
+constexpr int kPrefetchBricks = VOLRC_PREFETCH_BRICKS;  // look-ahead of a waiting ray, in bricks
 
 // Compositing variants of the forward kernel (template argument MODE of k_render).
 constexpr int kDvr = 0;      // emission/absorption, front to back (Sec. IV-A)
@@ -92,6 +96,7 @@ struct RenderDev {
     int skip_empty;     // skip bricks whose value range the TF maps to zero opacity
     int preview;        // a sample on a non-resident brick uses the finest coarser resident level
     int level_step;     // level-scaled sampling (chooses the kernel variant)
+    int prefetch;       // a suspended ray also requests this many bricks after the missing one
     float4* out;
     int* nsamp;
     unsigned* counters;

@@ -517,6 +517,35 @@ __device__ __forceinline__ void request_brick64(const RenderDev& P, unsigned lon
     }
 }
 
+// Look-ahead for a ray about to wait for brick miss_pti (sample k): request the next P.prefetch
+// bricks along the ray as well (those not resident), so that the resumed ray does not wait a
+// round for each of them.
+template <bool LOD>
+__device__ __noinline__ void prefetch_next_brick(const RenderDev& P, int k, uint32_t miss_pti, float o0, float o1,
+                                                 float o2, float d0, float d1, float d2, float t0, float t1,
+                                                 float lodscale, const LevelDev* s_lv, int bshift, int bmask, int row,
+                                                 int B) {
+    const float o3[3] = {o0, o1, o2}, d3[3] = {d0, d1, d2};
+    const int nlev = P.vol.nlevels;
+    uint32_t cur = miss_pti;
+    int kc = k;
+    for (int ahead = 0; ahead < P.prefetch; ++ahead) {
+        const int kl = brick_last_sample<LOD>(kc, cur, o3, d3, t0, t1, P.step, lodscale, P.lod_bias, nlev, s_lv, bshift,
+                                              bmask, row, B);
+        kc = kl + 1;
+        const float tn = __fadd_rn(t0, __fmul_rn((float)kc, P.step));
+        if (!(tn < t1)) return;
+        const float pn[3] = {__fadd_rn(o0, __fmul_rn(tn, d0)), __fadd_rn(o1, __fmul_rn(tn, d1)),
+                             __fadd_rn(o2, __fmul_rn(tn, d2))};
+        const int ln = LOD ? lod_level(tn, lodscale, P.lod_bias, nlev) : 0;
+        Resolved R;
+        resolve(s_lv[ln], bshift, bmask, row, pn, R);
+        if (R.pti == cur) return;  // no progress (cannot happen past the brick's last sample)
+        cur = R.pti;
+        if (__ldg(P.vol.pt + cur) == kInvalidSlot) request_brick(P, cur + 1u);
+    }
+}
+
 // Sparse page table: the request key of the sample at depth t (its level and brick).
 template <bool LOD>
 __device__ __noinline__ unsigned long long sparse_request_key(float t, float o0, float o1, float o2, float d0, float d1,
@@ -958,6 +987,9 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         suspend_ray(P, ray, k, C0, C1, C2, T, 0.0f);
                     } else if (!SP && P.req_table) {
                         request_brick(P, miss_pti + 1u);
+                        if (!LS && P.prefetch)
+                            prefetch_next_brick<LOD>(P, k, miss_pti, o0, o1, o2, d0, d1, d2, t0, t1, lodscale, s_lv,
+                                                     bshift, bmask, row, B1 - 1);
                         suspend_ray(P, ray, k, C0, C1, C2, T, LS ? tcur : 0.0f);
                     } else {
                         atomicAdd(&P.counters[kDevError], 1u);

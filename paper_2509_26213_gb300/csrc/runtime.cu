@@ -616,6 +616,8 @@ int run_pass(vol_t v, bool resume, bool may_miss) {
         p.req_list_cap = v->req_list_cap;
         CK(v, cudaMemsetAsync(v->req_table, 0, sizeof(unsigned) * v->req_cap, v->stream));
         CK(v, cudaMemsetAsync(v->req_list, 0, sizeof(unsigned) * v->req_list_cap, v->stream));
+        // look-ahead of a few bricks for rays that wait: only when a provider will load them
+        p.prefetch = (v->prov || v->prov_batch) && !(v->params.flags & VOL_RENDER_NO_PREFETCH) ? kPrefetchBricks : 0;
         if (v->sparse) {
             p.req_table64 = v->req_table64;
             p.req_list64 = v->req_list64;
