@@ -105,3 +105,22 @@ def test_overlapped_loading_equals_serial(P, cache_slots):
     assert loads > 0
     if cache_slots:
         assert over.stats()["resident"] <= cache_slots
+
+
+def test_look_ahead_changes_loads_not_images(P):
+    """Rays that wait request the next bricks along them too (default) or not (flag 32): the
+    images are the same; the look-ahead takes fewer passes."""
+    D, B, L, seed = (384, 320, 256), 32, 5, 17
+    tfd = torch.from_numpy(synth.tf_peaks(seed)).cuda()
+    cams = synth.flythrough(D, 192, 108, 3, seed)
+    params = {"lod_mode": 1, "lod_bias": 0, "max_passes": 5000}
+    a = procedural_volume(P, D, B, L, seed, cache_bytes=0)
+    b = procedural_volume(P, D, B, L, seed, cache_bytes=0)
+    passes = [0, 0]
+    for cam in cams:
+        ia = a.render(cam, tfd, params).cpu().numpy()
+        passes[0] += a.stats()["passes"]
+        ib = b.render(cam, tfd, dict(params, flags=32)).cpu().numpy()
+        passes[1] += b.stats()["passes"]
+        np.testing.assert_array_equal(ia, ib)
+    assert passes[0] <= passes[1]
