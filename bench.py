@@ -114,18 +114,24 @@ def render_kernel_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_key):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+def recorded_counter(workload_key, what):
+    """A per-launch figure from the committed ncu summary (`what` is the line's label: "dram bytes"
+    or "warp instructions"), if the summary was taken on this kernel source."""
     path = os.path.join(ROOT, "profiles", f"raycast_fwd_{workload_key}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     m_src = re.search(r"kernel source digest:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"dram bytes per launch \(scaled to the bench frame\):\s*([0-9.eE+]+)", text)
+    m_b = re.search(what + r" per launch \(scaled to the bench frame\):\s*([0-9.eE+]+)", text)
     if m_src and m_b and m_src.group(1) == render_kernel_digest():
         return float(m_b.group(1))
     return None
+
+
+def recorded_traffic(workload_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    return recorded_counter(workload_key, "dram bytes")
 
 
 def dist_setup():
@@ -348,6 +354,15 @@ def run_ours(args, dist, rank, ws, local):
                 "bytes_accounting": "bricks touched x (B+1)^3 x bytes/voxel + image 16 B/px + TF 4 KiB + 4 B/brick page-table word",
                 "bytes_per_frame": b_unique,
                 "per_sample_gather_GBps": b_sample / (t_mean * 1e-3) / 1e9}
+    # the bound the kernel actually meets: instruction issue (one warp instruction per scheduler
+    # and clock: 152 SMs x 4 schedulers at the sampled SM clock), from the recorded warp
+    # instructions of one launch
+    winst = recorded_counter(wl["key"], "warp instructions")
+    if winst and clocks.get("sm_mhz"):
+        issue_peak = 152 * 4 * clocks["sm_mhz"] * 1e6
+        roofline["issue"] = {"achieved_warp_inst_per_s": winst / (t_mean * 1e-3), "peak_warp_inst_per_s": issue_peak,
+                             "frac": winst / (t_mean * 1e-3) / issue_peak, "warp_inst_per_frame": winst,
+                             "peak_kind": "152 SMs x 4 schedulers x sampled SM clock"}
 
     variants = {}
     # empty-space skipping (the paper's ES column): same image and sample counts, less work
