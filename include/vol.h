@@ -65,7 +65,7 @@ typedef struct vol_s *vol_t;
  * CameraState / entry_exit_points). */
 typedef struct {
     float eye[3], right[3], up[3], fwd[3];
-    float tan_half_fov; /* tan(vertical field of view / 2) */
+    float tan_half_fov; /* tan(vertical field of view / 2); must be > 0 and finite */
     float aspect;       /* w / h */
     int32_t w, h;
 } vol_camera;
@@ -122,7 +122,8 @@ typedef struct {
 #define VOL_COMPOSITE_MIP 2
 
 typedef struct {
-    float step;          /* sample spacing in level-0 voxels (> 0) */
+    float step;          /* sample spacing in level-0 voxels (> 0; at most 2^24 - 64 samples
+                            along the volume diagonal, else VOL_ERR_INVALID_ARG) */
     float et_threshold;  /* stop a ray after the sample where 1 - T >= et_threshold */
     float bg[4];         /* background RGBA composited behind the volume */
     int32_t lod_mode;    /* 0: all samples on level 0; 1: footprint LOD (Sec. V-C) */

@@ -11,6 +11,9 @@ namespace volrc {
 constexpr uint32_t kInvalidSlot = 0xFFFFFFFFu;
 constexpr int kMaxLevels = VOL_MAX_LEVELS;
 constexpr int kCkptEvery = 32;      // transmittance checkpoint spacing (samples)
+// Sample indices of a ray stay below this, so that they and small offsets of them are exact in
+// binary32 (past 2^24, neighbouring indices round to the same depth).
+constexpr double kMaxSamplesPerRay = 16777216.0 - 64.0;
 constexpr int kRenderThreads = 128; // threads per CTA of the render kernels
 constexpr int kMaxProbe = 64;       // bounded linear probing of the request table
 #ifndef VOLRC_PREFETCH_BRICKS

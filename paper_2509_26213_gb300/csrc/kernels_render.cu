@@ -172,9 +172,10 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
         for (int jb = 0; jb < maxlen; jb += kBwdBatch) {
             uint32_t pti[kBwdBatch], loc[kBwdBatch];
             float wv[kBwdBatch][3];
+            const float kf = (float)(k0 + jb);  // + u stays exact: indices are below 2^24
 #pragma unroll
             for (int u = 0; u < kBwdBatch; ++u) {
-                const float t = __fadd_rn(t0, __fmul_rn((float)(k0 + jb + u), step));
+                const float t = __fadd_rn(t0, __fmul_rn(__fadd_rn(kf, (float)u), step));
                 const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
                                     __fadd_rn(o2, __fmul_rn(t, d2))};
                 if (LOD) {
@@ -217,10 +218,10 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                 }
             }
         }
-        for (int j = maxlen - 1; j >= 0; --j) {
+        float kf = (float)(k0 + maxlen - 1);  // (float)(k0 + j), stepped down exactly
+        for (int j = maxlen - 1; j >= 0; --j, kf = __fsub_rn(kf, 1.0f)) {
             if (j < len) {
-                const int k = k0 + j;
-                const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
+                const float t = __fadd_rn(t0, __fmul_rn(kf, step));
                 const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
                                     __fadd_rn(o2, __fmul_rn(t, d2))};
                 if (LOD) {
@@ -264,13 +265,14 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                     if (dv != 0.0f) {
                         // register accumulation while the trilinear cell (and level) stays the same
                         const int lq = LOD ? cur_l : 0;
-                        const int Dx = L0.Dm[0] + 1, Dy = L0.Dm[1] + 1;
+                        const int Dx = (int)L0.Dm[0] + 1, Dy = (int)L0.Dm[1] + 1;
                         const long long cell = (long long)Q.i0[0] + (long long)Dx * ((long long)Q.i0[1] + (long long)Dy * Q.i0[2]);
                         if (cell != cell_cur || lq != cell_lvl) {
                             flush_vox(P.dlev[cell_lvl], cell_cur, cell_mask, dim_x(cell_lvl), dim_y(cell_lvl), cacc);
                             cell_cur = cell;
                             cell_lvl = lq;
-                            cell_mask = (Q.i0[0] < L0.Dm[0] ? 1 : 0) | (Q.i0[1] < L0.Dm[1] ? 2 : 0) | (Q.i0[2] < L0.Dm[2] ? 4 : 0);
+                            cell_mask = ((float)Q.i0[0] < L0.Dm[0] ? 1 : 0) | ((float)Q.i0[1] < L0.Dm[1] ? 2 : 0) |
+                                        ((float)Q.i0[2] < L0.Dm[2] ? 4 : 0);
                         }
                         const float wx = Q.w[0], wy = Q.w[1], wz = Q.w[2];
 #pragma unroll

@@ -104,10 +104,11 @@ __device__ __forceinline__ void make_ray(const ViewDev& V, const float D0f[3], i
 }
 
 // Footprint LOD (Sec. V-C): l = clamp(ilogb(t * lodscale) + bias, 0, L-1); l = 0 when the
-// footprint has no normal exponent.
+// footprint has no normal exponent.  t >= 0 and lodscale > 0, so q has a clear sign bit and its
+// exponent field is the exponent + 127; +0 and subnormals have field 0, giving -127 as required.
 __device__ __forceinline__ int lod_level(float t, float lodscale, int bias, int nlevels) {
     const float q = __fmul_rn(t, lodscale);
-    const int e = (q >= 1.17549435e-38f) ? (int)((__float_as_uint(q) >> 23) & 0xFF) - 127 : -127;
+    const int e = (int)(__float_as_uint(q) >> 23) - 127;
     return min(max(e + bias, 0), nlevels - 1);
 }
 
@@ -121,7 +122,7 @@ struct Resolved {
 // One level's constants, held in registers by the render loop.
 struct LvReg {
     float r[3];     // D_l / D_0 per axis (binary32)
-    int Dm[3];      // D_l - 1 per axis
+    float Dm[3];    // D_l - 1 per axis, as floats (exact: D_l <= 2^24)
     int nb0, nb1;   // bricks along x and y
     uint32_t off;   // first page-table entry of the level (sparse table: of its top grid)
     int tn0, tn1;   // sparse table: top-grid entries along x and y
@@ -132,7 +133,7 @@ __device__ __forceinline__ LvReg load_lv(const LevelDev& L) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         R.r[a] = L.r[a];
-        R.Dm[a] = L.D[a] - 1;
+        R.Dm[a] = (float)(L.D[a] - 1);
     }
     R.nb0 = L.nb[0];
     R.nb1 = L.nb[1];
@@ -175,24 +176,20 @@ __device__ __forceinline__ uint32_t sparse_walk(const uint32_t* __restrict__ poo
 
 // Grid position on a level, clamp to edge, chunk addressing (Sec. III-A).
 // local = element (compact: row = B+1) or entry (quad: row = B) offset inside the slot.
+// Clamp to edge: i = floor(x) < 0 gives i0 = 0 and weight 0, i >= D_l - 1 gives i0 = D_l - 1 and
+// weight 0, else i0 = i and weight x - i.  Clamping x itself to [0, D_l - 1] first gives exactly
+// these (x below 0 becomes 0, x at or past D_l - 1 becomes D_l - 1, both with zero fraction)
+// without a branch.
 __device__ __forceinline__ void resolve_reg(const LvReg& L, int bshift, int bmask, int row, const float p[3],
                                             Resolved& R) {
     int h[3], l[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float x = __fsub_rn(__fmul_rn(p[a], L.r[a]), 0.5f);
-        const float fx = floorf(x);
-        const int i = (int)fx;
-        if (i < 0) {
-            R.i0[a] = 0;
-            R.w[a] = 0.0f;
-        } else if (i >= L.Dm[a]) {
-            R.i0[a] = L.Dm[a];
-            R.w[a] = 0.0f;
-        } else {
-            R.i0[a] = i;
-            R.w[a] = __fsub_rn(x, fx);
-        }
+        const float xc = fminf(fmaxf(x, 0.0f), L.Dm[a]);
+        const float fx = floorf(xc);
+        R.i0[a] = (int)fx;
+        R.w[a] = __fsub_rn(xc, fx);
         h[a] = R.i0[a] >> bshift;
         l[a] = R.i0[a] & bmask;
     }
@@ -815,9 +812,12 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 int lv[kBatch];        // LS: their levels
                 uint32_t sub[kBatch];  // SP: brick position inside the middle and leaf pages
                 tv[0] = tcur;
+                // sample indices as floats: (float)(k + j) = (float)k + j exactly, since the host
+                // keeps every index of a ray below 2^24 (kMaxSamplesPerRay)
+                const float kf = (float)k;
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
-                    const float t = LS ? tv[j] : __fadd_rn(t0, __fmul_rn((float)(k + j), step));
+                    const float t = LS ? tv[j] : __fadd_rn(t0, __fmul_rn(__fadd_rn(kf, (float)j), step));
                     if (!(t < t1) && nvalid == kBatch) nvalid = j;
                     const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
                                         __fadd_rn(o2, __fmul_rn(t, d2))};

@@ -1465,6 +1465,14 @@ int vol_set_provider_batch(vol_t v, vol_provider_batch_fn fn, void* user, int sr
     return VOL_OK;
 }
 
+// The longest segment of a ray inside [0, D0) is the box diagonal: its sample count (plus the
+// samples a batch computes past the exit) must stay within kMaxSamplesPerRay.
+static bool samples_fit(const vol_s* v, float step) {
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) d2 += (double)v->lay.dims[a] * (double)v->lay.dims[a];
+    return std::sqrt(d2) / (double)step + 2.0 < kMaxSamplesPerRay;
+}
+
 int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev, const vol_params* params,
                float* rgba_dev, int32_t* nsamples_dev) {
     if (!v) return VOL_ERR_INVALID_ARG;
@@ -1472,6 +1480,8 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     if (nviews < 1 || nviews > VOL_MAX_VIEWS) return fail(v, VOL_ERR_INVALID_ARG, "nviews out of range");
     vol_params p = *params;
     if (!(p.step > 0.0f) || !std::isfinite(p.step)) return fail(v, VOL_ERR_INVALID_ARG, "step must be > 0");
+    if (!samples_fit(v, p.step))
+        return fail(v, VOL_ERR_INVALID_ARG, "step too small: more than 2^24 samples along the volume diagonal");
     if (p.tile_w <= 0) p.tile_w = 4;
     if (p.tile_h <= 0) p.tile_h = 8;
     if (p.tile_w > 4096 || p.tile_h > 4096 || p.tile_w * p.tile_h > 4096)
@@ -1498,6 +1508,8 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     for (int i = 0; i < nviews; ++i) {
         const vol_camera& c = cams[i];
         if (c.w < 1 || c.h < 1 || c.w > 65536 || c.h > 65536) return fail(v, VOL_ERR_INVALID_ARG, "bad image size");
+        if (!(c.tan_half_fov > 0.0f) || !std::isfinite(c.tan_half_fov))
+            return fail(v, VOL_ERR_INVALID_ARG, "tan_half_fov must be > 0");
         ViewDev& V = v->views_host[i];
         for (int a = 0; a < 3; ++a) {
             V.eye[a] = c.eye[a];
@@ -1696,6 +1708,8 @@ int vol_trace(vol_t v, const vol_camera* cam, const vol_params* params, const in
         return fail(v, VOL_ERR_INVALID_ARG, "bad trace arguments");
     if (npix == 0) return VOL_OK;
     if (cam->w < 1 || cam->h < 1) return fail(v, VOL_ERR_INVALID_ARG, "bad image size");
+    if (!(cam->tan_half_fov > 0.0f) || !std::isfinite(cam->tan_half_fov))
+        return fail(v, VOL_ERR_INVALID_ARG, "tan_half_fov must be > 0");
     for (int i = 0; i < npix; ++i)
         if (pixels_host[2 * i] < 0 || pixels_host[2 * i] >= cam->w || pixels_host[2 * i + 1] < 0 ||
             pixels_host[2 * i + 1] >= cam->h)
@@ -1796,6 +1810,8 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
         return fail(v, VOL_ERR_INVALID_ARG, "nviews must be 1..VOL_NOALLOC_MAX_VIEWS (64) for vol_render_noalloc");
     vol_params p = *params;
     if (!(p.step > 0.0f) || !std::isfinite(p.step)) return fail(v, VOL_ERR_INVALID_ARG, "step must be > 0");
+    if (!samples_fit(v, p.step))
+        return fail(v, VOL_ERR_INVALID_ARG, "step too small: more than 2^24 samples along the volume diagonal");
     if (p.tile_w <= 0) p.tile_w = 4;
     if (p.tile_h <= 0) p.tile_h = 8;
     if (p.tile_w > 4096 || p.tile_h > 4096 || p.tile_w * p.tile_h > 4096)
@@ -1816,6 +1832,8 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
     for (int i = 0; i < nviews; ++i) {
         const vol_camera& c = cams[i];
         if (c.w < 1 || c.h < 1 || c.w > 65536 || c.h > 65536) return fail(v, VOL_ERR_INVALID_ARG, "bad image size");
+        if (!(c.tan_half_fov > 0.0f) || !std::isfinite(c.tan_half_fov))
+            return fail(v, VOL_ERR_INVALID_ARG, "tan_half_fov must be > 0");
         ViewDev& V = views[i];
         V = ViewDev{};
         for (int a = 0; a < 3; ++a) {

@@ -128,6 +128,23 @@ def test_empty_volume_and_edge_images(P, orc):
     np.testing.assert_array_equal(out, np.tile(np.float32(bg), (81, 1)))
 
 
+def test_camera_without_field_of_view_is_refused(P):
+    """A field of view of zero, negative or not finite gives no footprint (Sec. V-C) and no image:
+    VOL_ERR_INVALID_ARG from render and trace, before any device work."""
+    D = (40, 24, 33)
+    vol = gpu_volume(P, np.zeros((33, 24, 40), np.uint8), "u8", "u8", 16, 2)
+    good = synth.seeded_orbit(D, 8, 8, 3)
+    for bad in (0.0, -0.5, float("inf"), float("nan")):
+        cam = dict(good, tan_half_fov=bad)
+        with pytest.raises(RuntimeError) as e:
+            vol.render([good, cam], tf_dev(synth.tf_ramp()), {"lod_mode": 1})
+        assert e.value.code == P.C.VOL_ERR_INVALID_ARG
+        with pytest.raises(RuntimeError) as e:
+            vol.trace(cam, {"lod_mode": 1}, np.array([[0, 0]]), 8)
+        assert e.value.code == P.C.VOL_ERR_INVALID_ARG
+    vol.render(good, tf_dev(synth.tf_ramp()), {"lod_mode": 1})
+
+
 @pytest.mark.parametrize("dtype", ["u8", "u16", "f16", "f32"])
 def test_ragged_volume_inside_camera(P, orc, dtype):
     """Odd dims, bricks of 8, a camera inside the volume, all storage types, LOD on."""
