@@ -583,12 +583,12 @@ __device__ __forceinline__ void suspend_ray(const RenderDev& P, long long ray, i
 // Samples per lane per loop iteration: their page-table lookups and gathers are issued together,
 // then composited in order (memory-level parallelism along one ray).
 #ifndef VOLRC_BATCH
-#define VOLRC_BATCH 4
+#define VOLRC_BATCH 6
 #endif
 constexpr int kBatch = VOLRC_BATCH;
 // Minimum resident CTAs per SM the register allocation must allow.
 #ifndef VOLRC_MIN_CTAS
-#define VOLRC_MIN_CTAS 6
+#define VOLRC_MIN_CTAS 5
 #endif
 
 __host__ __device__ constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
@@ -865,13 +865,19 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
 #pragma unroll
                     for (int j = 0; j < kBatch; ++j) slot[j] = __ldg(P.vol.pt + (j < nvalid ? pti[j] : 0u));
                 }
+                // (the entries at miss_at and empty_at are selected in these loops: indexing the
+                // arrays with a run-time index would move them to local memory)
                 int miss_at = kBatch;
+                uint32_t miss_pti = 0u;
 #pragma unroll
                 for (int j = kBatch - 1; j >= 0; --j)
-                    if (j < nvalid && slot[j] == kInvalidSlot) miss_at = j;
-                const uint32_t miss_pti = miss_at < kBatch ? pti[miss_at] : 0u;
+                    if (j < nvalid && slot[j] == kInvalidSlot) {
+                        miss_at = j;
+                        miss_pti = pti[j];
+                    }
                 // usage stamps (one store per brick change) and empty-brick test
                 int empty_at = kBatch;
+                uint32_t empty_pti = 0u;
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
                     if (j < nvalid && j < miss_at) {
@@ -885,7 +891,10 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                                 else cur_empty = brick_empty<DT>(rng, s_apre);
                             }
                         }
-                        if (cur_empty && empty_at == kBatch) empty_at = j;
+                        if (cur_empty && empty_at == kBatch) {
+                            empty_at = j;
+                            empty_pti = pti[j];
+                        }
                     }
                 }
                 // (c) gathers, all issued together (unused samples read slot 0, element 0)
@@ -919,10 +928,10 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                             request_brick64(P, sparse_request_key<LOD>(tcur_or_t(LS, tcur, t0, k, step), o0, o1, o2, d0,
                                                                        d1, d2, lodscale, P.lod_bias, nlev, s_lv,
                                                                        bshift, bmask, row));
-                    } else if (P.req_table && pti[miss_at] != cur_pti) {
-                        request_brick(P, pti[miss_at] + 1u);
+                    } else if (P.req_table && miss_pti != cur_pti) {
+                        request_brick(P, miss_pti + 1u);
                     }
-                    cur_pti = SP ? kInvalidSlot : pti[miss_at];
+                    cur_pti = SP ? kInvalidSlot : miss_pti;
                     cur_empty = false;
                     const float tk = LS ? tcur : __fadd_rn(t0, __fmul_rn((float)k, step));
                     const int lk = LOD ? lod_level(tk, lodscale, P.lod_bias, nlev) : 0;
@@ -945,7 +954,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     // sample k is in a brick of zero opacity: every sample up to the brick's last
                     // composites nothing, so continue after it
                     const float o3[3] = {o0, o1, o2}, d3[3] = {d0, d1, d2};
-                    const int klast = brick_last_sample<LOD>(k, pti[empty_at], o3, d3, t0, t1, step, lodscale,
+                    const int klast = brick_last_sample<LOD>(k, empty_pti, o3, d3, t0, t1, step, lodscale,
                                                              P.lod_bias, nlev, s_lv, bshift, bmask, row, B1 - 1);
                     if (GRAD)
                         for (int kk = ((k + kCkptEvery - 1) / kCkptEvery) * kCkptEvery; kk <= klast; kk += kCkptEvery)
