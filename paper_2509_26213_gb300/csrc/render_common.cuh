@@ -593,19 +593,31 @@ constexpr int kBatch = VOLRC_BATCH;
 
 __host__ __device__ constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
 
-// One sample's compositing step for mode MODE (lane state C0..C2, T as k_render keeps it);
-// returns true when the ray may stop after it.
-template <int DT, int MODE, bool LS = false>
-__device__ __forceinline__ bool composite_sample(float val, const float4* s_tf, const float4* s_tfd, float amax_tf,
-                                                 float et, float& T, float& C0, float& C1, float& C2, int l = 0) {
+// The TF row of one sample: weight wt, entry a = tf[i] and dab = tf[i+1] - tf[i] at the TF
+// coordinate of the interpolated value (i = min(floor(x), 254)).
+template <int DT>
+__device__ __forceinline__ void tf_index(float val, int& i, float& wt) {
     const float x = tf_coord<DT>(val);
-    if (MODE == kMip) {
-        if (x > T) T = x;
-        return T >= 255.0f;  // no coordinate lies above 255
-    }
-    const int i = min((int)x, 254);
-    const float wt = x - (float)i;
-    const float4 a = s_tf[i], dab = s_tfd[i];  // entry i and tf[i+1] - tf[i]
+    i = min((int)x, 254);
+    wt = x - (float)i;
+}
+
+template <int DT>
+__device__ __forceinline__ void tf_row(float val, const float4* s_tf, const float4* s_tfd, float& wt, float4& a,
+                                       float4& dab) {
+    int i;
+    tf_index<DT>(val, i, wt);
+    a = s_tf[i];
+    dab = s_tfd[i];
+}
+
+// One sample's compositing step for mode MODE (not MIP) from its TF row (lane state C0..C2, T as
+// k_render keeps it); returns true when the ray may stop after it.  Split from the row read so
+// that a batch's rows can be read before any of its samples is composited.
+template <int MODE, bool LS = false>
+__device__ __forceinline__ bool composite_row(float wt, float4 a, float4 dab, float amax_tf, float et, float& T,
+                                              float& C0, float& C1, float& C2, int l = 0) {
+    static_assert(MODE != kMip, "MIP composites the TF coordinate");
     const float al = fmaf(wt, dab.w, a.w);
     if (MODE == kMop) {
         if (al > T) {  // the first sample of largest opacity is kept
@@ -633,6 +645,22 @@ __device__ __forceinline__ bool composite_sample(float val, const float4* s_tf, 
     C2 = fmaf(Ta, fmaf(wt, dab.z, a.z), C2);
     T = T * (1.0f - al);
     return __fsub_rn(1.0f, T) >= et;
+}
+
+// One sample's compositing step from its interpolated value, any mode.
+template <int DT, int MODE, bool LS = false>
+__device__ __forceinline__ bool composite_sample(float val, const float4* s_tf, const float4* s_tfd, float amax_tf,
+                                                 float et, float& T, float& C0, float& C1, float& C2, int l = 0) {
+    if constexpr (MODE == kMip) {
+        const float x = tf_coord<DT>(val);
+        if (x > T) T = x;
+        return T >= 255.0f;  // no coordinate lies above 255
+    } else {
+        float wt;
+        float4 a, dab;
+        tf_row<DT>(val, s_tf, s_tfd, wt, a, dab);
+        return composite_row<MODE, LS>(wt, a, dab, amax_tf, et, T, C0, C1, C2, l);
+    }
 }
 
 // Depth of sample k: the kept depth under level-scaled sampling, else t0 + k dt.
@@ -907,15 +935,37 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 }
                 const int stop = min(min(nvalid, miss_at), empty_at);
                 bool fin = false;
+                if constexpr (MODE != kMip) {
+                    // TF rows: indices and weights of the batch first, then each sample's row is
+                    // read while the one before it is composited (no branch before the read)
+                    int ti[kBatch];
+                    float tw[kBatch];
 #pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    if (j < stop && !fin) {
-                        if (GRAD && k > 0 && (k & (kCkptEvery - 1)) == 0)
-                            P.ckpt[(long long)(k / kCkptEvery - 1) * P.nrays + ray] = T;
-                        fin = composite_sample<DT, MODE, LS>(val[j], s_tf, s_tfd, amax_tf, et, T, C0, C1, C2,
-                                                             LS ? lv[j] : 0);
-                        ++k;
-                        if (LS) tcur = tv[j + 1];
+                    for (int j = 0; j < kBatch; ++j) tf_index<DT>(val[j], ti[j], tw[j]);
+                    float4 an = s_tf[ti[0]], dn = s_tfd[ti[0]];
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        const float4 a = an, dab = dn;
+                        if (j + 1 < kBatch) {
+                            an = s_tf[ti[j + 1]];
+                            dn = s_tfd[ti[j + 1]];
+                        }
+                        if (j < stop && !fin) {
+                            if (GRAD && k > 0 && (k & (kCkptEvery - 1)) == 0)
+                                P.ckpt[(long long)(k / kCkptEvery - 1) * P.nrays + ray] = T;
+                            fin = composite_row<MODE, LS>(tw[j], a, dab, amax_tf, et, T, C0, C1, C2,
+                                                          LS ? lv[j] : 0);
+                            ++k;
+                            if (LS) tcur = tv[j + 1];
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        if (j < stop && !fin) {
+                            fin = composite_sample<DT, MODE>(val[j], s_tf, s_tfd, amax_tf, et, T, C0, C1, C2);
+                            ++k;
+                        }
                     }
                 }
                 bool fell = false;
