@@ -145,6 +145,21 @@ def test_camera_without_field_of_view_is_refused(P):
     vol.render(good, tf_dev(synth.tf_ramp()), {"lod_mode": 1})
 
 
+def test_step_beyond_binary32_sample_indices_is_refused(P):
+    """Sample indices stay below 2^24 (past it neighbouring indices give the same depth in
+    binary32): a step that puts more samples than that on the volume diagonal (57.1 voxels here)
+    is VOL_ERR_INVALID_ARG; one just inside renders."""
+    D = (40, 24, 33)
+    vol = gpu_volume(P, np.zeros((33, 24, 40), np.uint8), "u8", "u8", 16, 1)
+    cam = synth.seeded_orbit(D, 2, 2, 3)
+    diag = float(np.sqrt(sum(d * d for d in D)))
+    with pytest.raises(RuntimeError) as e:
+        vol.render(cam, tf_dev(synth.tf_ramp()), {"step": diag / (2 ** 24 - 32)})
+    assert e.value.code == P.C.VOL_ERR_INVALID_ARG
+    out = vol.render(cam, tf_dev(synth.tf_ramp(alpha_max=0.0)), {"step": diag / (2 ** 24 - 128), "bg": (0, 0, 0, 1)})
+    np.testing.assert_array_equal(out.cpu().numpy(), np.tile(np.float32([0, 0, 0, 1]), (4, 1)))
+
+
 @pytest.mark.parametrize("dtype", ["u8", "u16", "f16", "f32"])
 def test_ragged_volume_inside_camera(P, orc, dtype):
     """Odd dims, bricks of 8, a camera inside the volume, all storage types, LOD on."""
