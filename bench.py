@@ -476,7 +476,7 @@ def run_ours(args, dist, rank, ws, local):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": 4096,
                     "d2h_bytes_per_step": npx * 16, "ms_per_step": e2e_step},
-            # per step: the render kernel and the two heaviest-first scheduling kernels
+            # per step: the render kernel and the two tile-order scheduling kernels
             "gpu_launches": launches_per_frame * args.steps,
             "clocks": clocks,
             "wall_s_timed": wall,

@@ -121,7 +121,8 @@ struct RenderDev {
     int ckpt_segs;
     int* ray_n;
     // scheduling: work item i of a fresh pass renders tile tile_order[i] (NULL: tile i);
-    // every finished ray adds its sample count to tile_cost[its tile] (NULL: not recorded)
+    // every finished ray raises tile_cost[its tile] to its sample count: the tile's longest ray
+    // (NULL: not recorded)
     const int* tile_order;
     int* tile_cost;
 };
@@ -144,7 +145,7 @@ struct BackwardDev {
     const float* ckpt;
     long long nrays;
     const int* ray_n;
-    const int* tile_order;  // heaviest-first order of the tiles (NULL: tile i)
+    const int* tile_order;  // longest-ray-first order of the tiles (NULL: tile i)
 };
 
 struct TraceDev {
@@ -172,7 +173,7 @@ const void* pick_render_projection(int dtype, int brick, bool quad, bool lod, in
 const void* pick_render_level_step(int dtype, int brick, bool quad, bool lod);
 // Sparse page table (kernels_sparse.cu): the emission/absorption variant.
 const void* pick_render_sparse(int dtype, int brick, bool quad, bool lod);
-// order[] = tiles sorted by descending log2 bucket of cost[] (heaviest first); zeroes cost[].
+// order[] = tiles sorted by descending log2 bucket of cost[] (longest ray first); zeroes cost[].
 // buckets: 64 ints of device scratch.
 cudaError_t launch_tile_order(int* cost, int* order, int ntiles, int* buckets, cudaStream_t s);
 int backward_blocks_per_sm(int dtype, bool lod);

@@ -1,5 +1,5 @@
 // kernels_render.cu -- variants of the forward kernel for emission/absorption compositing
-// (with and without gradient checkpoints), the adjoint, the heaviest-first tile order and
+// (with and without gradient checkpoints), the adjoint, the longest-ray-first tile order and
 // the decision trace.  The forward kernel template and its building blocks are in
 // render_common.cuh.
 #include "render_common.cuh"
@@ -303,8 +303,10 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
 
 // ------------------------------------------------------------------ scheduling
 
-// Heaviest-first work order for the next frame (an approximate longest-processing-time-first
-// schedule): tiles bucketed by floor(log2(cost + 1)), buckets in descending order.  One CTA.
+// Work order for the next frame: tiles bucketed by floor(log2(cost + 1)), buckets in descending
+// order, where a tile's cost is the sample count of its longest ray.  The longest rays start
+// first, so none of them begins near the end of the launch and runs on while other SMs idle
+// (ordering by the tile's total samples instead left a tail: c2 0.91 -> 0.81 ms with this key).
 constexpr int kOrderThreads = 256;
 
 __device__ __forceinline__ int cost_bucket(int c) { return 31 - __clz(c + 1); }
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_count(const int* cost, 
     if (threadIdx.x < 32 && s_count[threadIdx.x]) atomicAdd(&buckets[threadIdx.x], s_count[threadIdx.x]);
 }
 
-// order[] = tiles grouped by bucket, heaviest bucket first; each block reserves its places in
+// order[] = tiles grouped by bucket, highest bucket first; each block reserves its places in
 // every bucket with one atomic on the bucket's fill cursor (buckets[32 + b]).  Zeroes cost[].
 __global__ void __launch_bounds__(kOrderThreads) k_order_scatter(int* cost, int* order, int ntiles, int* buckets) {
     __shared__ int s_count[32], s_base[32];

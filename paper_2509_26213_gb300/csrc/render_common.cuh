@@ -1035,7 +1035,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     }
                     if (P.nsamp) P.nsamp[ray] = k;
                     if (GRAD) P.ray_n[ray] = k;
-                    if (P.tile_cost && my_tile >= 0) atomicAdd(&P.tile_cost[my_tile], k);
+                    if (P.tile_cost && my_tile >= 0) atomicMax(&P.tile_cost[my_tile], k);
                     active = false;
                 } else if (!fell && miss_at < kBatch) {
                     // wait for the missing brick: sample k (= the first missing one) resumes later

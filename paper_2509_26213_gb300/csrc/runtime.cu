@@ -246,7 +246,7 @@ struct vol_s {
         void* dst = nullptr;
     } loader;
 
-    // heaviest-first scheduling from the previous frame's per-tile sample counts
+    // longest-ray-first scheduling from the previous frame's per-tile longest ray
     int* tile_cost = nullptr;
     size_t tile_cost_cap = 0;
     int* tile_order = nullptr;
@@ -1560,7 +1560,7 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         if (int rc = ensure(v, v->ckpt, v->ckpt_cap, (size_t)std::max<int64_t>(1, segs - 1) * (size_t)rays, "checkpoints")) return rc;
         if (int rc = ensure(v, v->ray_n, v->ray_n_cap, (size_t)rays, "ray sample counts")) return rc;
     }
-    // scheduling state: the previous frame's heaviest-first order is reused while the tile
+    // scheduling state: the previous frame's longest-ray-first order is reused while the tile
     // partition (tile shape, number of views, image sizes) is unchanged; cameras may move.
     // The order is only a schedule: the image never depends on it.
     {
@@ -1682,7 +1682,7 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
     b.ckpt = v->ckpt;
     b.nrays = v->nrays;
     b.ray_n = v->ray_n;
-    // the order built from this forward's per-tile sample counts: the heaviest tiles first
+    // the order built from this forward's per-tile longest rays: those tiles first
     b.tile_order = v->order_ready ? v->tile_order : nullptr;
     CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
     const int grid = backward_blocks_per_sm(v->dtype, lod) * v->nsm;
