@@ -14,7 +14,8 @@ import statistics
 
 import torch
 
-DEFAULT_TILES = ((4, 8), (8, 4), (8, 8), (16, 16), (32, 4))
+# one warp's worth of rays per tile first (the shapes that win on GB300), then larger tiles
+DEFAULT_TILES = ((4, 8), (8, 4), (2, 16), (32, 1), (8, 8), (16, 16), (32, 4))
 DEFAULT_REFILL = (16, 20, 28)
 
 
