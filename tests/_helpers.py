@@ -44,6 +44,19 @@ def compare(gpu: np.ndarray, ref: dict, tol: float, idx=None):
     return float(err.max(initial=0.0)), bad, use_alt
 
 
+def compare_projection(gpu: np.ndarray, ref: dict, tol: float):
+    """MOP/MIP: alpha within tol of the oracle's; each colour within tol of the range the oracle
+    gives over the samples whose opacity ties the maximum within its ambiguity bound.
+    Returns (max error, pixels that failed, pixels with a non-degenerate range)."""
+    gpu = gpu.astype(np.float64)
+    ea = np.abs(gpu[:, 3] - ref["rgba"][:, 3])
+    below = np.clip(ref["lo"][:, :3] - gpu[:, :3], 0, None).max(axis=1)
+    above = np.clip(gpu[:, :3] - ref["hi"][:, :3], 0, None).max(axis=1)
+    err = np.maximum(ea, np.maximum(below, above))
+    strict = np.all(ref["lo"] == ref["hi"], axis=1)
+    return float(err.max(initial=0.0)), np.flatnonzero(err > tol), int((~strict).sum())
+
+
 def c1_inputs(seed=1):
     """Plain FP32 single view: 128^3 u8 blobs + noise, 32^3 bricks, 2 levels, 256x256 orbit view,
     45 deg FOV, step 0.5, piecewise-linear ramp TF, early termination at 0.99."""

@@ -8,9 +8,12 @@ import torch
 
 import synth
 from synth import workloads
-from _helpers import AMB, TOL_FP32, TOL_REDUCED, compare
+from _helpers import AMB, TOL_FP32, TOL_REDUCED, compare, compare_projection
 
 pytestmark = pytest.mark.gpu
+
+SKIP = 2         # VOL_RENDER_SKIP_EMPTY
+LEVEL_STEP = 16  # VOL_RENDER_LEVEL_STEP
 
 
 @pytest.fixture(scope="module")
@@ -81,6 +84,41 @@ def test_c2_reduced_precision_sampled(P, orc, c2_data, store):
     print(f"C2 {store}: max abs err {worst:.3g} on 4096 sampled pixels; levels traced {sorted(seen)}")
     assert worst <= TOL_FP32  # decoded alike on both sides: only float32 arithmetic differs
     assert len(seen) >= 2
+
+
+def test_c2_bench_variants_sampled(P, orc, c2_data):
+    """The variant lines bench.py times on the full C2 frame (u16 store): maximum-opacity and
+    maximum-intensity projection, level-scaled sampling and empty-space skipping, each on 1024
+    seeded pixels against the oracle (skipping must also give the default image bit for bit)."""
+    wl, raw, lev_u16, _ = c2_data
+    vol = P.Volume(wl["D"], "u16", wl["brick"], wl["levels"])
+    vol.upload_level(0, raw, wl["src"])
+    vol.build_lod(0)
+    tf = torch.from_numpy(wl["tf"]).cuda()
+    ovol = orc.Volume(lev_u16, "u16", wl["brick"])
+    cam = wl["cams"][0]
+    pix = synth.pixel_subset(cam["w"], cam["h"], 1024, 7)
+    idx = pix[:, 1].astype(np.int64) * cam["w"] + pix[:, 0]
+    base = dict(wl["params"])
+    default = vol.render(cam, tf, base).cpu().numpy()
+    np.testing.assert_array_equal(vol.render(cam, tf, dict(base, flags=SKIP)).cpu().numpy(), default)
+    for mode in ("mop", "mip"):
+        prm = dict(base, composite=mode)
+        gpu = vol.render(cam, tf, prm).cpu().numpy()[idx]
+        ref = orc.render_max(ovol, cam, wl["tf"], prm, mode, pixels=pix, amb=AMB)
+        err, bad, near = compare_projection(gpu, ref, TOL_REDUCED)
+        assert len(bad) == 0, f"{mode}: {len(bad)} pixels above {TOL_REDUCED}, max {err}"
+        assert err <= TOL_FP32
+        np.testing.assert_array_equal(vol.render(cam, tf, dict(prm, flags=SKIP)).cpu().numpy()[idx], gpu)
+    prm = dict(base, flags=LEVEL_STEP)
+    out, ns = vol.render(cam, tf, prm, nsamples=True)
+    gpu, n = out.cpu().numpy()[idx], ns.cpu().numpy()[idx]
+    ref = orc.render(ovol, cam, wl["tf"], prm, pixels=pix, amb=AMB)
+    err, bad, alt = compare(gpu, ref, TOL_REDUCED)
+    assert len(bad) == 0 and err <= TOL_FP32, (err, len(bad))
+    assert np.all((n == ref["n"]) | (alt & (n == ref["alt_n"])))
+    assert vol.stats()["device_error"] == 0
+    vol.close()
 
 
 def test_c3_batched_sampled(P, orc):

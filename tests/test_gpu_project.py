@@ -12,6 +12,7 @@ import torch
 
 import synth
 from _helpers import TOL_FP32, TOL_REDUCED, c1_inputs, store_levels
+from _helpers import compare_projection as check
 
 pytestmark = pytest.mark.gpu
 
@@ -39,17 +40,6 @@ def gpu_volume(P, raw0, dtype, brick, levels, cache_bytes=0, layout="quad"):
 
 def tf_dev(tf):
     return torch.from_numpy(np.ascontiguousarray(tf, dtype=np.float32)).cuda()
-
-
-def check(gpu, ref, tol):
-    """Alpha within tol of the oracle's; each colour within tol of the near-maximal range."""
-    gpu = gpu.astype(np.float64)
-    ea = np.abs(gpu[:, 3] - ref["rgba"][:, 3])
-    below = np.clip(ref["lo"][:, :3] - gpu[:, :3], 0, None).max(axis=1)
-    above = np.clip(gpu[:, :3] - ref["hi"][:, :3], 0, None).max(axis=1)
-    err = np.maximum(ea, np.maximum(below, above))
-    strict = np.all(ref["lo"] == ref["hi"], axis=1)
-    return float(err.max(initial=0.0)), np.flatnonzero(err > tol), int((~strict).sum())
 
 
 def tf_for(kind, seed):
