@@ -319,15 +319,15 @@ def run_ours(args, dist, rank, ws, local):
     total_samples = sum_over_ranks(dist, samples)
     value = total_samples / (t_step * 1e-3)
 
-    # end to end through the public API with host buffers: TF up, image down, every step
+    # end to end through the public API with host buffers: TF up, image down, every step.  The
+    # image goes to page-locked host memory that the render kernel writes directly (through the
+    # host link), so no separate copy follows the render.
     tf_host = torch.from_numpy(wl["tf"]).pin_memory()
     img_host = torch.empty((npx, 4), dtype=torch.float32).pin_memory()
     tf_dev = torch.empty_like(tf)
-    out_dev = torch.empty((npx, 4), dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         tf_dev.copy_(tf_host, non_blocking=True)
-        vol.render(cams, tf_dev, params, out=out_dev)
-        img_host.copy_(out_dev, non_blocking=True)
+        vol.render(cams, tf_dev, params, out=img_host)
     torch.cuda.synchronize()
     barrier(dist)
     e2e_ms = []
@@ -336,8 +336,7 @@ def run_ours(args, dist, rank, ws, local):
         torch.cuda.synchronize()
         t = time.perf_counter()
         tf_dev.copy_(tf_host, non_blocking=True)
-        vol.render(cams, tf_dev, params, out=out_dev)
-        img_host.copy_(out_dev, non_blocking=True)
+        vol.render(cams, tf_dev, params, out=img_host)
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t))
     e2e_step = max_over_ranks(dist, statistics.mean(e2e_ms))
@@ -475,7 +474,8 @@ def run_ours(args, dist, rank, ws, local):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": 4096,
-                    "d2h_bytes_per_step": npx * 16, "ms_per_step": e2e_step},
+                    "d2h_bytes_per_step": npx * 16, "ms_per_step": e2e_step,
+                    "image": "written by the render kernel into page-locked host memory"},
             # per step: the render kernel and the two tile-order scheduling kernels
             "gpu_launches": launches_per_frame * args.steps,
             "clocks": clocks,

@@ -299,9 +299,14 @@ int vol_set_provider_batch(vol_t v, vol_provider_batch_fn fn, void *user, int sr
 /* Renders nviews views (cams: host array) in one persistent launch that
  * takes ray tiles of all views from one work counter.  tf_dev: device
  * float [256][4] RGBA transfer function (entry j at value j / 255, linearly
- * interpolated).  rgba_dev: device output, the views' images packed in
- * order.  nsamples_dev: optional device int32 per pixel, the number of
- * samples composited (NULL to skip).
+ * interpolated).  rgba_dev: output float [pixels][4], the views' images
+ * packed in order, in memory of the volume's GPU or in page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister; the kernel then writes the image
+ * through its device mapping across the host link, so the result needs no
+ * copy and is complete when the volume's stream is); any other pointer gives
+ * VOL_ERR_INVALID_ARG before any launch.  nsamples_dev: optional int32 per
+ * pixel, the number of samples composited (NULL to skip), in the same kinds
+ * of memory.
  * Sample k of a ray is at t_k = t0 + k * step while t_k < t1 (entry/exit of
  * the box); C += T a rgb, T *= 1 - a; the ray stops after the sample where
  * 1 - T >= et_threshold; output rgb = C + T bg_rgb, a = (1 - T) + T bg_a.
@@ -367,7 +372,7 @@ int vol_trace(vol_t v, const vol_camera *cam, const vol_params *params, const in
  *     that are not ordered) race.  Calls on one stream are ordered and safe.
  *   - It neither queues brick requests nor keeps state for
  *     vol_render_backward(), and it does not update the LRU usage stamps.
- * Errors: VOL_ERR_INVALID_ARG (null pointers, nviews outside
+ * Errors: VOL_ERR_INVALID_ARG (null pointers, an output the GPU cannot address, nviews outside
  * 1..VOL_NOALLOC_MAX_VIEWS, bad image size or tile), VOL_ERR_UNSUPPORTED
  * (VOL_RENDER_GRAD set, or a needed level not fully resident), VOL_ERR_CUDA. */
 #define VOL_NOALLOC_SCRATCH_BYTES 8192

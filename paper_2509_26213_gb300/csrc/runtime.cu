@@ -1465,6 +1465,41 @@ int vol_set_provider_batch(vol_t v, vol_provider_batch_fn fn, void* user, int sr
     return VOL_OK;
 }
 
+// The address the kernels write an output through: memory of the volume's GPU (or managed memory)
+// as it is, page-locked host memory through its device mapping -- the kernels then write the
+// image across the host link and the caller needs no copy -- and anything else is refused
+// before any launch.
+static int device_address(vol_t v, void* p, void** out, const char* what) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(v, VOL_ERR_INVALID_ARG, what);
+    }
+    if ((a.type == cudaMemoryTypeDevice && a.device == v->device) || a.type == cudaMemoryTypeManaged) {
+        *out = p;
+        return VOL_OK;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *out = a.devicePointer;
+        return VOL_OK;
+    }
+    return fail(v, VOL_ERR_INVALID_ARG, what);
+}
+
+static int output_addresses(vol_t v, float*& rgba, int32_t*& nsamples) {
+    void* p = nullptr;
+    if (int rc = device_address(v, rgba, &p, "rgba must be memory of the volume's GPU or page-locked host memory"))
+        return rc;
+    rgba = (float*)p;
+    if (nsamples) {
+        if (int rc = device_address(v, nsamples, &p,
+                                    "nsamples must be memory of the volume's GPU or page-locked host memory"))
+            return rc;
+        nsamples = (int32_t*)p;
+    }
+    return VOL_OK;
+}
+
 // The longest segment of a ray inside [0, D0) is the box diagonal: its sample count (plus the
 // samples a batch computes past the exit) must stay within kMaxSamplesPerRay.
 static bool samples_fit(const vol_s* v, float step) {
@@ -1478,6 +1513,7 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     if (!v) return VOL_ERR_INVALID_ARG;
     if (!cams || !tf_dev || !params || !rgba_dev) return fail(v, VOL_ERR_INVALID_ARG, "null argument");
     if (nviews < 1 || nviews > VOL_MAX_VIEWS) return fail(v, VOL_ERR_INVALID_ARG, "nviews out of range");
+    if (int rc = output_addresses(v, rgba_dev, nsamples_dev)) return rc;
     vol_params p = *params;
     if (!(p.step > 0.0f) || !std::isfinite(p.step)) return fail(v, VOL_ERR_INVALID_ARG, "step must be > 0");
     if (!samples_fit(v, p.step))
@@ -1808,6 +1844,7 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
     if (!cams || !tf_dev || !params || !rgba_dev) return fail(v, VOL_ERR_INVALID_ARG, "null argument");
     if (nviews < 1 || nviews > VOL_NOALLOC_MAX_VIEWS)
         return fail(v, VOL_ERR_INVALID_ARG, "nviews must be 1..VOL_NOALLOC_MAX_VIEWS (64) for vol_render_noalloc");
+    if (int rc = output_addresses(v, rgba_dev, nsamples_dev)) return rc;
     vol_params p = *params;
     if (!(p.step > 0.0f) || !std::isfinite(p.step)) return fail(v, VOL_ERR_INVALID_ARG, "step must be > 0");
     if (!samples_fit(v, p.step))

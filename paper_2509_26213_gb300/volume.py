@@ -175,7 +175,8 @@ class Volume:
     # ------------------------------------------------------------ render
     def render(self, cams, tf: torch.Tensor, params: dict | None = None, out: torch.Tensor | None = None,
                nsamples: bool = False, grad: bool = False, check_incomplete: bool = True):
-        """Render views (list of camera dicts) -> float32 CUDA tensor [sum(w*h), 4] (views packed)."""
+        """Render views (list of camera dicts) -> float32 tensor [sum(w*h), 4] (views packed): a new
+        CUDA tensor, or ``out`` (CUDA, or pinned host memory that the kernel writes directly)."""
         if isinstance(cams, dict):
             cams = [cams]
         params = dict(params or {})
@@ -188,6 +189,10 @@ class Volume:
         dev = tf.device
         if out is None:
             out = torch.empty((npx, 4), dtype=torch.float32, device=dev)
+        elif not (out.dtype == torch.float32 and out.is_contiguous() and out.numel() >= 4 * npx
+                  and (out.is_cuda or out.is_pinned())):
+            # a pinned host tensor receives the image across the host link, with no copy
+            raise ValueError("out must be a contiguous float32 CUDA or pinned host tensor of sum(w*h) x 4")
         ns = torch.empty(npx, dtype=torch.int32, device=dev) if nsamples else None
         p = params_struct(**params, grad=grad)
         rc = self.lib.vol_render(self.h, arr, len(cams), ctypes.c_void_p(tf.data_ptr()), ctypes.byref(p),

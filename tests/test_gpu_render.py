@@ -247,6 +247,66 @@ def test_miss_path_with_provider_equals_resident(P, orc):
     assert vol.stats()["evicted"] > 0
 
 
+def test_render_into_page_locked_host_memory(P, orc):
+    """An image written straight into page-locked host memory (the kernel writes through the
+    host link) equals the image rendered into device memory, bit for bit: several views in one
+    launch, and a render whose rays wait for bricks over several passes."""
+    D, raw, _, tf, params = c1_inputs(seed=6)
+    params = dict(params, lod_mode=1)
+    cams = [synth.seeded_orbit(D, s, s, 6, view=i) for i, s in enumerate([64, 37, 96])]
+    npx = sum(c["w"] * c["h"] for c in cams)
+    full = gpu_volume(P, raw, "u8", "u8", 16, 2)
+    want = full.render(cams, tf_dev(tf), params).cpu().numpy()
+    host = torch.full((npx, 4), float("nan"), dtype=torch.float32).pin_memory()
+    got = full.render(cams, tf_dev(tf), params, out=host)
+    torch.cuda.synchronize()
+    assert got.data_ptr() == host.data_ptr()
+    np.testing.assert_array_equal(host.numpy(), want)
+    # the same through the miss path (a cache of half the bricks, bricks from a provider)
+    levels = store_levels(orc, raw, "u8", "u8", 2)
+    B = 16
+
+    def provider(level, b):
+        arr = levels[level]
+        Dz, Dy, Dx = arr.shape
+        zi = np.minimum(b[2] * B + np.arange(B + 1), Dz - 1)
+        yi = np.minimum(b[1] * B + np.arange(B + 1), Dy - 1)
+        xi = np.minimum(b[0] * B + np.arange(B + 1), Dx - 1)
+        return arr[np.ix_(zi, yi, xi)]
+
+    vol = P.Volume(D, "u8", B, 2, cache_bytes=300 * P.plan(D, "u8", B, 2).slot_bytes)
+    vol.set_provider(provider, "u8")
+    host.fill_(float("nan"))
+    vol.render(cams, tf_dev(tf), dict(params, max_passes=200), out=host)
+    torch.cuda.synchronize()
+    assert vol.stats()["passes"] > 1
+    np.testing.assert_array_equal(host.numpy(), want)
+
+
+def test_output_the_gpu_cannot_address_is_refused(P):
+    """Pageable host memory is neither the GPU's nor mapped for it: the binding refuses it, and
+    so does the library itself (checked before any launch) when called through the C ABI."""
+    import ctypes
+    from paper_2509_26213_gb300 import _capi as C
+    D, raw, cam, tf, params = c1_inputs(seed=6)
+    vol = gpu_volume(P, raw, "u8", "u8", 32, 1)
+    pageable = torch.empty((cam["w"] * cam["h"], 4), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        vol.render(cam, tf_dev(tf), params, out=pageable)
+    buf = np.empty((cam["w"] * cam["h"], 4), np.float32)
+    tfd = tf_dev(tf)
+    c = (C.vol_camera * 1)(P.camera_struct(cam))
+    prm = P.params_struct(**params)
+    rc = vol.lib.vol_render(vol.h, c, 1, ctypes.c_void_p(tfd.data_ptr()), ctypes.byref(prm),
+                            ctypes.c_void_p(buf.ctypes.data), None)
+    assert rc == C.VOL_ERR_INVALID_ARG
+    out = torch.empty((cam["w"] * cam["h"], 4), dtype=torch.float32, device="cuda")
+    rc = vol.lib.vol_render(vol.h, c, 1, ctypes.c_void_p(tfd.data_ptr()), ctypes.byref(prm),
+                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(buf.ctypes.data))
+    assert rc == C.VOL_ERR_INVALID_ARG
+    assert vol.render(cam, tfd, params, out=out).data_ptr() == out.data_ptr()
+
+
 def test_requests_without_provider_then_resume(P, orc):
     D, raw, cam, tf, params = c1_inputs(seed=6)
     levels = store_levels(orc, raw, "u8", "u8", 1)
