@@ -45,6 +45,13 @@ __device__ __forceinline__ void flush_vox(float* dvox, long long cell, int mask,
     for (int c = 0; c < 8; ++c) cacc[c] = 0.0f;
 }
 
+// Adds the 4 accumulators of one entry (acc[0..3], one per channel) to dL/dtf.
+__device__ __forceinline__ void flush_dtf4(float* s_dtf, int idx, const float* acc) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (acc[c] != 0.0f) atomicAdd(&s_dtf[c * 256 + idx], acc[c]);
+}
+
 // Samples per lane whose page-table lookups and gathers the adjoint's forward recompute issues
 // together.
 #ifndef VOLRC_BWD_BATCH
@@ -247,7 +254,25 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                 if (P.dtf) {
                     // register accumulation while the TF index stays the same
                     if (i != acc_i) {
-                        flush_dtf(s_dtf, acc_i, acc);
+                        // to a neighbouring index the entry both lookups share stays in registers:
+                        // only the one left behind is added to the table
+                        if (acc_i >= 0 && i == acc_i + 1) {
+                            flush_dtf4(s_dtf, acc_i, acc);
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                acc[c] = acc[4 + c];
+                                acc[4 + c] = 0.0f;
+                            }
+                        } else if (acc_i >= 0 && i == acc_i - 1) {
+                            flush_dtf4(s_dtf, acc_i + 1, acc + 4);
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                acc[4 + c] = acc[c];
+                                acc[c] = 0.0f;
+                            }
+                        } else {
+                            flush_dtf(s_dtf, acc_i, acc);
+                        }
                         acc_i = i;
                     }
                     const float w0 = 1.0f - wt;
