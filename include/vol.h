@@ -99,7 +99,7 @@ typedef struct {
  * skipping is not applied in this mode. */
 #define VOL_RENDER_LEVEL_STEP 16u
 /* With a provider, a ray that waits for a missing brick also requests the next bricks along it
- * (a look-ahead of four bricks), so that it does not wait a round for each when it resumes; the
+ * (a look-ahead of eight bricks), so that it does not wait a round for each when it resumes; the
  * extra bricks may go unused.  This flag turns the look-ahead off.  Images do not change. */
 #define VOL_RENDER_NO_PREFETCH 32u
 

@@ -17,7 +17,7 @@ constexpr double kMaxSamplesPerRay = 16777216.0 - 64.0;
 constexpr int kRenderThreads = 128; // threads per CTA of the render kernels
 constexpr int kMaxProbe = 64;       // bounded linear probing of the request table
 #ifndef VOLRC_PREFETCH_BRICKS
-#define VOLRC_PREFETCH_BRICKS 4
+#define VOLRC_PREFETCH_BRICKS 8
 #endif
 constexpr int kPrefetchBricks = VOLRC_PREFETCH_BRICKS;  // look-ahead of a waiting ray, in bricks
 
