@@ -42,13 +42,15 @@ def _time(vol, cams, tf, params, reps, warmup, flush):
 
 def autotune(make_volume, cams, tf, params: dict, key: str, bricks=(32, 64), tiles=DEFAULT_TILES,
              refills=DEFAULT_REFILL, reps: int = 5, warmup: int = 2, cache_path: str | None = None,
-             flush_bytes: int = 256 << 20) -> dict:
+             flush_bytes: int = 256 << 20, timer=None, device_name: str | None = None) -> dict:
     """Returns {"brick", "tile_w", "tile_h", "refill", "ms", "timings", "cached"}.
 
     make_volume(brick) -> Volume (resident, ready to render); the tuner closes each volume
     it does not return, and returns the winner's volume under "volume" unless it came from the
-    cache (then the caller builds it)."""
-    cache_key = f"{_gpu_name()}|{key}"
+    cache (then the caller builds it).  timer(vol, cams, tf, params) -> ms replaces the timing
+    of renders with CUDA events, and device_name the GPU's name in the cache key (both for
+    tests of the selection and the cache without a GPU)."""
+    cache_key = f"{device_name or _gpu_name()}|{key}"
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
@@ -57,7 +59,11 @@ def autotune(make_volume, cams, tf, params: dict, key: str, bricks=(32, 64), til
             out = dict(cache[cache_key])
             out["cached"] = True
             return out
-    flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda") if flush_bytes else None
+    if timer is None:
+        flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda") if flush_bytes else None
+
+        def timer(vol, cams, tf, prm):
+            return _time(vol, cams, tf, prm, reps, warmup, flush)
     timings = {}
     best = None
     best_vol = None
@@ -67,7 +73,7 @@ def autotune(make_volume, cams, tf, params: dict, key: str, bricks=(32, 64), til
         for tw, th in tiles:
             for refill in refills:
                 prm = dict(params, tile_w=tw, tile_h=th, refill=refill)
-                ms = _time(vol, cams, tf, prm, reps, warmup, flush)
+                ms = timer(vol, cams, tf, prm)
                 timings[f"b{brick} t{tw}x{th} r{refill}"] = ms
                 if local_best is None or ms < local_best[0]:
                     local_best = (ms, tw, th, refill)
@@ -79,7 +85,8 @@ def autotune(make_volume, cams, tf, params: dict, key: str, bricks=(32, 64), til
             best_vol = vol
         else:
             vol.close()
-        torch.cuda.empty_cache()
+        if torch.cuda.is_available():
+            torch.cuda.empty_cache()
     best["timings"] = timings
     if cache_path:
         cache[cache_key] = {k: v for k, v in best.items()}
