@@ -1,0 +1,105 @@
+"""Properties of the oracle's renders that hold for any input, on seeded random small volumes,
+cameras and transfer functions (Sec. IV-A front-to-back emission/absorption; Sec. V-C LOD).
+
+* The background enters linearly: out = C + T bg per channel, with T = 1 - (alpha - bg_a T)
+  read back from the alpha channel, for two backgrounds and the same samples.
+* Raising every TF opacity never lowers the output alpha (more absorption, never less); without
+  early termination it also never shortens a ray.
+* With one level, footprint LOD selects level 0 everywhere: the image equals lod_mode 0, and any
+  bias gives the same.
+* A render of a subset of pixels equals the same pixels of the full render.
+* Exchanging the TF's colour channels permutes the output's colour channels.
+A mistake in the compositing order, a sign, a transposed channel or a level choice breaks one of
+them.  (hypothesis is not installed on every machine: the tests are skipped there.)"""
+import numpy as np
+import pytest
+
+import synth
+
+hyp = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st  # noqa: E402
+
+SETTINGS = dict(max_examples=12, deadline=None, derandomize=True)
+
+
+def case(seed, dtype="u8"):
+    rng = np.random.default_rng(seed)
+    D = tuple(int(x) for x in rng.integers(9, 24, 3))
+    raw = synth.blobs(D, seed, dtype=dtype, nblobs=3, sigma=(2, 6), amp=(0.3, 1.0), noise=0.05, vmax=0.95) \
+        if dtype == "f32" else rng.integers(0, 256, D[::-1], dtype=np.uint8)
+    tf = rng.random((256, 4)).astype(np.float32)
+    tf[:, 3] *= np.float32(rng.uniform(0.02, 0.3))
+    cam = synth.seeded_orbit(D, int(rng.integers(3, 9)), int(rng.integers(3, 9)), seed)
+    return D, raw, tf, cam
+
+
+def volume(orc, raw, dtype, levels=1, brick=8):
+    lv = orc.pyramid(raw, levels, dtype) if levels > 1 else [raw]
+    return orc.Volume(lv, dtype, brick)
+
+
+@settings(**SETTINGS)
+@given(st.integers(0, 10 ** 6))
+def test_background_enters_linearly(orc, seed):
+    D, raw, tf, cam = case(seed)
+    vol = volume(orc, raw, "u8")
+    bg1, bg2 = (0.0, 0.0, 0.0, 0.0), (0.5, 0.25, 1.0, 0.75)
+    o1 = orc.render(vol, cam, tf, {"bg": bg1, "et": 2.0})
+    o2 = orc.render(vol, cam, tf, {"bg": bg2, "et": 2.0})
+    np.testing.assert_array_equal(o1["n"], o2["n"])
+    T = 1.0 - o1["rgba"][:, 3]                      # bg alpha 0: alpha = 1 - T
+    b = np.float64(np.float32(bg2))
+    np.testing.assert_allclose(o2["rgba"][:, :3], o1["rgba"][:, :3] + T[:, None] * b[:3], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(o2["rgba"][:, 3], (1.0 - T) + T * b[3], rtol=0, atol=1e-12)
+    assert np.all((T >= 0) & (T <= 1))
+
+
+@settings(**SETTINGS)
+@given(st.integers(0, 10 ** 6), st.floats(1.0, 3.0))
+def test_more_opacity_never_less_alpha(orc, seed, gain):
+    D, raw, tf, cam = case(seed)
+    vol = volume(orc, raw, "u8")
+    hi = tf.copy()
+    hi[:, 3] = np.minimum(tf[:, 3] * np.float32(gain), 1).astype(np.float32)
+    a = orc.render(vol, cam, tf, {"et": 2.0})
+    b = orc.render(vol, cam, hi, {"et": 2.0})
+    assert np.all(b["rgba"][:, 3] >= a["rgba"][:, 3] - 1e-12)
+    np.testing.assert_array_equal(a["n"], b["n"])   # no early termination: every ray to its exit
+
+
+@settings(**SETTINGS)
+@given(st.integers(0, 10 ** 6), st.integers(-3, 3))
+def test_single_level_lod_is_level_zero(orc, seed, bias):
+    D, raw, tf, cam = case(seed, "f32")
+    vol = volume(orc, raw, "f32")
+    plain = orc.render(vol, cam, tf, {"lod_mode": 0})
+    lod = orc.render(vol, cam, tf, {"lod_mode": 1, "lod_bias": bias})
+    np.testing.assert_array_equal(lod["rgba"], plain["rgba"])
+    np.testing.assert_array_equal(lod["n"], plain["n"])
+
+
+@settings(**SETTINGS)
+@given(st.integers(0, 10 ** 6))
+def test_pixel_subset_equals_full_frame(orc, seed):
+    D, raw, tf, cam = case(seed)
+    vol = volume(orc, raw, "u8", levels=2)
+    params = {"lod_mode": 1, "bg": (0.1, 0.2, 0.3, 0.4)}
+    full = orc.render(vol, cam, tf, params)
+    pix = synth.pixel_subset(cam["w"], cam["h"], max(1, cam["w"] * cam["h"] // 3), seed)
+    sub = orc.render(vol, cam, tf, params, pixels=pix)
+    idx = pix[:, 1].astype(np.int64) * cam["w"] + pix[:, 0]
+    np.testing.assert_array_equal(sub["rgba"], full["rgba"][idx])
+    np.testing.assert_array_equal(sub["n"], full["n"][idx])
+
+
+@settings(**SETTINGS)
+@given(st.integers(0, 10 ** 6), st.permutations([0, 1, 2]))
+def test_colour_channels_permute(orc, seed, perm):
+    D, raw, tf, cam = case(seed)
+    vol = volume(orc, raw, "u8")
+    tfp = tf.copy()
+    tfp[:, :3] = tf[:, perm]
+    a = orc.render(vol, cam, tf, {})
+    b = orc.render(vol, cam, tfp, {})
+    np.testing.assert_array_equal(b["rgba"][:, :3], a["rgba"][:, perm])
+    np.testing.assert_array_equal(b["rgba"][:, 3], a["rgba"][:, 3])
