@@ -9,6 +9,8 @@ cameras and transfer functions (Sec. IV-A front-to-back emission/absorption; Sec
   bias gives the same.
 * A render of a subset of pixels equals the same pixels of the full render.
 * Exchanging the TF's colour channels permutes the output's colour channels.
+* With TF opacity increasing in the coordinate, MOP and MIP give the same image (Sec. V-A).
+* Level-scaled sampling with every sample on level 0 is the plain render.
 A mistake in the compositing order, a sign, a transposed channel or a level choice breaks one of
 them.  (hypothesis is not installed on every machine: the tests are skipped there.)"""
 import numpy as np
@@ -103,3 +105,32 @@ def test_colour_channels_permute(orc, seed, perm):
     b = orc.render(vol, cam, tfp, {})
     np.testing.assert_array_equal(b["rgba"][:, :3], a["rgba"][:, perm])
     np.testing.assert_array_equal(b["rgba"][:, 3], a["rgba"][:, 3])
+
+
+@settings(**SETTINGS)
+@given(st.integers(0, 10 ** 6))
+def test_increasing_opacity_makes_mop_and_mip_agree(orc, seed):
+    """With TF opacity strictly increasing in the coordinate, the most opaque sample is the one
+    of largest coordinate: maximum-opacity and maximum-intensity projection give the same image
+    (Sec. V-A; the two keep their state in different forms)."""
+    D, raw, tf, cam = case(seed)
+    tf[:, 3] = np.linspace(0.01, 0.6, 256, dtype=np.float32)
+    vol = volume(orc, raw, "u8", levels=2)
+    params = {"lod_mode": 1, "bg": (0.2, 0.1, 0.4, 0.3)}
+    mop = orc.render_max(vol, cam, tf, params, "mop")
+    mip = orc.render_max(vol, cam, tf, params, "mip")
+    np.testing.assert_allclose(mop["rgba"], mip["rgba"], rtol=0, atol=1e-12)
+
+
+@settings(**SETTINGS)
+@given(st.integers(0, 10 ** 6))
+def test_level_step_on_level_zero_is_the_plain_render(orc, seed):
+    """Level-scaled sampling changes nothing where every sample is on level 0 (step 2^0 dt,
+    opacity to the power 2^0)."""
+    D, raw, tf, cam = case(seed, "f32")
+    vol = volume(orc, raw, "f32", levels=2)
+    for params in ({"lod_mode": 0}, {"lod_mode": 1, "lod_bias": -30}):
+        plain = orc.render(vol, cam, tf, params)
+        ls = orc.render(vol, cam, tf, dict(params, flags=16))
+        np.testing.assert_array_equal(ls["rgba"], plain["rgba"])
+        np.testing.assert_array_equal(ls["n"], plain["n"])
