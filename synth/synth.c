@@ -127,11 +127,19 @@ int synth_blobs(int dtype, const int64_t D[3], uint64_t seed, int nblobs,
 
 static inline double smooth01(double f) { return f * f * (3.0 - 2.0 * f); }
 
-static inline double lattice(uint64_t seed, int oct, int64_t ix, int64_t iy, int64_t iz)
+/* The value at lattice point (ix, iy, iz) of octave oct is draw01(seed, ST_LATTICE + 16 oct,
+ * key(ix, iy, iz)).  draw01 hashes the (seed, stream) pair first; that hash is taken once per
+ * octave (lattice_stream) and the point's draw finished from it (lattice_h). */
+static inline uint64_t lattice_stream(uint64_t seed, int oct)
+{
+    return splitmix64(seed ^ ((ST_LATTICE + 16 * (uint64_t)oct) * 0xD1B54A32D192ED03ull));
+}
+
+static inline double lattice_h(uint64_t h_oct, int64_t ix, int64_t iy, int64_t iz)
 {
     uint64_t key = ((uint64_t)(ix & 0x1FFFFF)) | ((uint64_t)(iy & 0x1FFFFF) << 21) |
                    ((uint64_t)(iz & 0x1FFFFF) << 42);
-    return draw01(seed, ST_LATTICE + 16 * (uint64_t)oct, key);
+    return (double)(splitmix64(h_oct + key) >> 11) * 0x1.0p-53;
 }
 
 typedef struct {
@@ -255,6 +263,32 @@ static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], cons
             pos[a][i] = ((double)gi + 0.5) * sp[a];
         }
     }
+    /* the spheres that can reach the region: the box of its voxel centres against each sphere's
+     * bounding box, widened far beyond rounding so that no sphere the exact tests below could
+     * accept is dropped (kept in their order: later spheres win) */
+    int *near = malloc(sizeof(int) * (nspheres ? nspheres : 1));
+    int nnear = 0;
+    for (int s = 0; s < nspheres; ++s) {
+        int in = 1;
+        for (int a = 0; a < 3 && in; ++a) {
+            const double rw = sph[s].r * (1.0 + 1e-9) + 1e-9;
+            in = sph[s].c[a] + rw >= pos[a][0] && sph[s].c[a] - rw <= pos[a][extent[a] - 1];
+        }
+        if (in) near[nnear++] = s;
+    }
+    /* per octave and x: the lattice cell and the blend weight along x (they do not depend on y
+     * or z, so every row of the region reuses them) */
+    int64_t *cellx = malloc(sizeof(int64_t) * (size_t)octaves * (size_t)Ex);
+    double *wxt = malloc(sizeof(double) * (size_t)octaves * (size_t)Ex);
+    for (int o = 0; o < octaves; ++o) {
+        const double P = period0 / (double)(1 << o);
+        for (int64_t x = 0; x < Ex; ++x) {
+            const double fx0 = pos[0][x] / P;
+            const int64_t ix = (int64_t)floor(fx0);
+            cellx[(size_t)o * Ex + x] = ix;
+            wxt[(size_t)o * Ex + x] = smooth01(fx0 - (double)ix);
+        }
+    }
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -264,8 +298,10 @@ static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], cons
         int *cand = malloc(sizeof(int) * (nspheres ? nspheres : 1));
         const double pz = pos[2][z];
         int ncand = 0;
-        for (int s = 0; s < nspheres; ++s)
+        for (int q = 0; q < nnear; ++q) {
+            const int s = near[q];
             if (fabs(pz - sph[s].c[2]) <= sph[s].r) cand[ncand++] = s;
+        }
         for (int64_t y = 0; y < Ey; ++y) {
             const double py = pos[1][y];
             for (int64_t x = 0; x < Ex; ++x) acc[x] = 0.0;
@@ -281,16 +317,22 @@ static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], cons
                 const double wy = smooth01(fy0 - (double)iy), wz = smooth01(fz0 - (double)iz);
                 int64_t cur = INT64_MIN;
                 double e0 = 0, e1 = 0;
+                const int64_t *cx = cellx + (size_t)o * Ex;
+                const double *wxo = wxt + (size_t)o * Ex;
+                const uint64_t h_oct = lattice_stream(seed, o);
                 for (int64_t x = 0; x < Ex; ++x) {
-                    const double fx0 = pos[0][x] / P;
-                    const int64_t ix = (int64_t)floor(fx0);
+                    const int64_t ix = cx[x];
                     if (ix != cur) {
+                        /* the blend along y and z at lattice columns ix and ix + 1; the next
+                         * cell's left column is this cell's right one */
                         double e[2];
-                        for (int k = 0; k < 2; ++k) {
-                            double l00 = lattice(seed, o, ix + k, iy, iz);
-                            double l10 = lattice(seed, o, ix + k, iy + 1, iz);
-                            double l01 = lattice(seed, o, ix + k, iy, iz + 1);
-                            double l11 = lattice(seed, o, ix + k, iy + 1, iz + 1);
+                        const int k0 = (cur != INT64_MIN && ix == cur + 1) ? 1 : 0;
+                        if (k0) e[0] = e1;
+                        for (int k = k0; k < 2; ++k) {
+                            double l00 = lattice_h(h_oct, ix + k, iy, iz);
+                            double l10 = lattice_h(h_oct, ix + k, iy + 1, iz);
+                            double l01 = lattice_h(h_oct, ix + k, iy, iz + 1);
+                            double l11 = lattice_h(h_oct, ix + k, iy + 1, iz + 1);
                             double a0 = l00 + wy * (l10 - l00);
                             double a1 = l01 + wy * (l11 - l01);
                             e[k] = a0 + wz * (a1 - a0);
@@ -299,7 +341,7 @@ static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], cons
                         e1 = e[1];
                         cur = ix;
                     }
-                    const double wx = smooth01(fx0 - (double)ix);
+                    const double wx = wxo[x];
                     acc[x] += gw * (e0 + wx * (e1 - e0));
                 }
             }
@@ -336,6 +378,9 @@ static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], cons
         free(acc);
     }
     for (int a = 0; a < 3; ++a) free(pos[a]);
+    free(cellx);
+    free(wxt);
+    free(near);
     free(sph);
     return 0;
 }
