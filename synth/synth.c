@@ -280,6 +280,7 @@ static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], cons
      * or z, so every row of the region reuses them) */
     int64_t *cellx = malloc(sizeof(int64_t) * (size_t)octaves * (size_t)Ex);
     double *wxt = malloc(sizeof(double) * (size_t)octaves * (size_t)Ex);
+    int64_t ncolmax = 2;
     for (int o = 0; o < octaves; ++o) {
         const double P = period0 / (double)(1 << o);
         for (int64_t x = 0; x < Ex; ++x) {
@@ -288,6 +289,8 @@ static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], cons
             cellx[(size_t)o * Ex + x] = ix;
             wxt[(size_t)o * Ex + x] = smooth01(fx0 - (double)ix);
         }
+        const int64_t nc = cellx[(size_t)o * Ex + Ex - 1] - cellx[(size_t)o * Ex] + 2;
+        if (nc > ncolmax) ncolmax = nc;
     }
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -295,6 +298,13 @@ static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], cons
 #endif
     for (int64_t z = 0; z < Ez; ++z) {
         double *acc = malloc(sizeof(double) * Ex);
+        /* per octave: the lattice values at the region's columns ix0 .. ix1 + 1 for the current
+         * cell row (iy, iz) -- l00, l10, l01, l11 -- refilled when iy changes, and their blend
+         * along y and z for the current row */
+        double *lat = malloc(sizeof(double) * 4 * (size_t)octaves * (size_t)ncolmax);
+        double *ecol = malloc(sizeof(double) * (size_t)ncolmax);
+        int64_t lat_iy[16];
+        for (int o = 0; o < octaves; ++o) lat_iy[o] = INT64_MIN;
         int *cand = malloc(sizeof(int) * (nspheres ? nspheres : 1));
         const double pz = pos[2][z];
         int ncand = 0;
@@ -315,34 +325,30 @@ static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], cons
                 const double fy0 = py / P, fz0 = pz / P;
                 const int64_t iy = (int64_t)floor(fy0), iz = (int64_t)floor(fz0);
                 const double wy = smooth01(fy0 - (double)iy), wz = smooth01(fz0 - (double)iz);
-                int64_t cur = INT64_MIN;
-                double e0 = 0, e1 = 0;
                 const int64_t *cx = cellx + (size_t)o * Ex;
                 const double *wxo = wxt + (size_t)o * Ex;
-                const uint64_t h_oct = lattice_stream(seed, o);
-                for (int64_t x = 0; x < Ex; ++x) {
-                    const int64_t ix = cx[x];
-                    if (ix != cur) {
-                        /* the blend along y and z at lattice columns ix and ix + 1; the next
-                         * cell's left column is this cell's right one */
-                        double e[2];
-                        const int k0 = (cur != INT64_MIN && ix == cur + 1) ? 1 : 0;
-                        if (k0) e[0] = e1;
-                        for (int k = k0; k < 2; ++k) {
-                            double l00 = lattice_h(h_oct, ix + k, iy, iz);
-                            double l10 = lattice_h(h_oct, ix + k, iy + 1, iz);
-                            double l01 = lattice_h(h_oct, ix + k, iy, iz + 1);
-                            double l11 = lattice_h(h_oct, ix + k, iy + 1, iz + 1);
-                            double a0 = l00 + wy * (l10 - l00);
-                            double a1 = l01 + wy * (l11 - l01);
-                            e[k] = a0 + wz * (a1 - a0);
-                        }
-                        e0 = e[0];
-                        e1 = e[1];
-                        cur = ix;
+                const int64_t ix0 = cx[0], ncol = cx[Ex - 1] - ix0 + 2;  /* cellx rises with x */
+                double *L = lat + 4 * (size_t)o * (size_t)ncolmax;
+                if (iy != lat_iy[o]) {
+                    const uint64_t h_oct = lattice_stream(seed, o);
+                    for (int64_t c = 0; c < ncol; ++c) {
+                        L[4 * c + 0] = lattice_h(h_oct, ix0 + c, iy, iz);
+                        L[4 * c + 1] = lattice_h(h_oct, ix0 + c, iy + 1, iz);
+                        L[4 * c + 2] = lattice_h(h_oct, ix0 + c, iy, iz + 1);
+                        L[4 * c + 3] = lattice_h(h_oct, ix0 + c, iy + 1, iz + 1);
                     }
-                    const double wx = wxo[x];
-                    acc[x] += gw * (e0 + wx * (e1 - e0));
+                    lat_iy[o] = iy;
+                }
+                for (int64_t c = 0; c < ncol; ++c) {
+                    const double l00 = L[4 * c + 0], l10 = L[4 * c + 1], l01 = L[4 * c + 2], l11 = L[4 * c + 3];
+                    const double a0 = l00 + wy * (l10 - l00);
+                    const double a1 = l01 + wy * (l11 - l01);
+                    ecol[c] = a0 + wz * (a1 - a0);
+                }
+                for (int64_t x = 0; x < Ex; ++x) {
+                    const int64_t c = cx[x] - ix0;
+                    const double e0 = ecol[c], e1 = ecol[c + 1];
+                    acc[x] += gw * (e0 + wxo[x] * (e1 - e0));
                 }
             }
             for (int64_t x = 0; x < Ex; ++x) acc[x] /= gsum;
@@ -375,6 +381,8 @@ static int region_impl(const int64_t D0[3], int level, const int64_t Dl[3], cons
             }
         }
         free(cand);
+        free(ecol);
+        free(lat);
         free(acc);
     }
     for (int a = 0; a < 3; ++a) free(pos[a]);
