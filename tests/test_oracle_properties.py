@@ -11,6 +11,7 @@ cameras and transfer functions (Sec. IV-A front-to-back emission/absorption; Sec
 * Exchanging the TF's colour channels permutes the output's colour channels.
 * With TF opacity increasing in the coordinate, MOP and MIP give the same image (Sec. V-A).
 * Level-scaled sampling with every sample on level 0 is the plain render.
+* The adjoint is linear in dL/dI; dL/dtf is zero on TF entries no lookup reads.
 A mistake in the compositing order, a sign, a transposed channel or a level choice breaks one of
 them.  (hypothesis is not installed on every machine: the tests are skipped there.)"""
 import numpy as np
@@ -134,3 +135,42 @@ def test_level_step_on_level_zero_is_the_plain_render(orc, seed):
         ls = orc.render(vol, cam, tf, dict(params, flags=16))
         np.testing.assert_array_equal(ls["rgba"], plain["rgba"])
         np.testing.assert_array_equal(ls["n"], plain["n"])
+
+
+@settings(**SETTINGS)
+@given(st.integers(0, 10 ** 6), st.floats(-2.0, 2.0), st.floats(-2.0, 2.0))
+def test_adjoint_is_linear_in_the_upstream_gradient(orc, seed, a, b):
+    """The adjoint (gradients with respect to the TF and the voxels) is linear in dL/dI, and a
+    zero dL/dI gives zero gradients."""
+    D, raw, tf, cam = case(seed, "f32")
+    vol = volume(orc, raw, "f32")
+    n = cam["w"] * cam["h"]
+    rng = np.random.default_rng(seed + 1)
+    d1, d2 = rng.standard_normal((n, 4)), rng.standard_normal((n, 4))
+    g1 = orc.render_grad(vol, cam, tf, {}, d1)
+    g2 = orc.render_grad(vol, cam, tf, {}, d2)
+    g = orc.render_grad(vol, cam, tf, {}, a * d1 + b * d2)
+    for k in range(2):
+        want = a * g1[k] + b * g2[k]
+        scale = max(np.abs(g1[k]).max(), np.abs(g2[k]).max(), 1e-300)
+        np.testing.assert_allclose(g[k], want, rtol=0, atol=1e-11 * scale * (1 + abs(a) + abs(b)))
+    z = orc.render_grad(vol, cam, tf, {}, np.zeros((n, 4)))
+    assert not z[0].any() and not z[1].any()
+
+
+@settings(**SETTINGS)
+@given(st.integers(0, 10 ** 6), st.integers(40, 120), st.integers(10, 60))
+def test_tf_gradient_only_on_entries_the_samples_touch(orc, seed, lo, width):
+    """A u8 volume with values in [lo, lo + width]: every TF lookup uses entries lo .. lo + width
+    (the interpolation between entry i and i + 1 at coordinate i exactly reads entry i + 1 with
+    weight 0), so dL/dtf is zero outside lo .. lo + width + 1."""
+    D, _, tf, cam = case(seed)
+    rng = np.random.default_rng(seed + 2)
+    raw = rng.integers(lo, lo + width + 1, D[::-1], dtype=np.uint8)
+    vol = volume(orc, raw, "u8")
+    dI = rng.standard_normal((cam["w"] * cam["h"], 4))
+    dtf, _ = orc.render_grad(vol, cam, tf, {}, dI)
+    outside = np.ones(256, bool)
+    outside[lo:lo + width + 2] = False
+    assert not dtf[outside].any()
+    assert dtf[~outside].any()
