@@ -69,18 +69,37 @@ def test_plan_rejects(lib, bad):
     assert rc == lib.VOL_ERR_INVALID_ARG
 
 
+def zettabyte_figures():
+    """The figures Sec. V-C prints for its virtual volume (tests/golden/zettabyte_volume.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "zettabyte_volume.txt")
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                out[k] = float(v)
+    return out
+
+
 def test_plan_sparse_page_table(lib):
     """The paper's virtual 2 ZB volume (8,000,000^3 voxels, 128^3 bricks): too many bricks for a
     flat table, a few hundred MB of top grids for the sparse one."""
     from paper_2509_26213_gb300.volume import plan
-    D = (8_000_000,) * 3
+    z = zettabyte_figures()
+    n, B = int(z["voxels_per_axis"]), int(z["brick_edge"])
+    # the printed size: 8,000,000^3 voxels at 4 bytes is 2 ZB, and its 62,500^3 bricks fit the
+    # printed three-level tree of 2^16-entry pages (2^48 leaves) -- "the upper limit"
+    assert abs(n ** 3 * z["bytes_per_voxel"] / z["total_bytes_order"] - 1) < 0.03
+    assert (n // B) ** 3 <= int(z["page_table_entries_per_page"]) ** int(z["page_table_levels"]) < 2 * (n // B) ** 3
+    D = (n,) * 3
     with pytest.raises(RuntimeError):
-        plan(D, "f32", 128, 8, cache_bytes=16 << 30)
+        plan(D, "f32", B, 8, cache_bytes=16 << 30)
     with pytest.raises(RuntimeError):  # a sparse table needs a cache budget
-        plan(D, "f32", 128, 8, sparse_pt=True)
-    lay = plan(D, "f32", 128, 8, cache_bytes=16 << 30, sparse_pt=True)
+        plan(D, "f32", B, 8, sparse_pt=True)
+    lay = plan(D, "f32", B, 8, cache_bytes=16 << 30, sparse_pt=True)
     assert lay.sparse_pt == 1
-    assert lay.level_bricks[0][0] == 62500 and lay.total_bricks > 2 ** 47
+    assert lay.level_bricks[0][0] == n // B == 62500 and lay.total_bricks > 2 ** 47
     tops = [(-(-lay.level_bricks[l][0] // 256)) ** 3 for l in range(8)]
     assert list(lay.level_pt_offset[:8]) == [sum(tops[:l]) for l in range(8)]
     assert lay.pt_top_entries == sum(tops) and lay.pt_top_entries * 4 < (1 << 30)
