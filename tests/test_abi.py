@@ -106,6 +106,25 @@ def test_plan_sparse_page_table(lib):
     assert lay.nslots == (16 << 30) // lay.slot_bytes
 
 
+def test_plan_the_benchmark_volumes(lib):
+    """The printed sizes of the Table I volumes follow from their printed dimensions and types,
+    and both plan as out-of-core volumes of 64^3 bricks with a 16 GiB cache (flat page tables)."""
+    import os
+    from paper_2509_26213_gb300.volume import plan
+    path = os.path.join(os.path.dirname(__file__), "golden", "benchmark_volumes.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 2
+    bpv = {"u16": 2, "f32": 4}
+    for name, x, y, z, dtype, gb, mode in rows:
+        D = (int(x), int(y), int(z))
+        size = D[0] * D[1] * D[2] * bpv[dtype]
+        assert abs(size / 1e9 - float(gb)) < 1.0, (name, size)
+        lay = plan(D, dtype, 64, 8, cache_bytes=16 << 30)
+        assert tuple(lay.level_bricks[0][a] for a in range(3)) == tuple(-(-d // 64) for d in D)
+        assert lay.nslots == (16 << 30) // lay.slot_bytes and lay.sparse_pt == 0
+        assert mode in ("dvr", "mop")
+
+
 def test_missing_library_fails_loudly(lib, monkeypatch, tmp_path):
     import importlib
     from paper_2509_26213_gb300 import _capi
