@@ -90,6 +90,7 @@ def _load():
             lib.orc_float_to_half.restype = ctypes.c_uint16
             lib.orc_u16_to_f16.argtypes = [ctypes.c_int64, vp, vp]
             lib.orc_u8_to_f32.argtypes = [ctypes.c_int64, vp, vp]
+            lib.orc_u16_to_f32.argtypes = [ctypes.c_int64, vp, vp]
             lib.orc_downsample.argtypes = [ctypes.c_int, i64p, vp, vp]
             lib.orc_downsample.restype = ctypes.c_int
             lib.orc_trace.argtypes = [ctypes.POINTER(_Volume), ctypes.POINTER(_Camera),
@@ -175,9 +176,18 @@ def u16_to_f16(a: np.ndarray) -> np.ndarray:
 
 
 def u8_to_f32(a: np.ndarray) -> np.ndarray:
+    """Float32 storage of a uint8 volume: u / 255 rounded once to binary32."""
     a = np.ascontiguousarray(a, dtype=np.uint8)
     out = np.empty(a.shape, dtype=np.float32)
     _load().orc_u8_to_f32(a.size, a.ctypes.data, out.ctypes.data)
+    return out
+
+
+def u16_to_f32(a: np.ndarray) -> np.ndarray:
+    """Float32 storage of a uint16 volume: u / 65535 rounded once to binary32."""
+    a = np.ascontiguousarray(a, dtype=np.uint16)
+    out = np.empty(a.shape, dtype=np.float32)
+    _load().orc_u16_to_f32(a.size, a.ctypes.data, out.ctypes.data)
     return out
 
 
@@ -314,7 +324,7 @@ def render_preview(vol: Volume, cam: dict, tf: np.ndarray, params: dict, residen
                    amb=1e-5, nthreads=0) -> dict:
     """``render`` under a residency map (uint8 per page-table index, levels end to end, brick id
     x fastest): a sample whose brick is absent uses the finest coarser resident level, or
-    composites nothing (progressive preview, Sec. IV-B)."""
+    composites nothing (progressive preview, Sec. III-H)."""
     tf = np.ascontiguousarray(tf, dtype=np.float32)
     resident = np.ascontiguousarray(resident, dtype=np.uint8)
     assert resident.shape == (page_table_size(vol),)

@@ -16,7 +16,7 @@
  *   - maximum-opacity projection (MOP), and maximum-intensity projection
  *     beside it                                                 (Sec. V-A; Table I)
  *   - progressive preview: absent bricks replaced by coarser
- *     resident levels                                           (Sec. IV-B)
+ *     resident levels                                           (Sec. III-H)
  * The paper gives no formulas for ray setup, interpolation, LOD choice or
  * compositing; the readings used here are listed in the design notes and in
  * the comments of each function.
@@ -143,10 +143,17 @@ void orc_u16_to_f16(int64_t n, const uint16_t *src, uint16_t *dst)
     free(tab);
 }
 
-/* u8 -> float32 normalised value (u / 255 as one float division). */
+/* u8 -> float32 normalised value (the normalisation u / 255 of the storage
+ * convention, rounded once to binary32: one correctly rounded float division). */
 void orc_u8_to_f32(int64_t n, const uint8_t *src, float *dst)
 {
     for (int64_t i = 0; i < n; ++i) dst[i] = (float)src[i] / 255.0f;
+}
+
+/* u16 -> float32 normalised value (u / 65535, rounded once to binary32). */
+void orc_u16_to_f32(int64_t n, const uint16_t *src, float *dst)
+{
+    for (int64_t i = 0; i < n; ++i) dst[i] = (float)src[i] / 65535.0f;
 }
 
 /* ------------------------------------------------------ downsample */
@@ -510,7 +517,7 @@ static int64_t pt_index(const orc_volume *V, int level, int64_t brick_id)
 }
 
 /*
- * Progressive preview (Sec. IV-B, Rendering: a low-resolution image from coarser LOD levels
+ * Progressive preview (Sec. III-H, Rendering: a low-resolution image from coarser LOD levels
  * first, refined as bricks arrive).  Reading: with a residency map (one byte per page-table
  * index), a sample whose brick on its level l is not resident is taken on the finest coarser
  * level l' > l whose brick at the same position is resident; when none is, the sample

@@ -22,7 +22,7 @@ def store_levels(orc, raw0: np.ndarray, src_dtype: str, store_dtype: str, nlevel
     elif (src_dtype, store_dtype) == ("u8", "f32"):
         l0 = orc.u8_to_f32(raw0)
     elif (src_dtype, store_dtype) == ("u16", "f32"):
-        l0 = (raw0.astype(np.float32) / np.float32(65535.0)).astype(np.float32)
+        l0 = orc.u16_to_f32(raw0)
     else:
         raise ValueError((src_dtype, store_dtype))
     return orc.pyramid(l0, nlevels, store_dtype)

@@ -108,3 +108,66 @@ def test_downsample_constant_and_conservation(orc, dtype):
         rng = np.random.default_rng(3)
         b = (rng.integers(0, 64, shape) / 64.0).astype(np.float32)
         assert orc.downsample(b, "f32").sum(dtype=np.float64) * 8 == pytest.approx(b.sum(dtype=np.float64), abs=0)
+
+
+def _nearest_binary32(q):
+    """The binary32 value nearest to the exact rational q >= 0 (ties to an even significand),
+    found by exact rational arithmetic: no float division or conversion rounds anything here."""
+    from fractions import Fraction
+    if q == 0:
+        return np.float32(0.0)
+    e = q.numerator.bit_length() - q.denominator.bit_length()
+    if Fraction(2) ** e > q:
+        e -= 1
+    assert Fraction(2) ** e <= q < Fraction(2) ** (e + 1) and e >= -126  # a normal number
+    quantum = Fraction(2) ** (e - 23)
+    m = q // quantum
+    below, above = q - m * quantum, (m + 1) * quantum - q
+    if above < below or (above == below and m % 2 == 1):
+        m += 1
+    value = m * quantum  # at most 24 significant bits: exact in float64 and in binary32
+    out = np.float32(float(value))
+    assert Fraction(float(out)) == value
+    return out
+
+
+def test_nearest_binary32_helper_by_hand():
+    from fractions import Fraction
+    assert _nearest_binary32(Fraction(1, 2)) == np.float32(0.5)
+    # 1/3 = 0.0101...b: binary32 0x3eaaaaab (rounded up: the dropped bits are 1010... > half)
+    assert _nearest_binary32(Fraction(1, 3)).view(np.uint32) == 0x3EAAAAAB
+    # 1 + 2^-24 lies exactly halfway between 1 and 1 + 2^-23: ties to the even significand (1)
+    assert _nearest_binary32(1 + Fraction(1, 2 ** 24)) == np.float32(1.0)
+    assert _nearest_binary32(1 + Fraction(3, 2 ** 24)).view(np.uint32) == 0x3F800002
+
+
+def test_u8_to_f32_every_code_is_u_over_255_rounded_once(orc):
+    """orc_u8_to_f32 (the normalisation u / 255): all 256 codes against the correctly rounded
+    binary32 of the exact quotient."""
+    from fractions import Fraction
+    u = np.arange(256, dtype=np.uint8)
+    want = np.array([_nearest_binary32(Fraction(int(c), 255)) for c in u], dtype=np.float32)
+    got = orc.u8_to_f32(u)
+    np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
+    assert got[255] == 1.0 and got[0] == 0.0
+    # a quotient by 256, or a double rounding through a coarser type, would not match
+    assert not np.array_equal(got, (u / 256.0).astype(np.float32))
+
+
+def test_u16_to_f32_every_code_is_u_over_65535_rounded_once(orc):
+    """orc_u16_to_f32 (the normalisation u / 65535): all 65536 codes against the correctly
+    rounded binary32 of the exact quotient."""
+    from fractions import Fraction
+    u = np.arange(65536, dtype=np.uint16)
+    want = np.array([_nearest_binary32(Fraction(int(c), 65535)) for c in u], dtype=np.float32)
+    got = orc.u16_to_f32(u)
+    np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
+    assert got[65535] == 1.0 and got[0] == 0.0 and got[32768] > 0.5 > got[32767]
+
+
+def test_u16_to_f16_is_binary16_of_the_pinned_quotient(orc):
+    """The reduced-precision store: binary16 (nearest, ties to even) of the pinned binary32
+    quotient, every code."""
+    u = np.arange(65536, dtype=np.uint16)
+    want = orc.u16_to_f32(u).astype(np.float16).view(np.uint16)
+    np.testing.assert_array_equal(orc.u16_to_f16(u), want)
