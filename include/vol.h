@@ -83,7 +83,7 @@ typedef struct {
  * loads all requested bricks between passes instead, on the calling thread.  The image is
  * the same either way. */
 #define VOL_RENDER_SERIAL_LOADS 4u
-/* Progressive preview (Sec. IV-B: a low-resolution image from coarser levels first, refined as
+/* Progressive preview (Sec. III-H: a low-resolution image from coarser levels first, refined as
  * bricks arrive).  One pass: a sample whose brick on its level is not resident is taken on the
  * finest coarser level whose brick at that position is resident (left out when none is) instead
  * of waiting, and the brick it wanted is requested.  With a provider the requested bricks start
@@ -102,6 +102,11 @@ typedef struct {
  * (a look-ahead of eight bricks), so that it does not wait a round for each when it resumes; the
  * extra bricks may go unused.  This flag turns the look-ahead off.  Images do not change. */
 #define VOL_RENDER_NO_PREFETCH 32u
+/* Debug, with VOL_RENDER_GRAD only: keep the transmittance before every sample instead of every
+ * 32nd (4 bytes per sample of each ray), so vol_render_backward() reads every T_k instead of
+ * recomputing it forward within a 32-sample segment.  The gradients equal the checkpointed ones
+ * up to the order of the atomic additions; it exists to test that recompute. */
+#define VOL_RENDER_CKPT_ALL 64u
 
 /* Compositing (vol_params.composite).
  * VOL_COMPOSITE_DVR: front-to-back emission/absorption with early termination (Sec. IV-A).
@@ -195,6 +200,9 @@ typedef struct {
     int64_t load_wait_us;    /* host time the last render spent waiting for the provider (us) */
     int64_t launches;        /* kernels the library launched since the last render began */
     int64_t preview_samples; /* preview: samples taken on a coarser level or left out */
+    int64_t allocations;     /* device and pinned-host allocations the volume has made since
+                                vol_create (cumulative; never reset) */
+    int64_t skipped_samples; /* VOL_RENDER_SKIP_EMPTY: samples jumped over (not composited) */
 } vol_stats;
 
 /* Provider of bricks that are not resident (procedural or out-of-core source).
@@ -229,31 +237,50 @@ typedef struct {
 
 /* Computes the layout for dims / dtype / brick (power of two, 4..128) /
  * levels (1..16) / cache_bytes (0 = room for every brick of every level) /
- * flags (VOL_LAYOUT_COMPACT or 0).  Pure host code; needs no GPU. */
+ * flags (VOL_LAYOUT_COMPACT, VOL_LAYOUT_SPARSE_PT or 0): the bricking of
+ * Sec. III-A (chunk position h = floor(g / B) per axis), the level dims of
+ * Sec. III-D and the page-table extents of Sec. III-E.  Pure host code; needs
+ * no GPU.  Errors: VOL_ERR_INVALID_ARG (bad sizes, type or flags),
+ * VOL_ERR_UNSUPPORTED (more bricks than the chosen page table can index). */
 int vol_plan(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes,
              uint32_t flags, vol_layout *out);
 
-/* Creates a volume on the current CUDA device: allocates the atlas (the
- * cache of brick slots), the page tables (all entries non-resident) and the
- * slot usage stamps.  flags: VOL_LAYOUT_COMPACT or 0 (quad).  `stream` is a
- * cudaStream_t or NULL. */
+/* Creates a volume on the current CUDA device (Sec. III-C: the GPU-side brick
+ * store, here an atlas of equal slots; Sec. III-E: one page table per LOD
+ * level).  Allocates the atlas (the cache of brick slots), the page tables
+ * (all entries non-resident) and the slot usage stamps.  Arguments as for
+ * vol_plan(); `stream` is a cudaStream_t or NULL.  *out receives the handle,
+ * which the caller releases with vol_destroy().  Errors: those of vol_plan(),
+ * VOL_ERR_OOM, VOL_ERR_CUDA (message from vol_last_error(NULL)). */
 int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t cache_bytes,
                uint32_t flags, void *stream, vol_t *out);
 
-/* Frees everything the volume allocated.  NULL is ignored. */
+/* Frees everything the volume allocated, after waiting for its stream.  NULL
+ * is ignored.  (Library plumbing; the paper has no counterpart.) */
 void vol_destroy(vol_t v);
 
 /* Message of the last failure on v (or of the last vol_create failure when
- * v is NULL).  Valid until the next call on v. */
+ * v is NULL).  Valid until the next call on v.  (Library plumbing; the paper
+ * has no counterpart.) */
 const char *vol_last_error(vol_t v);
 
+/* Sets the CUDA stream (cudaStream_t or NULL) that orders the volume's later
+ * device work.  (Library plumbing; the paper has no counterpart.) */
 int vol_set_stream(vol_t v, void *stream);
+
+/* Copies the volume's layout (as vol_plan() computed it) to *out.  (Library
+ * plumbing; the paper has no counterpart.) */
 int vol_get_layout(vol_t v, vol_layout *out);
-int vol_get_stats(vol_t v, vol_stats *out); /* synchronises the stream */
+
+/* Copies the counters of the last render to *out; `touched` is read from the
+ * per-slot usage stamps (Sec. III-C/III-E use tracking).  Synchronises the
+ * stream. */
+int vol_get_stats(vol_t v, vol_stats *out);
 
 /* ---- bricks -------------------------------------------------------------- */
 
-/* Makes every brick of `level` resident from a dense level array `src`
+/* Sec. III-A bricking and Sec. III-E page-table insertion of a whole level:
+ * makes every brick of `level` resident from a dense level array `src`
  * (D_l voxels per axis, x fastest) of type src_dtype, in host memory
  * (src_on_device = 0) or device memory (1).  Each brick is written into its
  * atlas slot with its +side apron (edge voxels replicated at the volume
@@ -263,9 +290,14 @@ int vol_get_stats(vol_t v, vol_stats *out); /* synchronises the stream */
  * Host sources are copied synchronously. */
 int vol_upload_level(vol_t v, int level, const void *src, int src_dtype, int src_on_device);
 
-/* Makes one brick resident from (B+1)^3 voxels (apron included, layout as
- * for vol_provider_fn) of type src_dtype in host or device memory.  Evicts
- * the least recently used brick when the atlas is full. */
+/* Answers a brick request (Sec. III-H) by hand: makes brick (bx, by, bz) of
+ * `level` resident from (B+1)^3 voxels (apron included, layout as for
+ * vol_provider_fn) of type src_dtype in host (src_on_device = 0, copied
+ * before the call returns) or device memory (1, read on the stream) and
+ * publishes it in the level's page table (Sec. III-E).  Evicts the least
+ * recently used brick when the atlas is full (Sec. III-C).  Errors:
+ * VOL_ERR_INVALID_ARG (level or brick out of range), VOL_ERR_UNSUPPORTED
+ * (conversion), VOL_ERR_CACHE_FULL, VOL_ERR_CUDA. */
 int vol_upload_brick(vol_t v, int level, const int32_t brick[3], const void *src, int src_dtype,
                      int src_on_device);
 
@@ -280,24 +312,33 @@ int vol_build_lod(vol_t v, int from_level);
 
 /* Copies the (B+1)^3 stored voxels of a resident brick (apron included, x
  * fastest, whatever the slot layout) to host memory dst; synchronous.
- * VOL_ERR_INVALID_ARG when not resident. */
+ * VOL_ERR_INVALID_ARG when not resident.  (A debugging aid; the paper has no
+ * counterpart.) */
 int vol_download_brick(vol_t v, int level, const int32_t brick[3], void *dst);
 
-/* Drops every brick (page tables back to non-resident). */
+/* Drops every brick: page tables back to non-resident (Sec. III-E), every
+ * slot free (Sec. III-C).  Enqueued on the stream. */
 int vol_evict_all(vol_t v);
 
 /* Installs (or with fn = NULL removes) the provider used by vol_render() to
- * load missing bricks; src_dtype is the type the provider writes. */
+ * load missing bricks: the source that answers the brick requests of
+ * Sec. III-H, e.g. chunks generated on the fly as in Sec. V-C.  src_dtype is
+ * the type the provider writes; `user` is passed back to it unchanged and is
+ * owned by the caller. */
 int vol_set_provider(vol_t v, vol_provider_fn fn, void *user, int src_dtype);
 
-/* Installs (or with fn = NULL removes) a batch provider; it takes precedence over the
- * per-brick provider.  Bricks are requested in batches of up to 64 MiB of source voxels. */
+/* Installs (or with fn = NULL removes) a batch provider (the source of Sec. III-H's brick
+ * requests, called for many bricks at once; Sec. V-C's on-the-fly chunk generation); it takes
+ * precedence over the per-brick provider.  Bricks are requested in batches of up to 64 MiB of
+ * source voxels.  `user` is owned by the caller and must outlive the volume's use of it. */
 int vol_set_provider_batch(vol_t v, vol_provider_batch_fn fn, void *user, int src_dtype);
 
 /* ---- rendering ----------------------------------------------------------- */
 
-/* Renders nviews views (cams: host array) in one persistent launch that
- * takes ray tiles of all views from one work counter.  tf_dev: device
+/* Direct volume rendering (Sec. IV-A; ray entry/exit and camera of Fig. 1;
+ * footprint LOD of Sec. V-C; brick requests of Sec. III-H; tiles as tasks of
+ * Sec. III-H).  Renders nviews views (cams: host array) in one persistent
+ * launch that takes ray tiles of all views from one work counter.  tf_dev: device
  * float [256][4] RGBA transfer function (entry j at value j / 255, linearly
  * interpolated).  rgba_dev: output float [pixels][4], the views' images
  * packed in order, in memory of the volume's GPU or in page-locked host
@@ -322,27 +363,40 @@ int vol_render(vol_t v, const vol_camera *cams, int nviews, const float *tf_dev,
                const vol_params *params, float *rgba_dev, int32_t *nsamples_dev);
 
 /* Resumes the rays that the last vol_render() left suspended, after the
- * caller uploaded the requested bricks (vol_upload_brick). Synchronises.
- * VOL_OK when every ray finished, else VOL_ERR_INCOMPLETE. */
+ * caller uploaded the requested bricks (vol_upload_brick): the kernel run
+ * again after the requests are answered, Sec. III-H.  Synchronises.
+ * VOL_OK when every ray finished, else VOL_ERR_INCOMPLETE;
+ * VOL_ERR_NO_FORWARD_STATE without a render. */
 int vol_render_resume(vol_t v);
 
-/* Copies up to cap outstanding brick requests of the last pass as
- * [level, bx, by, bz] int32 quadruples to host memory; *n receives their
- * total count (which may exceed cap). Synchronises. */
+/* Reads the brick-request table of Sec. III-H: copies up to cap outstanding
+ * brick requests of the last pass as [level, bx, by, bz] int32 quadruples to
+ * host memory `out` (caller-owned, cap * 4 int32); *n receives their total
+ * count (which may exceed cap).  Synchronises.  VOL_ERR_INVALID_ARG for a
+ * NULL n, or a NULL out with cap > 0. */
 int vol_poll_requests(vol_t v, int32_t *out, int cap, int *n);
 
-/* Adjoint of the last vol_render() made with VOL_RENDER_GRAD (lod_mode 0,
- * every brick resident, no suspended rays).  drgba_dev: dL/dRGBA in the
- * layout of rgba_dev.  Accumulates (+=) dL/dtf into dtf_dev (device float
+/* Adjoint of the last vol_render() made with VOL_RENDER_GRAD (every brick of
+ * the levels it sampled still resident, no suspended rays).  Not in the paper:
+ * the reverse of Sec. IV-A's front-to-back compositing.  drgba_dev: dL/dRGBA in
+ * the layout of rgba_dev.  Accumulates (+=) dL/dtf into dtf_dev (device float
  * [256][4]) and dL/dvoxel into dvoxel_dev (device float, dense level 0, x
  * fastest; gradient with respect to the normalised voxel value).  Either
  * output may be NULL.  Transmittance is recomputed forward from checkpoints
- * stored every 32 samples, never by dividing by (1 - a). */
+ * stored every 32 samples, never by dividing by (1 - a).  With footprint LOD
+ * (lod_mode 1) a sample on level l reads level-l voxels, each the 2x2x2 box
+ * filter of level l-1 (Sec. III-D): their gradients are carried down to level
+ * 0 through the filter's adjoint, 1/8 to each child (a child index past an
+ * odd edge counts as the last voxel, as in the filter; integer storage is
+ * differentiated as the mean).  Errors: VOL_ERR_NO_FORWARD_STATE (no gradient
+ * render, an incomplete one, or a level evicted since), VOL_ERR_INVALID_ARG
+ * (NULL drgba_dev), VOL_ERR_CUDA. */
 int vol_render_backward(vol_t v, const float *drgba_dev, float *dtf_dev, float *dvoxel_dev);
 
-/* Debug: the decision-layer record of up to max_samples samples of each of
- * npix pixels (pixels_host: int32 [npix][2] = px, py of view `cam`), without
- * early termination.  out_host: [npix][max_samples] records; counts_host:
+/* Debug: the decision-layer record (sample depth, Sec. V-C footprint level,
+ * Sec. III-A voxel, brick and local position, Sec. III-E slot) of up to
+ * max_samples samples of each of npix pixels (pixels_host: int32 [npix][2] =
+ * px, py of view `cam`), without early termination.  out_host: [npix][max_samples] records; counts_host:
  * int32 [npix] total samples per ray.  Synchronises. */
 int vol_trace(vol_t v, const vol_camera *cam, const vol_params *params, const int32_t *pixels_host,
               int npix, int max_samples, vol_trace_rec *out_host, int32_t *counts_host);
@@ -374,7 +428,10 @@ int vol_trace(vol_t v, const vol_camera *cam, const vol_params *params, const in
  *     vol_render_backward(), and it does not update the LRU usage stamps.
  * Errors: VOL_ERR_INVALID_ARG (null pointers, an output the GPU cannot address, nviews outside
  * 1..VOL_NOALLOC_MAX_VIEWS, bad image size or tile), VOL_ERR_UNSUPPORTED
- * (VOL_RENDER_GRAD set, or a needed level not fully resident), VOL_ERR_CUDA. */
+ * (VOL_RENDER_GRAD set, a needed level not fully resident, or a sparse page
+ * table with a projection or level-scaled sampling), VOL_ERR_CUDA.
+ * vol_stats then describes this call (launches = 1), and
+ * vol_stats.allocations stays unchanged. */
 #define VOL_NOALLOC_SCRATCH_BYTES 8192
 #define VOL_NOALLOC_MAX_VIEWS 64
 int vol_render_noalloc(vol_t v, const vol_camera *cams, int nviews, const float *tf_dev,

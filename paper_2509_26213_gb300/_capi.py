@@ -32,6 +32,7 @@ VOL_RENDER_SERIAL_LOADS = 4
 VOL_RENDER_PREVIEW = 8
 VOL_RENDER_LEVEL_STEP = 16
 VOL_RENDER_NO_PREFETCH = 32
+VOL_RENDER_CKPT_ALL = 64
 VOL_COMPOSITE_DVR, VOL_COMPOSITE_MOP, VOL_COMPOSITE_MIP = 0, 1, 2
 COMPOSITES = {"dvr": VOL_COMPOSITE_DVR, "mop": VOL_COMPOSITE_MOP, "mip": VOL_COMPOSITE_MIP}
 VOL_LAYOUT_COMPACT = 1
@@ -75,7 +76,8 @@ class vol_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("passes", "rays", "suspended", "requests", "request_overflow",
                                                "bricks_loaded", "bytes_loaded", "evicted", "resident", "frame",
                                                "device_error", "touched", "load_wait_us", "launches",
-                                               "preview_samples")]
+                                               "preview_samples", "allocations",
+                                               "skipped_samples")]
 
 
 class vol_trace_rec(ctypes.Structure):

@@ -10,7 +10,8 @@ namespace volrc {
 
 constexpr uint32_t kInvalidSlot = 0xFFFFFFFFu;
 constexpr int kMaxLevels = VOL_MAX_LEVELS;
-constexpr int kCkptEvery = 32;      // transmittance checkpoint spacing (samples)
+constexpr int kCkptEvery = 32;      // transmittance checkpoint spacing (samples), the largest allowed
+constexpr int kCkptShift = 5;       // log2 kCkptEvery
 // Sample indices of a ray stay below this, so that they and small offsets of them are exact in
 // binary32 (past 2^24, neighbouring indices round to the same depth).
 constexpr double kMaxSamplesPerRay = 16777216.0 - 64.0;
@@ -35,6 +36,7 @@ enum Counter : int {
     kReqOverflow = 3,
     kDevError = 4,
     kPreview = 5,    // preview: samples taken from a coarser level, or left out
+    kSkipped = 6,    // words 6-7: 64-bit count of samples jumped over by empty-space skipping
     kNumCounters = 8
 };
 
@@ -115,10 +117,11 @@ struct RenderDev {
     unsigned long long* req_list64;
     unsigned* last_used;
     unsigned frame;
-    // gradient checkpoints
+    // gradient checkpoints: T before samples 2^ckpt_shift, 2 * 2^ckpt_shift, ... (ckpt_shift 5:
+    // every 32nd sample; 0: every sample, the store-all debug mode)
     float* ckpt;
     long long nrays;
-    int ckpt_segs;
+    int ckpt_shift;
     int* ray_n;
     // scheduling: work item i of a fresh pass renders tile tile_order[i] (NULL: tile i);
     // every finished ray raises tile_cost[its tile] to its sample count: the tile's longest ray
@@ -143,6 +146,7 @@ struct BackwardDev {
     int lod_mode, lod_bias;
     unsigned* counters;
     const float* ckpt;
+    int ckpt_shift;         // checkpoint spacing 2^ckpt_shift samples (0..kCkptShift)
     long long nrays;
     const int* ray_n;
     const int* tile_order;  // longest-ray-first order of the tiles (NULL: tile i)

@@ -73,6 +73,8 @@ constexpr int kBwdMinBlocks = VOLRC_BWD_MINB;
 // processes one segment of it (samples 32 s .. 32 s + 31, the last one partial), first
 // forward -- transmittance from the segment's checkpoint and the sample values into shared
 // memory, kBwdBatch samples at a time -- then in reverse, accumulating dL/dtf and dL/dvoxel.
+// (With checkpoints before every sample -- the store-all debug mode -- a segment is one sample
+// and its transmittance is read, not recomputed.)
 // Lanes take a new ray between rounds, so a warp waits only on segments, not on whole rays.
 // LOD: samples on footprint levels; the gradient of a level-l voxel goes to P.dlev[l], which
 // the host then carries down to level 0 through the box filter's adjoint.
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                         lodscale = V.lodscale;
                         g = P.drgba[ray];
                         R0 = P.bg.x; R1 = P.bg.y; R2 = P.bg.z; R3 = P.bg.w;
-                        s = (n - 1) / kCkptEvery;
+                        s = (n - 1) >> P.ckpt_shift;
                         has = true;
                     }
                 }
@@ -170,9 +172,9 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
         }
         if (!__ballot_sync(kFull, has)) break;
 
-        // ---- one round: segment s of every lane's ray
-        const int k0 = s * kCkptEvery;
-        const int len = has ? min(kCkptEvery, n - k0) : 0;
+        // ---- one round: segment s of every lane's ray (2^ckpt_shift <= kCkptEvery samples)
+        const int k0 = s << P.ckpt_shift;
+        const int len = has ? min(1 << P.ckpt_shift, n - k0) : 0;
         float T = (has && s > 0) ? P.ckpt[(long long)(s - 1) * P.nrays + ray] : 1.0f;
         const int maxlen = __reduce_max_sync(kFull, len);
         // forward: decisions, then the page-table lookups, then the gathers of kBwdBatch samples

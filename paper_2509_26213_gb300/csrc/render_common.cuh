@@ -394,7 +394,7 @@ __device__ __noinline__ int brick_last_sample(int k_start, uint32_t pti_start, c
     return ke;
 }
 
-// Progressive preview (Sec. IV-B: a low-resolution image from coarser levels first): the
+// Progressive preview (Sec. III-H: a low-resolution image from coarser levels first): the
 // sample at depth t, whose brick on its level is not resident, on the finest coarser level
 // whose brick at the same position is resident.  ok = false when no level is.
 struct Fallback {
@@ -957,8 +957,8 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                             dn = s_tfd[ti[j + 1]];
                         }
                         if (j < stop && !fin) {
-                            if (GRAD && k > 0 && (k & (kCkptEvery - 1)) == 0)
-                                P.ckpt[(long long)(k / kCkptEvery - 1) * P.nrays + ray] = T;
+                            if (GRAD && k > 0 && (k & ((1 << P.ckpt_shift) - 1)) == 0)
+                                P.ckpt[(long long)((k >> P.ckpt_shift) - 1) * P.nrays + ray] = T;
                             fin = composite_row<MODE, LS>(tw[j], a, dab, amax_tf, et, T, C0, C1, C2,
                                                           LS ? lv[j] : 0);
                             ++k;
@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 }
                 bool fell = false;
                 if (!GRAD && P.preview && !fin && miss_at < kBatch && miss_at < empty_at) {
-                    // preview (Sec. IV-B): sample k lies in a brick that is not resident.  Request the
+                    // preview (Sec. III-H): sample k lies in a brick that is not resident.  Request the
                     // brick for the refinement and take the sample on the finest coarser resident
                     // level (left out when none is).
                     if (SP) {
@@ -1012,9 +1012,18 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     const float o3[3] = {o0, o1, o2}, d3[3] = {d0, d1, d2};
                     const int klast = brick_last_sample<LOD>(k, empty_pti, o3, d3, t0, t1, step, lodscale,
                                                              P.lod_bias, nlev, s_lv, bshift, bmask, row, B1 - 1);
-                    if (GRAD)
-                        for (int kk = ((k + kCkptEvery - 1) / kCkptEvery) * kCkptEvery; kk <= klast; kk += kCkptEvery)
-                            if (kk > 0) P.ckpt[(long long)(kk / kCkptEvery - 1) * P.nrays + ray] = T;
+                    {  // count the samples jumped over (one atomic per warp)
+                        const unsigned long long nskip = (unsigned long long)(klast + 1 - k);
+                        const unsigned m = __activemask();
+                        const unsigned long long tot = __reduce_add_sync(m, (unsigned)nskip);
+                        if ((int)lane == __ffs(m) - 1)
+                            atomicAdd(reinterpret_cast<unsigned long long*>(P.counters + kSkipped), tot);
+                    }
+                    if (GRAD) {
+                        const int cs = P.ckpt_shift;
+                        for (int kk = ((k + (1 << cs) - 1) >> cs) << cs; kk <= klast; kk += 1 << cs)
+                            if (kk > 0) P.ckpt[(long long)((kk >> cs) - 1) * P.nrays + ray] = T;
+                    }
                     k = klast + 1;
                 } else if (fin) {
                     const float4 bg = P.bg;

@@ -190,6 +190,7 @@ struct vol_s {
     // gradient state
     float* ckpt = nullptr;
     size_t ckpt_cap = 0;
+    int ckpt_shift = kCkptShift;  // checkpoints every 2^ckpt_shift samples (0: VOL_RENDER_CKPT_ALL)
     int* ray_n = nullptr;
     size_t ray_n_cap = 0;
     float* dlev_buf = nullptr;  // adjoint with LOD: gradients of levels 1..L-1
@@ -257,10 +258,25 @@ struct vol_s {
     float2* range = nullptr;               // per slot: min and max stored value
 
     vol_stats stats{};
+    int64_t allocations = 0;  // device and pinned-host allocations since vol_create
+    bool counters_collected = true;  // the counter words hold a pass collect_pass already read
+    unsigned* last_counters = nullptr;  // the counter words of the last pass (NULL: counters)
     int occ_cache[4][2] = {{0}};
+    ViewDev noalloc_views[VOL_NOALLOC_MAX_VIEWS];  // vol_render_noalloc's host staging of its view table
 };
 
 namespace {
+
+// Every device and pinned-host allocation of a volume goes through these two, which count it
+// (vol_stats.allocations).
+cudaError_t dev_alloc(vol_t v, void** p, size_t bytes) {
+    ++v->allocations;
+    return cudaMalloc(p, bytes);
+}
+cudaError_t host_alloc(vol_t v, void** p, size_t bytes, unsigned flags) {
+    ++v->allocations;
+    return cudaHostAlloc(p, bytes, flags);
+}
 
 int fail(vol_t v, int code, const std::string& msg) {
     if (v) v->err = msg;
@@ -334,7 +350,7 @@ int pool_page(vol_t v, uint32_t* base) {
         if (cap >= (size_t(1) << 32) - 16) return fail(v, VOL_ERR_OOM, "sparse page table: pool full");
         uint32_t* np = nullptr;
         CK(v, cudaStreamSynchronize(v->stream));
-        CK(v, cudaMalloc((void**)&np, sizeof(uint32_t) * cap));
+        CK(v, dev_alloc(v, (void**)&np, sizeof(uint32_t) * cap));
         CK(v, cudaMemcpyAsync(np, v->pt, sizeof(uint32_t) * v->pool_used, cudaMemcpyDeviceToDevice, v->stream));
         CK(v, cudaMemsetAsync(np + v->pool_used, 0xFF, sizeof(uint32_t) * (cap - v->pool_used), v->stream));
         CK(v, cudaStreamSynchronize(v->stream));
@@ -397,7 +413,7 @@ int ensure(vol_t v, T*& ptr, size_t& cap, size_t n, const char* what) {
     if (ptr) cudaFree(ptr);
     ptr = nullptr;
     cap = 0;
-    cudaError_t e = cudaMalloc((void**)&ptr, sizeof(T) * std::max<size_t>(n, 1));
+    cudaError_t e = dev_alloc(v, (void**)&ptr, sizeof(T) * std::max<size_t>(n, 1));
     if (e != cudaSuccess) return cuda_fail(v, e, what);
     cap = std::max<size_t>(n, 1);
     return VOL_OK;
@@ -550,12 +566,12 @@ int ensure_miss_buffers(vol_t v) {
     if (!v->req_table) {
         v->req_cap = 1u << 16;
         v->req_list_cap = 1u << 16;
-        CK(v, cudaMalloc((void**)&v->req_table, sizeof(unsigned) * v->req_cap));
-        CK(v, cudaMalloc((void**)&v->req_list, sizeof(unsigned) * v->req_list_cap));
+        CK(v, dev_alloc(v, (void**)&v->req_table, sizeof(unsigned) * v->req_cap));
+        CK(v, dev_alloc(v, (void**)&v->req_list, sizeof(unsigned) * v->req_list_cap));
     }
     if (v->sparse && !v->req_table64) {
-        CK(v, cudaMalloc((void**)&v->req_table64, sizeof(unsigned long long) * v->req_cap));
-        CK(v, cudaMalloc((void**)&v->req_list64, sizeof(unsigned long long) * v->req_list_cap));
+        CK(v, dev_alloc(v, (void**)&v->req_table64, sizeof(unsigned long long) * v->req_cap));
+        CK(v, dev_alloc(v, (void**)&v->req_list64, sizeof(unsigned long long) * v->req_list_cap));
     }
     if (v->susp_cap < v->nrays) {
         for (int i = 0; i < 2; ++i) {
@@ -563,7 +579,7 @@ int ensure_miss_buffers(vol_t v) {
             v->susp[i] = nullptr;
         }
         v->susp_cap = 0;
-        for (int i = 0; i < 2; ++i) CK(v, cudaMalloc((void**)&v->susp[i], sizeof(SuspRec) * (size_t)v->nrays));
+        for (int i = 0; i < 2; ++i) CK(v, dev_alloc(v, (void**)&v->susp[i], sizeof(SuspRec) * (size_t)v->nrays));
         v->susp_cap = v->nrays;
     }
     return VOL_OK;
@@ -601,6 +617,7 @@ RenderDev render_args(vol_t v) {
     p.nrays = v->nrays;
     if (v->grad) {
         p.ckpt = v->ckpt;
+        p.ckpt_shift = v->ckpt_shift;
         p.ray_n = v->ray_n;
     }
     return p;
@@ -638,6 +655,8 @@ int run_pass(vol_t v, bool resume, bool may_miss) {
     }
     p.tile_cost = v->tile_cost;
     CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
+    v->counters_collected = false;
+    v->last_counters = v->counters;
     const int grid = grid_for(v, v->dtype, v->grad, v->params.ctas_per_sm);
     if (v->ev_pass_start) CK(v, cudaEventRecord(v->ev_pass_start, v->stream));
     CK(v, launch_render(v->dtype, render_mode(v->params, v->grad), p, grid, v->stream));
@@ -655,6 +674,8 @@ int collect_pass(vol_t v, bool resumed) {
     CK(v, cudaStreamSynchronize(v->stream));
     v->stats.device_error += c[kDevError];
     v->stats.preview_samples += c[kPreview];
+    v->stats.skipped_samples += (int64_t)(((uint64_t)c[kSkipped + 1] << 32) | c[kSkipped]);
+    v->counters_collected = true;
     v->stats.request_overflow += c[kReqOverflow];
     const uint32_t nreq = std::min<uint32_t>(c[kReqCount], v->req_list_cap);
     v->stats.requests += nreq;
@@ -686,9 +707,9 @@ int ensure_stage(vol_t v) {
     const int64_t B1 = v->B + 1;
     const size_t brick_bytes = (size_t)(B1 * B1 * B1) * 4;  // room for the widest source type
     v->stage_bricks = (int)std::max<int64_t>(1, std::min<int64_t>(256, (64ll << 20) / (int64_t)brick_bytes));
-    CK(v, cudaMallocHost(&v->stage_host, brick_bytes * v->stage_bricks));
-    CK(v, cudaMalloc(&v->stage_dev, brick_bytes * v->stage_bricks));
-    CK(v, cudaMalloc((void**)&v->stage_slots_dev, sizeof(uint32_t) * v->stage_bricks));
+    CK(v, host_alloc(v, &v->stage_host, brick_bytes * v->stage_bricks, cudaHostAllocDefault));
+    CK(v, dev_alloc(v, (void**)&v->stage_dev, brick_bytes * v->stage_bricks));
+    CK(v, dev_alloc(v, (void**)&v->stage_slots_dev, sizeof(uint32_t) * v->stage_bricks));
     return VOL_OK;
 }
 
@@ -859,7 +880,7 @@ int ensure_overlap(vol_t v) {
     const size_t bb = (size_t)(B1 * B1 * B1) * bpv_of(v->prov_dtype);
     if (!v->poll_stream) CK(v, cudaStreamCreateWithFlags(&v->poll_stream, cudaStreamNonBlocking));
     if (!v->poll_host)
-        CK(v, cudaHostAlloc((void**)&v->poll_host, sizeof(uint32_t) * ((size_t)v->req_list_cap + 1), cudaHostAllocDefault));
+        CK(v, host_alloc(v, (void**)&v->poll_host, sizeof(uint32_t) * ((size_t)v->req_list_cap + 1), cudaHostAllocDefault));
     for (cudaEvent_t* e : {&v->ev_pass_start, &v->ev_pass_end})
         if (!*e) CK(v, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     if (R.host && R.brick_bytes == bb) return VOL_OK;
@@ -873,9 +894,9 @@ int ensure_overlap(vol_t v) {
     R.brick_bytes = bb;
     R.cap = (int)std::max<size_t>(64, std::min<size_t>(65536, (size_t(1) << 30) / bb));
     const unsigned fl = cudaHostAllocMapped | cudaHostAllocPortable;
-    CK(v, cudaHostAlloc((void**)&R.host, bb * R.cap, fl));
-    CK(v, cudaHostAlloc((void**)&R.slots, sizeof(uint32_t) * R.cap, fl));
-    CK(v, cudaHostAlloc((void**)&R.ptis, sizeof(uint32_t) * R.cap, fl));
+    CK(v, host_alloc(v, (void**)&R.host, bb * R.cap, fl));
+    CK(v, host_alloc(v, (void**)&R.slots, sizeof(uint32_t) * R.cap, fl));
+    CK(v, host_alloc(v, (void**)&R.ptis, sizeof(uint32_t) * R.cap, fl));
     CK(v, cudaHostGetDevicePointer((void**)&R.host_dev, R.host, 0));
     CK(v, cudaHostGetDevicePointer((void**)&R.slots_dev, R.slots, 0));
     CK(v, cudaHostGetDevicePointer((void**)&R.ptis_dev, R.ptis, 0));
@@ -1190,13 +1211,13 @@ int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t
     const size_t pt_entries = v->sparse ? (size_t)lay.pt_top_entries + 256 * (size_t)kPageEntries : (size_t)lay.total_bricks;
     cudaError_t e = cudaGetDevice(&v->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v->nsm, cudaDevAttrMultiProcessorCount, v->device);
-    if (e == cudaSuccess) e = cudaMalloc(&v->atlas, (size_t)lay.atlas_bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v->pt, sizeof(uint32_t) * pt_entries);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v->last_used, sizeof(unsigned) * (size_t)lay.nslots);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v->counters, sizeof(unsigned) * kNumCounters);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v->aux, sizeof(unsigned) * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v->order_buckets, sizeof(int) * 64);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v->range, sizeof(float2) * (size_t)lay.nslots);
+    if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->atlas, (size_t)lay.atlas_bytes);
+    if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->pt, sizeof(uint32_t) * pt_entries);
+    if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->last_used, sizeof(unsigned) * (size_t)lay.nslots);
+    if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->counters, sizeof(unsigned) * kNumCounters);
+    if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->aux, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->order_buckets, sizeof(int) * 64);
+    if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->range, sizeof(float2) * (size_t)lay.nslots);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * pt_entries, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->last_used, 0, sizeof(unsigned) * (size_t)lay.nslots, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->aux, 0, sizeof(unsigned) * 4, v->stream);
@@ -1271,7 +1292,8 @@ int vol_get_layout(vol_t v, vol_layout* out) {
 int vol_get_stats(vol_t v, vol_stats* out) {
     if (!v || !out) return VOL_ERR_INVALID_ARG;
     unsigned c[kNumCounters], aux[4];
-    CK(v, cudaMemcpyAsync(c, v->counters, sizeof(c), cudaMemcpyDeviceToHost, v->stream));
+    CK(v, cudaMemcpyAsync(c, v->last_counters ? v->last_counters : v->counters, sizeof(c), cudaMemcpyDeviceToHost,
+                          v->stream));
     CK(v, cudaMemcpyAsync(aux, v->aux, sizeof(aux), cudaMemcpyDeviceToHost, v->stream));
     CK(v, cudaStreamSynchronize(v->stream));
     std::vector<uint32_t> stamp((size_t)v->lay.nslots);
@@ -1282,7 +1304,13 @@ int vol_get_stats(vol_t v, vol_stats* out) {
         if (v->owner[s] != kInvalidSlot && stamp[s] == v->frame && v->frame) out->touched++;
     out->resident = v->resident;
     out->frame = v->frame;
-    out->device_error = v->stats.device_error + c[kDevError] + aux[0];
+    // the counters of a pass that collect_pass has not read yet (a render that missed nothing)
+    if (!v->counters_collected) {
+        out->device_error += c[kDevError];
+        out->skipped_samples += (int64_t)(((uint64_t)c[kSkipped + 1] << 32) | c[kSkipped]);
+    }
+    out->device_error += aux[0];
+    out->allocations = v->allocations;
     return VOL_OK;
 }
 
@@ -1304,9 +1332,9 @@ int vol_upload_level(vol_t v, int level, const void* src, int src_dtype, int src
     const void* dsrc = src;
     void* tmp = nullptr;
     uint32_t* dslots = nullptr;
-    CK(v, cudaMalloc((void**)&dslots, sizeof(uint32_t) * (size_t)nb));
+    CK(v, dev_alloc(v, (void**)&dslots, sizeof(uint32_t) * (size_t)nb));
     if (!src_on_device) {
-        cudaError_t e = cudaMalloc(&tmp, sbytes);
+        cudaError_t e = dev_alloc(v, (void**)&tmp, sbytes);
         if (e != cudaSuccess) { cudaFree(dslots); return cuda_fail(v, e, "upload staging"); }
         e = cudaMemcpyAsync(tmp, src, sbytes, cudaMemcpyHostToDevice, v->stream);
         if (e != cudaSuccess) { cudaFree(dslots); cudaFree(tmp); return cuda_fail(v, e, "upload copy"); }
@@ -1369,7 +1397,7 @@ int vol_build_lod(vol_t v, int from_level) {
         for (int64_t b = 0; b < nb; ++b)
             if (int rc = slot_for(v, (uint32_t)(v->lay.level_pt_offset[l] + b), &slots[(size_t)b])) return rc;
         uint32_t* dslots = nullptr;
-        CK(v, cudaMalloc((void**)&dslots, sizeof(uint32_t) * (size_t)nb));
+        CK(v, dev_alloc(v, (void**)&dslots, sizeof(uint32_t) * (size_t)nb));
         cudaError_t e = cudaMemcpyAsync(dslots, slots.data(), sizeof(uint32_t) * (size_t)nb, cudaMemcpyHostToDevice, v->stream);
         int rc = VOL_OK;
         if (e == cudaSuccess) rc = flush_pt_updates(v);  // the source level's entries must be live
@@ -1529,6 +1557,8 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     const bool grad = (p.flags & VOL_RENDER_GRAD) != 0;
     if (grad && p.composite != VOL_COMPOSITE_DVR)
         return fail(v, VOL_ERR_UNSUPPORTED, "gradients need emission/absorption compositing");
+    if ((p.flags & VOL_RENDER_CKPT_ALL) && !grad)
+        return fail(v, VOL_ERR_INVALID_ARG, "VOL_RENDER_CKPT_ALL needs VOL_RENDER_GRAD");
     const bool preview = (p.flags & VOL_RENDER_PREVIEW) != 0;
     if (grad && preview) return fail(v, VOL_ERR_UNSUPPORTED, "a preview keeps no gradient state");
     if ((p.flags & VOL_RENDER_LEVEL_STEP) && (grad || p.composite != VOL_COMPOSITE_DVR))
@@ -1569,7 +1599,7 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         if (v->views_dev) cudaFree(v->views_dev);
         v->views_dev = nullptr;
         v->views_cap = 0;
-        CK(v, cudaMalloc((void**)&v->views_dev, sizeof(ViewDev) * nviews));
+        CK(v, dev_alloc(v, (void**)&v->views_dev, sizeof(ViewDev) * nviews));
         v->views_cap = nviews;
     }
     CK(v, cudaMemcpyAsync(v->views_dev, v->views_host.data(), sizeof(ViewDev) * nviews, cudaMemcpyHostToDevice, v->stream));
@@ -1592,7 +1622,9 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         double diag = 0.0;
         for (int a = 0; a < 3; ++a) diag += (double)v->lay.dims[a] * (double)v->lay.dims[a];
         const int64_t max_n = (int64_t)std::ceil(std::sqrt(diag) / (double)p.step) + 2;
-        const int64_t segs = (max_n + kCkptEvery - 1) / kCkptEvery;
+        v->ckpt_shift = (p.flags & VOL_RENDER_CKPT_ALL) ? 0 : kCkptShift;
+        const int64_t every = int64_t(1) << v->ckpt_shift;
+        const int64_t segs = (max_n + every - 1) / every;
         if (int rc = ensure(v, v->ckpt, v->ckpt_cap, (size_t)std::max<int64_t>(1, segs - 1) * (size_t)rays, "checkpoints")) return rc;
         if (int rc = ensure(v, v->ray_n, v->ray_n_cap, (size_t)rays, "ray sample counts")) return rc;
     }
@@ -1716,11 +1748,14 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
     }
     b.counters = v->counters;
     b.ckpt = v->ckpt;
+    b.ckpt_shift = v->ckpt_shift;
     b.nrays = v->nrays;
     b.ray_n = v->ray_n;
     // the order built from this forward's per-tile longest rays: those tiles first
     b.tile_order = v->order_ready ? v->tile_order : nullptr;
     CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
+    v->counters_collected = false;  // vol_get_stats adds the adjoint's device-side check count
+    v->last_counters = v->counters;
     const int grid = backward_blocks_per_sm(v->dtype, lod) * v->nsm;
     CK(v, launch_backward(v->dtype, b, grid, v->stream));
     v->stats.launches += 1;
@@ -1773,9 +1808,9 @@ int vol_trace(vol_t v, const vol_camera* cam, const vol_params* params, const in
     int* dcnt = nullptr;
     vol_trace_rec* drec = nullptr;
     const size_t nrec = (size_t)npix * (size_t)std::max(1, max_samples);
-    cudaError_t e = cudaMalloc((void**)&dpix, sizeof(int) * 2 * npix);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&dcnt, sizeof(int) * npix);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&drec, sizeof(vol_trace_rec) * nrec);
+    cudaError_t e = dev_alloc(v, (void**)&dpix, sizeof(int) * 2 * npix);
+    if (e == cudaSuccess) e = dev_alloc(v, (void**)&dcnt, sizeof(int) * npix);
+    if (e == cudaSuccess) e = dev_alloc(v, (void**)&drec, sizeof(vol_trace_rec) * nrec);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dpix, pixels_host, sizeof(int) * 2 * npix, cudaMemcpyHostToDevice, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(drec, 0, sizeof(vol_trace_rec) * nrec, v->stream);
     if (e == cudaSuccess) {
@@ -1861,10 +1896,15 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
         return fail(v, VOL_ERR_UNSUPPORTED, "vol_render_noalloc keeps no gradient state; use vol_render");
     if ((p.flags & VOL_RENDER_LEVEL_STEP) && p.composite != VOL_COMPOSITE_DVR)
         return fail(v, VOL_ERR_UNSUPPORTED, "level-scaled sampling is for emission/absorption");
+    if (v->sparse && (p.composite != VOL_COMPOSITE_DVR || (p.flags & VOL_RENDER_LEVEL_STEP)))
+        return fail(v, VOL_ERR_UNSUPPORTED, "the sparse page table renders emission/absorption without "
+                                            "level-scaled sampling");
     if (!all_resident(v, p.lod_mode != 0))
         return fail(v, VOL_ERR_UNSUPPORTED, "vol_render_noalloc needs every brick of the used levels resident");
 
-    ViewDev views[VOL_NOALLOC_MAX_VIEWS];
+    // the view table is staged in host memory the volume owns (not a local array), so the
+    // source of the copy below outlives the call
+    ViewDev* views = v->noalloc_views;
     int64_t rays = 0, tiles = 0;
     for (int i = 0; i < nviews; ++i) {
         const vol_camera& c = cams[i];
@@ -1922,7 +1962,14 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
     r.counters = counters;
     r.nrays = rays;  // no request table, no suspension buffers, no usage stamps, no checkpoints
     const int grid = grid_for(v, v->dtype, false, p.ctas_per_sm);
+    // the per-render counters describe this call, as they do after vol_render (the state a
+    // gradient render left for vol_render_backward is not touched)
+    v->stats = vol_stats{};
+    v->stats.rays = rays;
+    v->counters_collected = false;
+    v->last_counters = counters;  // vol_get_stats reads this call's counters from the shared array
     CK(v, launch_render(v->dtype, render_mode(p, false), r, grid, v->stream));
-    v->stats.launches += 1;
+    v->stats.launches = 1;
+    v->stats.passes = 1;
     return VOL_OK;
 }

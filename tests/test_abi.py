@@ -32,6 +32,28 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(so, n), n
 
 
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment in vol.h names the passage of the paper it follows (a section
+    or figure), or says that the paper has no counterpart."""
+    text = open(os.path.join(ROOT, "include", "vol.h")).read()
+    cite = re.compile(r"Sec\. (III|IV|V|VI)-?[A-H]?|Fig\. \d|no counterpart|[Nn]ot in the paper")
+    missing = []
+    for m in re.finditer(r"^(?:int|void|const char \*)\s*(vol_[a-z_]+)\s*\(", text, flags=re.M):
+        # the comment block directly above the declaration (#define lines in between belong to it)
+        lines = text[:m.start()].rstrip().split("\n")
+        while lines and lines[-1].startswith("#define"):
+            lines.pop()
+        before = "\n".join(lines)
+        if not before.endswith("*/"):
+            missing.append(m.group(1))
+            continue
+        block = re.sub(r"\s*\n\s*\*?\s*", " ", before[before.rfind("/*"):])
+        if not cite.search(block):
+            missing.append(m.group(1))
+    assert not missing, f"declarations without a passage: {missing}"
+    assert len(re.findall(r"^(?:int|void|const char \*)\s*vol_", text, flags=re.M)) >= 20
+
+
 def test_struct_sizes_match_header(lib):
     # sizes follow from the field lists in vol.h (natural alignment)
     assert ctypes.sizeof(lib.vol_camera) == 4 * 14 + 8

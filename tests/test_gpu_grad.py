@@ -175,3 +175,50 @@ def test_autograd_function_matches_direct_calls(P):
     torch.cuda.synchronize()
     grad_close(tfd.grad.cpu().numpy(), dtf.cpu().numpy(), "dtf")
     grad_close(dens.grad.cpu().numpy(), dvox.cpu().numpy(), "dvoxel")
+
+
+def test_checkpoint_recompute_equals_store_all(P, orc):
+    """Transmittance recomputed forward from checkpoints every 32 samples against the store-all
+    debug mode (T kept before every sample and read back): the same images bit for bit, and the
+    same gradients up to the order of the atomic additions; both against the FP64 oracle."""
+    D, raw, cams, tf, params = small_case()
+    vol = P.Volume(D, "f32", 16, 1)
+    vol.upload_level(0, raw, "f32")
+    tfd = torch.from_numpy(tf).cuda()
+    rng = np.random.default_rng(11)
+    npx = sum(c["w"] * c["h"] for c in cams)
+    dI = torch.from_numpy(rng.standard_normal((npx, 4)).astype(np.float32) * np.float32(0.1)).cuda()
+    res = {}
+    for name, flags in (("ckpt32", 0), ("all", P.C.VOL_RENDER_CKPT_ALL)):
+        img, ns = vol.render(cams, tfd, dict(params, flags=flags), grad=True, nsamples=True)
+        dtf = torch.zeros((256, 4), dtype=torch.float32, device="cuda")
+        dvox = torch.zeros(raw.shape, dtype=torch.float32, device="cuda")
+        vol.render_backward(dI, dtf, dvox)
+        torch.cuda.synchronize()
+        assert vol.stats()["device_error"] == 0
+        res[name] = (img.cpu().numpy(), ns.cpu().numpy(), dtf.cpu().numpy(), dvox.cpu().numpy())
+    a, b = res["ckpt32"], res["all"]
+    assert int(a[1].max()) > 64  # rays span several checkpoint segments
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    for i, what in ((2, "dtf"), (3, "dvoxel")):
+        scale = float(np.abs(b[i]).max())
+        err = float(np.abs(a[i] - b[i]).max())
+        assert err <= 1e-6 * scale, f"{what}: checkpointed vs store-all max err {err:.3g} (scale {scale:.3g})"
+    ovol = orc.Volume([raw], "f32", 16)
+    odtf, odvox = np.zeros((256, 4)), np.zeros(raw.shape)
+    off = 0
+    dIh = dI.cpu().numpy().astype(np.float64)
+    for cam in cams:
+        n = cam["w"] * cam["h"]
+        pix = np.stack([np.arange(n) % cam["w"], np.arange(n) // cam["w"]], 1).astype(np.int32)
+        ref = orc.render(ovol, cam, tf, params, pixels=pix, amb=AMB)
+        _, bad, use_alt = compare(b[0][off:off + n], ref, TOL_FP32)
+        assert len(bad) == 0
+        g1, g2 = orc.render_grad(ovol, cam, tf, params, dIh[off:off + n], pixels=pix,
+                                 alt_select=use_alt.astype(np.int32), amb=AMB)
+        odtf += g1
+        odvox += g2
+        off += n
+    grad_close(b[2], odtf, "dtf (store-all)")
+    grad_close(b[3], odvox, "dvoxel (store-all)")

@@ -1,4 +1,4 @@
-"""Progressive preview (Sec. IV-B: a low-resolution image from coarser levels first, refined as
+"""Progressive preview (Sec. III-H: a low-resolution image from coarser levels first, refined as
 bricks arrive) on the GPU, against the FP64 oracle under the same residency map.
 
 * explicit residency (bricks uploaded one by one): the preview equals the oracle's preview,

@@ -1,4 +1,4 @@
-"""Pins for the oracle's progressive preview (Sec. IV-B: a coarse image first, refined as bricks
+"""Pins for the oracle's progressive preview (Sec. III-H: a coarse image first, refined as bricks
 arrive): under a residency map, a sample whose brick is absent on its level is taken on the
 finest coarser resident level at the same position, or composites nothing.
 

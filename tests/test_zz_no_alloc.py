@@ -2,10 +2,13 @@
 after set-up (a host that hands out a fixed device-memory budget once, a render loop that must
 never wait in the allocator).  Its scratch lives in a fixed 8 KiB array inside the library.
 
-The test calls it through the C ABI twice in a row -- with different view sets, so stale scratch
-from the first call would show in the second -- and compares each image with the one the regular
-entry point vol_render() gives for the same inputs, within the tests' float32 tolerance.  It is
-collected last so that a failure here stops a -x run only after every other test has run."""
+The test calls it through the C ABI twice in a row on a volume that has never rendered (so no
+render scratch of the volume exists) -- with different view sets, so stale scratch from the
+first call would show in the second -- checks through the volume's allocation count that the
+calls allocated nothing, and compares each image with the one the regular entry point
+vol_render() gives for the same inputs on a second volume built from the same data, within the
+tests' float32 tolerance.  It is collected last so that a failure here stops a -x run only
+after every other test has run."""
 import ctypes
 
 import numpy as np
@@ -37,20 +40,32 @@ def noalloc(P, vol, cams, tf, params, out):
 def test_noalloc_matches_regular_render_twice(P):
     D, raw, cam, tf_np, params = c1_inputs(seed=7)
     params = dict(params, lod_mode=1)
-    vol = P.Volume(D, "u8", 32, 2)
-    vol.upload_level(0, raw, "u8")
-    vol.build_lod(0)
+
+    def make():
+        v = P.Volume(D, "u8", 32, 2)
+        v.upload_level(0, raw, "u8")
+        v.build_lod(0)
+        return v
+
+    vol, ref = make(), make()
     tf = torch.from_numpy(tf_np).cuda()
     first = [synth.seeded_orbit(D, 96, 80, 7, view=0), synth.seeded_orbit(D, 64, 64, 7, view=1)]
     second = [synth.seeded_orbit(D, 200, 120, 7, view=2)]
+    allocs = vol.stats()["allocations"]
     for cams in (first, second):
         npx = sum(c["w"] * c["h"] for c in cams)
-        want = vol.render(cams, tf, params)
         got = torch.full((npx, 4), float("nan"), dtype=torch.float32, device="cuda")
         assert noalloc(P, vol, cams, tf, params, got) == 0
         torch.cuda.synchronize()
+        st = vol.stats()
+        assert st["allocations"] == allocs, "vol_render_noalloc allocated"
+        assert st["device_error"] == 0 and st["launches"] == 1
+        want = ref.render(cams, tf, params)
+        torch.cuda.synchronize()
         err = float((got - want).abs().max().item())
         assert err <= TOL_FP32, err
+    # the regular entry point allocated its render scratch on first use: the count sees it
+    assert ref.stats()["allocations"] > allocs
 
 
 def test_noalloc_rejects_what_it_cannot_do(P):
@@ -65,4 +80,17 @@ def test_noalloc_rejects_what_it_cannot_do(P):
     assert noalloc(P, vol, [cam] * (C.VOL_NOALLOC_MAX_VIEWS + 1), tf, params, out) == C.VOL_ERR_INVALID_ARG
     assert noalloc(P, vol, [cam], tf, dict(params, grad=True), out) == C.VOL_ERR_UNSUPPORTED
     assert noalloc(P, vol, [cam], tf, params, out) == 0
+    torch.cuda.synchronize()
+    # a sparse page table renders emission/absorption only: a projection is refused, not launched
+    sp = P.Volume(D, "u8", 32, 1, cache_bytes=64 << 20, sparse_pt=True)
+    B1 = 33
+    for bz in range(4):
+        for by in range(4):
+            for bx in range(4):
+                blk = np.ascontiguousarray(raw[np.minimum(np.arange(bz * 32, bz * 32 + B1), 127)][
+                    :, np.minimum(np.arange(by * 32, by * 32 + B1), 127)][
+                    :, :, np.minimum(np.arange(bx * 32, bx * 32 + B1), 127)])
+                sp.upload_brick(0, (bx, by, bz), blk, "u8")
+    assert noalloc(P, sp, [cam], tf, dict(params, composite="mop"), out) == C.VOL_ERR_UNSUPPORTED
+    assert noalloc(P, sp, [cam], tf, params, out) == 0
     torch.cuda.synchronize()
