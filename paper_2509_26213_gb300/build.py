@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvolrc.so")
 SOURCES = ["runtime.cu", "kernels_render.cu", "kernels_project.cu", "kernels_lstep.cu", "kernels_sparse.cu",
-           "kernels_volume.cu"]
+           "kernels_skip.cu", "kernels_skip_project.cu", "kernels_volume.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC]

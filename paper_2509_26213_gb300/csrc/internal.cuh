@@ -44,6 +44,7 @@ struct LevelDev {
     int D[3];        // voxels per axis
     int nb[3];       // bricks per axis
     float r[3];      // D_l / D_0 per axis, binary32
+    float ir[3];     // D_0 / D_l per axis (for estimates only; never in a decision)
     uint32_t pt_off; // first page-table entry (sparse table: of the level's top grid)
     int tn[3];       // sparse table: top-grid entries per axis, ceil(nb / 256)
 };
@@ -82,6 +83,12 @@ struct VolDev {
     const uint32_t* pt;            // flat page table, or the sparse table's pool
     int sparse;                    // 1: three-level sparse page table
     const float2* range;           // per slot: min and max stored value (stored units)
+    // per slot: the TF-entry span of each macro-cell (8 x 8 x 8 cells per brick, or B per axis
+    // when B < 8; cell c covers local voxels [c M, c M + M] per axis, M = B >> cbits): byte 0 the
+    // lowest and byte 1 the highest TF entry a trilinear lookup inside the cell can touch
+    const uint16_t* cells;
+    int cshift;                    // log2 M: a voxel's cell along an axis is (i0 & bmask) >> cshift
+    int cbits;                     // log2 of the cells per brick axis
     LevelDev lv[kMaxLevels];
     float D0f[3];
 };
@@ -98,7 +105,7 @@ struct RenderDev {
     float step, et;
     float4 bg;
     int lod_mode, lod_bias;
-    int skip_empty;     // skip bricks whose value range the TF maps to zero opacity
+    int skip_empty;     // empty-space skipping: launch the ES variant of the kernel
     int preview;        // a sample on a non-resident brick uses the finest coarser resident level
     int level_step;     // level-scaled sampling (chooses the kernel variant)
     int prefetch;       // a suspended ray also requests this many bricks after the missing one
@@ -177,6 +184,10 @@ const void* pick_render_projection(int dtype, int brick, bool quad, bool lod, in
 const void* pick_render_level_step(int dtype, int brick, bool quad, bool lod);
 // Sparse page table (kernels_sparse.cu): the emission/absorption variant.
 const void* pick_render_sparse(int dtype, int brick, bool quad, bool lod);
+// Empty-space skipping (kernels_skip.cu: emission/absorption; kernels_skip_project.cu: MOP, MIP):
+// the variant for mode kDvr, kMop or kMip (nullptr for a quad layout with bricks other than 32 or 64).
+const void* pick_render_skip(int dtype, int brick, bool quad, bool lod, int mode);
+const void* pick_render_skip_projection(int dtype, int brick, bool quad, bool lod, int mode);
 // order[] = tiles sorted by descending log2 bucket of cost[] (longest ray first); zeroes cost[].
 // buckets: 64 ints of device scratch.
 cudaError_t launch_tile_order(int* cost, int* order, int ntiles, int* buckets, cudaStream_t s);
@@ -197,9 +208,10 @@ cudaError_t launch_downsample(int dtype, const VolDev& vol, int level, const uin
 // level of dims Dfine filtered into the level of coarse (a child index past the edge counts as
 // the last voxel, as in the filter).
 cudaError_t launch_downsample_transpose(const float* coarse, float* fine, const int Dfine[3], cudaStream_t s);
-// range[slots[i]] = (min, max) of the stored values of each listed slot (one CTA per slot).
-cudaError_t launch_slot_range(int dtype, const VolDev& vol, float2* range, const uint32_t* slots, long long n,
-                              cudaStream_t s);
+// range[slots[i]] = (min, max) of the stored values of each listed slot, and the slot's macro-cell
+// TF-entry spans in cells (one CTA per slot).
+cudaError_t launch_slot_range(int dtype, const VolDev& vol, float2* range, uint16_t* cells, const uint32_t* slots,
+                              long long n, cudaStream_t s);
 // pt[idx[i]] = val[i] for i < n (atomic exchange; Sec. III-E parallel insert/remove).
 cudaError_t launch_pt_update(uint32_t* pt, const uint32_t* idx, const uint32_t* val, int n,
                              cudaStream_t s);

@@ -459,7 +459,15 @@ const void* pick_backward(int dtype, bool lod) { return lod ? pick_backward_l<tr
 
 cudaError_t launch_render(int dtype, int mode, const RenderDev& p, int grid, cudaStream_t s) {
     const void* fn = nullptr;
-    if (mode == kMop || mode == kMip)
+    // empty-space skipping: flat page table, uniform steps (a quad layout with bricks other than
+    // 32 or 64 has no such variant and renders without it; the image is the same)
+    if (p.skip_empty && !p.vol.sparse && !p.level_step)
+        fn = (mode == kMop || mode == kMip) ? pick_render_skip_projection(dtype, p.vol.B1 - 1, p.vol.quad != 0,
+                                                                          p.lod_mode != 0, mode)
+                                            : pick_render_skip(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0,
+                                                               mode);
+    if (fn) {
+    } else if (mode == kMop || mode == kMip)
         fn = pick_render_projection(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0, mode);
     else if (p.vol.sparse && mode == kDvr && !p.level_step)
         fn = pick_render_sparse(dtype, p.vol.B1 - 1, p.vol.quad != 0, p.lod_mode != 0);

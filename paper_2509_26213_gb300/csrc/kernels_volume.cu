@@ -207,11 +207,36 @@ __global__ void __launch_bounds__(kThreads) k_downsample(typename Stored<DT>::T*
     store4<DT>(atlas + ((unsigned long long)slot * vol.slot_entries + r) * 4, v0, v1, v2, v3);
 }
 
+// Transfer-function coordinate x = 255 clamp(v, 0, 1) of a stored value (u8: v; u16: v / 65535;
+// floats: v), with the arithmetic the render kernels use.
+template <int DT>
+__device__ __forceinline__ float stored_coord(float v) {
+    if (DT == VOL_U8) return v;
+    if (DT == VOL_U16) return v * (255.0f / 65535.0f);
+    return fminf(fmaxf(v, 0.0f), 1.0f) * 255.0f;
+}
+
+// Stored voxel (x, y, z), 0 <= x, y, z <= B, of slot a (either layout).
+template <int DT>
+__device__ __forceinline__ float slot_voxel(const typename Stored<DT>::T* a, bool quad, int B, int x, int y, int z) {
+    long long i;
+    if (quad) i = 4ll * (((long long)z * B + min(y, B - 1)) * B + min(x, B - 1)) + (x == B) + 2 * (y == B);
+    else i = ((long long)z * (B + 1) + y) * (B + 1) + x;
+    if constexpr (DT == VOL_F16) return __half2float(a[i]);
+    else return (float)a[i];
+}
+
 // Value range of a slot (its brick plus apron, any layout): the render loop skips bricks whose
-// range the transfer function maps to zero opacity.
+// range the transfer function maps to zero opacity.  And per macro-cell (local voxels
+// [c M, c M + M] per axis: every corner a trilinear sample inside the cell reads) the span of TF
+// entries [lo, hi] a lookup there can touch: the entries of the coordinates of the cell's
+// smallest and largest value, widened by one entry on each side for the last-bit rounding of the
+// interpolation (floats may overshoot their corners by an ulp).  A cell holding a NaN, or one
+// whose range is not ordered, spans every entry.
 template <int DT>
 __global__ void __launch_bounds__(kThreads) k_slot_range(const typename Stored<DT>::T* __restrict__ atlas, VolDev vol,
-                                                         float2* range, const uint32_t* __restrict__ slots) {
+                                                         float2* range, uint16_t* cells,
+                                                         const uint32_t* __restrict__ slots) {
     __shared__ float s_lo[kThreads / 32], s_hi[kThreads / 32];
     const uint32_t slot = slots[blockIdx.x];
     if (slot == kInvalidSlot) return;
@@ -241,6 +266,30 @@ __global__ void __launch_bounds__(kThreads) k_slot_range(const typename Stored<D
             hi = fmaxf(hi, s_hi[w]);
         }
         range[slot] = make_float2(lo, hi);
+    }
+    if (!cells) return;
+    const int cb = vol.cbits, M = 1 << vol.cshift, CB = 1 << cb;
+    const int ncell = 1 << (3 * cb);
+    const bool quad = vol.quad != 0;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const int x0 = (c & (CB - 1)) * M, y0 = ((c >> cb) & (CB - 1)) * M, z0 = (c >> (2 * cb)) * M;
+        float clo = __int_as_float(0x7f800000), chi = -__int_as_float(0x7f800000);
+        bool nan = false;
+        for (int z = z0; z <= z0 + M; ++z)
+            for (int y = y0; y <= y0 + M; ++y)
+                for (int x = x0; x <= x0 + M; ++x) {
+                    const float v = slot_voxel<DT>(a, quad, B, x, y, z);
+                    nan |= v != v;
+                    clo = fminf(clo, v);
+                    chi = fmaxf(chi, v);
+                }
+        uint16_t span = 0xFF00u;  // entries 0 .. 255
+        if (!nan && clo <= chi) {
+            const int ilo = max((int)stored_coord<DT>(clo) - 1, 0);
+            const int ihi = min((int)stored_coord<DT>(chi) + 2, 255);
+            span = (uint16_t)(ilo | (ihi << 8));
+        }
+        cells[(unsigned long long)slot * ncell + c] = span;
     }
 }
 
@@ -331,16 +380,16 @@ cudaError_t launch_downsample(int dtype, const VolDev& vol, int level, const uin
     return cudaGetLastError();
 }
 
-cudaError_t launch_slot_range(int dtype, const VolDev& vol, float2* range, const uint32_t* slots, long long n,
-                              cudaStream_t s) {
+cudaError_t launch_slot_range(int dtype, const VolDev& vol, float2* range, uint16_t* cells, const uint32_t* slots,
+                              long long n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     for (long long i0 = 0; i0 < n; i0 += 1ll << 30) {
         const unsigned g = (unsigned)((n - i0) < (1ll << 30) ? (n - i0) : (1ll << 30));
         switch (dtype) {
-        case VOL_U8: k_slot_range<VOL_U8><<<g, kThreads, 0, s>>>((const uint8_t*)vol.atlas, vol, range, slots + i0); break;
-        case VOL_U16: k_slot_range<VOL_U16><<<g, kThreads, 0, s>>>((const uint16_t*)vol.atlas, vol, range, slots + i0); break;
-        case VOL_F16: k_slot_range<VOL_F16><<<g, kThreads, 0, s>>>((const __half*)vol.atlas, vol, range, slots + i0); break;
-        case VOL_F32: k_slot_range<VOL_F32><<<g, kThreads, 0, s>>>((const float*)vol.atlas, vol, range, slots + i0); break;
+        case VOL_U8: k_slot_range<VOL_U8><<<g, kThreads, 0, s>>>((const uint8_t*)vol.atlas, vol, range, cells, slots + i0); break;
+        case VOL_U16: k_slot_range<VOL_U16><<<g, kThreads, 0, s>>>((const uint16_t*)vol.atlas, vol, range, cells, slots + i0); break;
+        case VOL_F16: k_slot_range<VOL_F16><<<g, kThreads, 0, s>>>((const __half*)vol.atlas, vol, range, cells, slots + i0); break;
+        case VOL_F32: k_slot_range<VOL_F32><<<g, kThreads, 0, s>>>((const float*)vol.atlas, vol, range, cells, slots + i0); break;
         default: return cudaErrorInvalidValue;
         }
     }

@@ -354,6 +354,85 @@ __device__ __forceinline__ bool brick_below_coord(float2 rng, float kept) {
     return coord_range<DT>(rng).y <= kept;
 }
 
+// Macro-cell index of a clamped voxel inside its brick (cells of 2^cs voxels, 2^cb per axis).
+__device__ __forceinline__ uint32_t cell_of(const int i0[3], int bmask, int cs, int cb) {
+    return ((uint32_t)((i0[2] & bmask) >> cs) << (2 * cb)) | ((uint32_t)((i0[1] & bmask) >> cs) << cb) |
+           (uint32_t)((i0[0] & bmask) >> cs);
+}
+
+// A macro-cell whose TF-entry span is [span & 255, span >> 8] holds no sample that changes the
+// lane's state (the per-cell form of brick_empty / brick_below_alpha / brick_below_coord; the
+// span already carries the one-entry margins).  MIP: every coordinate in the cell is below the
+// span's upper entry.
+template <int MODE>
+__device__ __forceinline__ bool span_skippable(uint32_t span, const int* s_apre, const float* s_amx, float kept) {
+    const int lo = (int)(span & 255u), hi = (int)(span >> 8);
+    if (MODE == kMop) {
+        const float b = tf_alpha_max(s_amx, lo, hi);
+        return fmaf(fabsf(b), 2.4e-7f, b) <= kept;
+    }
+    if (MODE == kMip) return (float)hi <= kept;
+    return s_apre[hi + 1] - s_apre[lo] == 0;
+}
+
+// The brick form of the same test, from the slot's value range.
+template <int DT, int MODE>
+__device__ __forceinline__ bool brick_skippable(float2 rng, const int* s_apre, const float* s_amx, float kept) {
+    if (MODE == kMop) return brick_below_alpha<DT>(rng, s_amx, kept);
+    if (MODE == kMip) return brick_below_coord<DT>(rng, kept);
+    return brick_empty<DT>(rng, s_apre);
+}
+
+// Decision record of sample k for the block searches below: its level and clamped voxel.
+struct SampleKey {
+    bool valid;  // t_k < t1
+    int l;
+    Resolved R;
+};
+
+template <bool LOD>
+__device__ __forceinline__ SampleKey sample_key(int k, const float o[3], const float d[3], float t0, float t1, float step,
+                                                float lodscale, int bias, int nlev, const LevelDev* s_lv, int bshift,
+                                                int bmask, int row) {
+    SampleKey K;
+    const float t = __fadd_rn(t0, __fmul_rn((float)k, step));
+    K.valid = t < t1;
+    const float p[3] = {__fadd_rn(o[0], __fmul_rn(t, d[0])), __fadd_rn(o[1], __fmul_rn(t, d[1])),
+                        __fadd_rn(o[2], __fmul_rn(t, d[2]))};
+    K.l = LOD ? lod_level(t, lodscale, bias, nlev) : 0;
+    resolve(s_lv[K.l], bshift, bmask, row, p, K.R);
+    return K;
+}
+
+// Estimated last sample of the ray in the block of sample k (key K): the block is the level and
+// the voxel index >> shift on every axis (shift = log2 B: the brick; log2 M: the macro-cell).
+// Samples of one block are contiguous along a ray (level and clamped voxel indices are monotone
+// in t), and the block ends at its exit face or at the next LOD switch, whichever comes first.
+// Reciprocals are approximate: the caller verifies the estimate with the exact decision
+// arithmetic (the batch that starts at the estimate checks that its first sample is in the block).
+template <bool LOD>
+__device__ __forceinline__ int block_end_estimate(int k, const SampleKey& K, int shift, const float o[3],
+                                                  const float d[3], float t0, float t1, float step, float lodscale,
+                                                  int bias, int nlev, const LevelDev* s_lv) {
+    const LevelDev& L = s_lv[K.l];
+    float te = t1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int g = K.R.i0[a] >> shift;
+        if (d[a] > 0.0f && ((g + 1) << shift) <= L.D[a] - 1)
+            te = fminf(te, __fdividef(((float)((g + 1) << shift) + 0.5f) * L.ir[a] - o[a], d[a]));
+        else if (d[a] < 0.0f && g > 0)
+            te = fminf(te, __fdividef(((float)(g << shift) + 0.5f) * L.ir[a] - o[a], d[a]));
+    }
+    if (LOD && K.l < nlev - 1) {  // the level rises once t * lodscale reaches 2^(l + 1 - bias)
+        const int e = K.l + 1 - bias;
+        if (e <= -126) te = 0.0f;  // (only at t = 0: no jump)
+        else if (e < 127) te = fminf(te, __fdividef(__int_as_float((e + 127) << 23), lodscale));
+    }
+    const float est = __fdividef(te - t0, step);
+    return est > (float)k && est < 16777216.0f ? (int)est : k;
+}
+
 // Last sample of the ray that resolves to the same page-table entry (level and brick) as
 // sample k_start: estimated from the brick's exit faces (and the next LOD switch), then fixed
 // by the exact decision arithmetic.  Samples with one page-table entry are contiguous along a
@@ -687,11 +766,17 @@ __device__ __forceinline__ float next_t_level_step(float t, float step, int l) {
 // on level l, whose opacity is corrected to that longer step; t of the lane's next sample is
 // kept in tcur (and in a suspended ray's record).
 // SP: three-level sparse page table (emission/absorption, uniform steps, no empty-space jumps).
-template <int DT, bool LOD, int MODE, int BS, bool Q, bool LS = false, bool SP = false>
+// ES: empty-space skipping: when a batch meets a sample in a brick or macro-cell that cannot change
+// the lane's state (zero TF opacity over its value range; for MOP/MIP no opacity / coordinate
+// above the kept one), the lane's next batch starts at that block's estimated last sample instead;
+// the batch's first decision verifies the estimate exactly (same level and block), so a lane
+// crosses a whole block per iteration in step with the other lanes of its warp.
+template <int DT, bool LOD, int MODE, int BS, bool Q, bool LS = false, bool SP = false, bool ES = false>
 __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const __grid_constant__ RenderDev P) {
     static_assert(!LS || MODE == kDvr, "level-scaled sampling is for emission/absorption without gradients");
     static_assert(!SP || (MODE == kDvr && !LS), "the sparse page table variant is for emission/absorption");
-    constexpr int kBatch = LS ? kBatchLevelStep : kBatchDefault;
+    static_assert(!ES || (!LS && !SP), "empty-space skipping assumes uniform steps and the flat page table");
+    constexpr int kBatch = (LS || ES) ? kBatchLevelStep : kBatchDefault;
     constexpr bool GRAD = MODE == kDvrGrad;
     constexpr float kT0 = MODE == kMop ? 0.0f : (MODE == kMip ? -1.0f : 1.0f);
     __shared__ float4 s_tf[256];
@@ -748,7 +833,14 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
     float C0 = 0, C1 = 0, C2 = 0, T = kT0;
     float tcur = 0.0f;  // LS: depth of sample k
     uint32_t cur_pti = kInvalidSlot;
-    bool cur_empty = false;  // the brick of cur_pti has zero opacity everywhere
+    // ES: the brick of cur_pti cannot change the lane's state; the macro-cell last tested and
+    // whether it cannot
+    bool cur_bskip = false, cur_cskip = false;
+    uint32_t cur_cell = kInvalidSlot;
+    const unsigned long long ncells = ES ? 1ull << (3 * P.vol.cbits) : 0ull;
+    // ES: sample k lies in a block (brick when sk_brick, else macro-cell) that cannot change the
+    // lane's state
+    bool sk = false, sk_brick = false;
     const int nlev = P.vol.nlevels;
     int cur_l = 0;
     LvReg L = load_lv(s_lv[0]);
@@ -823,6 +915,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         k = k0; C0 = c0; C1 = c1; C2 = c2; T = tt;
                         if (LS) tcur = P.resume ? tk0 : R.t0;
                         cur_pti = kInvalidSlot;
+                        sk = false;
                     } else {
                         P.out[ray] = P.bg;
                         if (P.nsamp) P.nsamp[ray] = 0;
@@ -846,39 +939,86 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 int lv[kBatch];        // LS: their levels
                 uint32_t sub[kBatch];  // SP: brick position inside the middle and leaf pages
                 tv[0] = tcur;
-                // sample indices as floats: (float)(k + j) = (float)k + j exactly, since the host
-                // keeps every index of a ray below 2^24 (kMaxSamplesPerRay)
-                const float kf = (float)k;
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const float t = LS ? tv[j] : __fadd_rn(t0, __fmul_rn(__fadd_rn(kf, (float)j), step));
-                    if (!(t < t1) && nvalid == kBatch) nvalid = j;
-                    const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
-                                        __fadd_rn(o2, __fmul_rn(t, d2))};
-                    if (LOD) {
-                        const int l = lod_level(t, lodscale, P.lod_bias, nlev);
-                        if (l != cur_l) {
-                            cur_l = l;
-                            L = load_lv(s_lv[l]);
-                        }
-                    }
-                    if (LS) {
-                        lv[j] = LOD ? cur_l : 0;
-                        tv[j + 1] = next_t_level_step(t, step, lv[j]);
-                    }
-                    Resolved R;
-                    resolve_reg(L, bshift, bmask, row, p, R);
-                    pti[j] = R.pti;
-                    if (SP) {
-                        const int h0 = R.i0[0] >> bshift, h1 = R.i0[1] >> bshift, h2 = R.i0[2] >> bshift;
-                        pti[j] = sparse_top(L, h0, h1, h2);
-                        sub[j] = sparse_sub(h0, h1, h2);
-                    }
-                    loc[j] = R.local;
-                    wgt[j][0] = R.w[0];
-                    wgt[j][1] = R.w[1];
-                    wgt[j][2] = R.w[2];
+                // ES: a lane whose sample k lies in a block that cannot change its state starts the
+                // batch at the block's estimated last sample kb (verified below by sample kb)
+                int kb = k;
+                int key_l = 0, key_g[3] = {0, 0, 0}, key_shift = 0;  // ES: the block of sample k
+                if (ES && sk) {
+                    const float o3[3] = {o0, o1, o2}, d3[3] = {d0, d1, d2};
+                    const SampleKey K = sample_key<LOD>(k, o3, d3, t0, t1, step, lodscale, P.lod_bias, nlev, s_lv,
+                                                        bshift, bmask, row);
+                    key_shift = sk_brick ? bshift : P.vol.cshift;
+                    key_l = K.l;
+                    key_g[0] = K.R.i0[0] >> key_shift;
+                    key_g[1] = K.R.i0[1] >> key_shift;
+                    key_g[2] = K.R.i0[2] >> key_shift;
+                    // one sample short of the estimate: the batch then lands inside the block, and the
+                    // block's samples at its start are passed over below
+                    kb = max(k, block_end_estimate<LOD>(k, K, key_shift, o3, d3, t0, t1, step, lodscale, P.lod_bias,
+                                                        nlev, s_lv) - 1);
                 }
+                // ES: sample kb must lie in the block of sample k; then every sample in between does
+                // (a block's samples are contiguous along the ray) and composites nothing.  When it
+                // does not (the estimate overshot), the decisions are taken again from k.
+                for (;;) {
+                    nvalid = kBatch;
+                    bool in_block = true;  // ES: sample kb lies in the block of sample k
+                    // sample indices as floats: (float)(k + j) = (float)k + j exactly, since the host
+                    // keeps every index of a ray below 2^24 (kMaxSamplesPerRay)
+                    const float kf = (float)kb;
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        const float t = LS ? tv[j] : __fadd_rn(t0, __fmul_rn(__fadd_rn(kf, (float)j), step));
+                        if (!(t < t1) && nvalid == kBatch) nvalid = j;
+                        const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
+                                            __fadd_rn(o2, __fmul_rn(t, d2))};
+                        if (LOD) {
+                            const int l = lod_level(t, lodscale, P.lod_bias, nlev);
+                            if (l != cur_l) {
+                                cur_l = l;
+                                L = load_lv(s_lv[l]);
+                            }
+                        }
+                        if (LS) {
+                            lv[j] = LOD ? cur_l : 0;
+                            tv[j + 1] = next_t_level_step(t, step, lv[j]);
+                        }
+                        Resolved R;
+                        resolve_reg(L, bshift, bmask, row, p, R);
+                        pti[j] = R.pti;
+                        if (ES && j == 0)
+                            in_block = (LOD ? cur_l : 0) == key_l && (R.i0[0] >> key_shift) == key_g[0] &&
+                                       (R.i0[1] >> key_shift) == key_g[1] && (R.i0[2] >> key_shift) == key_g[2];
+                        if (SP) {
+                            const int h0 = R.i0[0] >> bshift, h1 = R.i0[1] >> bshift, h2 = R.i0[2] >> bshift;
+                            pti[j] = sparse_top(L, h0, h1, h2);
+                            sub[j] = sparse_sub(h0, h1, h2);
+                        }
+                        // ES: the sample's macro-cell in bits 22..30 (local offsets stay below 2^22)
+                        loc[j] = ES ? (R.local | (cell_of(R.i0, bmask, P.vol.cshift, P.vol.cbits) << 22)) : R.local;
+                        wgt[j][0] = R.w[0];
+                        wgt[j][1] = R.w[1];
+                        wgt[j][2] = R.w[2];
+                    }
+                    if (!(ES && sk && kb > k) || (nvalid > 0 && in_block)) break;
+                    kb = k;
+                }
+                const bool in_skip = ES && sk;
+                if (ES && in_skip && kb > k) {
+                    if (GRAD) {
+                        const int cs = P.ckpt_shift;
+                        for (int kk = ((k + (1 << cs) - 1) >> cs) << cs; kk < kb; kk += 1 << cs)
+                            if (kk > 0) P.ckpt[(long long)((kk >> cs) - 1) * P.nrays + ray] = T;
+                    }
+                    {  // count the samples jumped over (one atomic per warp)
+                        const unsigned m = __activemask();
+                        const unsigned long long tot = __reduce_add_sync(m, (unsigned)(kb - k));
+                        if ((int)lane == __ffs(m) - 1)
+                            atomicAdd(reinterpret_cast<unsigned long long*>(P.counters + kSkipped), tot);
+                    }
+                    k = kb;
+                }
+                sk = false;
                 // (b) page-table lookups, all issued together (samples past the exit read entry 0)
                 uint32_t slot[kBatch];
                 if (SP) {
@@ -909,25 +1049,38 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         miss_at = j;
                         miss_pti = pti[j];
                     }
-                // usage stamps (one store per brick change) and empty-brick test
+                // usage stamps (one store per brick change); ES: the first sample in a brick or
+                // macro-cell that cannot change the lane's state
                 int empty_at = kBatch;
-                uint32_t empty_pti = 0u;
+                bool empty_brick = false;
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
                     if (j < nvalid && j < miss_at) {
                         if (pti[j] != cur_pti) {
                             cur_pti = pti[j];
                             if (P.last_used) P.last_used[slot[j]] = P.frame;
-                            if (!LS && !SP && P.skip_empty) {
-                                const float2 rng = __ldg(P.vol.range + slot[j]);
-                                if (MODE == kMop) cur_empty = brick_below_alpha<DT>(rng, s_amx, T);
-                                else if (MODE == kMip) cur_empty = brick_below_coord<DT>(rng, T);
-                                else cur_empty = brick_empty<DT>(rng, s_apre);
+                            if (ES) {
+                                cur_bskip = brick_skippable<DT, MODE>(__ldg(P.vol.range + slot[j]), s_apre, s_amx, T);
+                                cur_cell = kInvalidSlot;
                             }
                         }
-                        if (cur_empty && empty_at == kBatch) {
-                            empty_at = j;
-                            empty_pti = pti[j];
+                        // (a skipping lane's leading samples in the block it jumped into are passed over)
+                        const bool lead = in_skip && pti[j] == pti[0] && (sk_brick || (loc[j] >> 22) == (loc[0] >> 22));
+                        if (ES && empty_at == kBatch && !lead) {
+                            bool e = cur_bskip;
+                            if (!e) {
+                                const uint32_t c = loc[j] >> 22;
+                                if (c != cur_cell) {
+                                    cur_cell = c;
+                                    cur_cskip = span_skippable<MODE>(__ldg(P.vol.cells + slot[j] * ncells + c), s_apre,
+                                                                     s_amx, T);
+                                }
+                                e = cur_cskip;
+                            }
+                            if (e) {
+                                empty_at = j;
+                                empty_brick = cur_bskip;
+                            }
                         }
                     }
                 }
@@ -936,7 +1089,8 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
                     const bool use = j < nvalid && j < miss_at;
-                    const unsigned long long base = use ? (unsigned long long)slot[j] * slot_stride + loc[j] : 0ull;
+                    const unsigned long long base =
+                        use ? (unsigned long long)slot[j] * slot_stride + (ES ? (loc[j] & 0x3FFFFFu) : loc[j]) : 0ull;
                     val[j] = sample_value<DT, BS, Q>(P.vol.atlas, base, B1, wgt[j]);
                 }
                 const int stop = min(min(nvalid, miss_at), empty_at);
@@ -988,7 +1142,8 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         request_brick(P, miss_pti + 1u);
                     }
                     cur_pti = SP ? kInvalidSlot : miss_pti;
-                    cur_empty = false;
+                    cur_bskip = false;
+                    cur_cell = kInvalidSlot;
                     const float tk = LS ? tcur : __fadd_rn(t0, __fmul_rn((float)k, step));
                     const int lk = LOD ? lod_level(tk, lodscale, P.lod_bias, nlev) : 0;
                     const Fallback F = preview_fallback<LOD, SP>(P.vol.pt, tk, o0, o1, o2, d0, d1, d2, lodscale,
@@ -1006,25 +1161,11 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     if ((int)lane == __ffs(m) - 1) atomicAdd(&P.counters[kPreview], (unsigned)__popc(m));
                 }
                 if (!fin && !fell && nvalid < kBatch && nvalid <= miss_at && nvalid <= empty_at) fin = true;  // left the volume
-                if (!fin && !fell && empty_at < kBatch && empty_at < miss_at && empty_at < nvalid) {
-                    // sample k is in a brick of zero opacity: every sample up to the brick's last
-                    // composites nothing, so continue after it
-                    const float o3[3] = {o0, o1, o2}, d3[3] = {d0, d1, d2};
-                    const int klast = brick_last_sample<LOD>(k, empty_pti, o3, d3, t0, t1, step, lodscale,
-                                                             P.lod_bias, nlev, s_lv, bshift, bmask, row, B1 - 1);
-                    {  // count the samples jumped over (one atomic per warp)
-                        const unsigned long long nskip = (unsigned long long)(klast + 1 - k);
-                        const unsigned m = __activemask();
-                        const unsigned long long tot = __reduce_add_sync(m, (unsigned)nskip);
-                        if ((int)lane == __ffs(m) - 1)
-                            atomicAdd(reinterpret_cast<unsigned long long*>(P.counters + kSkipped), tot);
-                    }
-                    if (GRAD) {
-                        const int cs = P.ckpt_shift;
-                        for (int kk = ((k + (1 << cs) - 1) >> cs) << cs; kk <= klast; kk += 1 << cs)
-                            if (kk > 0) P.ckpt[(long long)((kk >> cs) - 1) * P.nrays + ray] = T;
-                    }
-                    k = klast + 1;
+                if (ES && !fin && !fell && empty_at < kBatch && empty_at < miss_at && empty_at < nvalid) {
+                    // sample k lies in a brick or macro-cell that cannot change the state: the next
+                    // batch starts at the block's end
+                    sk = true;
+                    sk_brick = empty_brick;
                 } else if (fin) {
                     const float4 bg = P.bg;
                     if (MODE == kMop || MODE == kMip) {

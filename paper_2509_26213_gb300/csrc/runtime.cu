@@ -256,6 +256,8 @@ struct vol_s {
     bool order_ready = false;
     int* order_buckets = nullptr;          // 64 ints: bucket counts and fill cursors
     float2* range = nullptr;               // per slot: min and max stored value
+    uint16_t* cells = nullptr;             // per slot: TF-entry span of each macro-cell
+    int cbits = 0, cshift = 0;             // log2 cells per brick axis, log2 cell edge
 
     vol_stats stats{};
     int64_t allocations = 0;  // device and pinned-host allocations since vol_create
@@ -307,11 +309,15 @@ VolDev vol_dev(const vol_t v) {
     d.nlevels = v->L;
     d.pt = v->pt;
     d.range = v->range;
+    d.cells = v->cells;
+    d.cbits = v->cbits;
+    d.cshift = v->cshift;
     for (int l = 0; l < v->L; ++l) {
         for (int a = 0; a < 3; ++a) {
             d.lv[l].D[a] = (int)v->lay.level_dims[l][a];
             d.lv[l].nb[a] = (int)v->lay.level_bricks[l][a];
             d.lv[l].r[a] = (float)v->lay.level_dims[l][a] / (float)v->lay.level_dims[0][a];
+            d.lv[l].ir[a] = (float)((double)v->lay.level_dims[0][a] / (double)v->lay.level_dims[l][a]);
         }
         d.lv[l].pt_off = (uint32_t)v->lay.level_pt_offset[l];
         for (int a = 0; a < 3; ++a) {
@@ -787,7 +793,7 @@ int load_requests(vol_t v) {
         CK(v, cudaMemcpyAsync(v->stage_slots_dev, slots.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, v->stream));
         CK(v, launch_upload_bricks(v->dtype, v->prov_dtype, v->stage_dev, vol_dev(v), v->stage_slots_dev, (long long)n,
                                    v->stream));
-        CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, v->stage_slots_dev, (long long)n, v->stream));
+        CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, v->cells, v->stage_slots_dev, (long long)n, v->stream));
         v->stats.launches += 2;
         if (int rc = flush_pt_updates(v)) return rc;
         CK(v, cudaStreamSynchronize(v->stream));  // the pinned stage is reused by the next batch
@@ -1046,7 +1052,7 @@ int ovl_publish(vol_t v, int* published) {
     const size_t bb = R.brick_bytes;
     CK(v, launch_upload_bricks(v->dtype, v->prov_dtype, R.host_dev + (size_t)st * bb, vol_dev(v), R.slots_dev + st,
                                (long long)n, v->stream));
-    CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, R.slots_dev + st, (long long)n, v->stream));
+    CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, v->cells, R.slots_dev + st, (long long)n, v->stream));
     CK(v, launch_pt_update(v->pt, R.ptis_dev + st, R.slots_dev + st, n, v->stream));
     v->stats.launches += 3;
     cudaEvent_t ev = nullptr;
@@ -1218,6 +1224,11 @@ int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t
     if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->aux, sizeof(unsigned) * 4);
     if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->order_buckets, sizeof(int) * 64);
     if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->range, sizeof(float2) * (size_t)lay.nslots);
+    // macro-cells for empty-space skipping: 8 per brick axis (B per axis for B < 8), 2 bytes each
+    v->cbits = std::min(v->bshift, 3);
+    v->cshift = v->bshift - v->cbits;
+    if (e == cudaSuccess)
+        e = dev_alloc(v, (void**)&v->cells, sizeof(uint16_t) * ((size_t)1 << (3 * v->cbits)) * (size_t)lay.nslots);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->pt, 0xFF, sizeof(uint32_t) * pt_entries, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->last_used, 0, sizeof(unsigned) * (size_t)lay.nslots, v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->aux, 0, sizeof(unsigned) * 4, v->stream);
@@ -1260,7 +1271,7 @@ void vol_destroy(vol_t v) {
     else cudaDeviceSynchronize();
     void* bufs[] = {v->atlas, v->pt, v->last_used, v->counters, v->aux, v->upd_dev, v->views_dev, v->req_table,
                     v->req_list, v->susp[0], v->susp[1], v->ckpt, v->ray_n, v->stage_dev, v->stage_slots_dev,
-                    v->tile_cost, v->tile_order, v->order_buckets, v->range, v->dlev_buf, v->req_table64,
+                    v->tile_cost, v->tile_order, v->order_buckets, v->range, v->cells, v->dlev_buf, v->req_table64,
                     v->req_list64};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -1342,7 +1353,7 @@ int vol_upload_level(vol_t v, int level, const void* src, int src_dtype, int src
     }
     cudaError_t e = cudaMemcpyAsync(dslots, slots.data(), sizeof(uint32_t) * (size_t)nb, cudaMemcpyHostToDevice, v->stream);
     if (e == cudaSuccess) e = launch_upload_level(v->dtype, src_dtype, dsrc, vol_dev(v), level, dslots, nb, v->stream);
-    if (e == cudaSuccess) e = launch_slot_range(v->dtype, vol_dev(v), v->range, dslots, nb, v->stream);
+    if (e == cudaSuccess) e = launch_slot_range(v->dtype, vol_dev(v), v->range, v->cells, dslots, nb, v->stream);
     int rc = e == cudaSuccess ? flush_pt_updates(v) : cuda_fail(v, e, "upload_level kernel");
     cudaError_t e2 = cudaStreamSynchronize(v->stream);
     cudaFree(dslots);
@@ -1371,7 +1382,7 @@ int vol_upload_brick(vol_t v, int level, const int32_t brick[3], const void* src
     }
     CK(v, cudaMemcpyAsync(v->stage_slots_dev, &s, sizeof(uint32_t), cudaMemcpyHostToDevice, v->stream));
     CK(v, launch_upload_bricks(v->dtype, src_dtype, dsrc, vol_dev(v), v->stage_slots_dev, 1, v->stream));
-    CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, v->stage_slots_dev, 1, v->stream));
+    CK(v, launch_slot_range(v->dtype, vol_dev(v), v->range, v->cells, v->stage_slots_dev, 1, v->stream));
     v->stats.launches += 2;
     if (int rc = flush_pt_updates(v)) return rc;
     CK(v, cudaStreamSynchronize(v->stream));
@@ -1402,7 +1413,7 @@ int vol_build_lod(vol_t v, int from_level) {
         int rc = VOL_OK;
         if (e == cudaSuccess) rc = flush_pt_updates(v);  // the source level's entries must be live
         if (e == cudaSuccess && !rc) e = launch_downsample(v->dtype, vol_dev(v), l, dslots, nb, v->aux, v->stream);
-        if (e == cudaSuccess && !rc) e = launch_slot_range(v->dtype, vol_dev(v), v->range, dslots, nb, v->stream);
+        if (e == cudaSuccess && !rc) e = launch_slot_range(v->dtype, vol_dev(v), v->range, v->cells, dslots, nb, v->stream);
         cudaError_t e2 = cudaStreamSynchronize(v->stream);
         cudaFree(dslots);
         if (rc) return rc;

@@ -98,3 +98,58 @@ def test_skip_with_bricks_on_demand(P):
         vol.close()
     for a, b in zip(*imgs):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("store,brick,layout", [("u16", 64, "quad"), ("f16", 32, "compact"), ("u8", 32, "quad"),
+                                               ("f32", 64, "compact")])
+def test_macro_cell_skip_is_exact(P, orc, store, brick, layout):
+    """Noise + spheres under a TF of narrow opacity peaks: no brick is empty, but many 8^3-cell
+    blocks are.  Images and sample counts are bit-identical with the skipping, which jumps over
+    a measured share of the samples; MOP and MIP likewise; and the image is the oracle's."""
+    D = (200, 176, 160)
+    raw16 = synth.noise_spheres(D, 21, octaves=5, period0=48.0, nspheres=30, radius=(4.0, 30.0), value=(0.3, 1.0))
+    src = "u16" if store in ("u16", "f16", "f32") else "u8"
+    raw = raw16 if src == "u16" else (raw16 >> 8).astype(np.uint8)
+    vol = P.Volume(D, store, brick, 3, layout=layout)
+    vol.upload_level(0, raw, src)
+    vol.build_lod(0)
+    tf = synth.tf_peaks(21)
+    tfd = torch.from_numpy(tf).cuda()
+    cams = [synth.seeded_orbit(D, 120, 90, 21, view=v) for v in range(2)] + \
+           [synth.look_at((90.0, 70.0, 60.0), (150.0, 120.0, 110.0), 80, 60, fov_deg=70.0)]
+    params = {"lod_mode": 1}
+    a, na, b, nb = both(vol, cams, tfd, params)
+    skipped = vol.stats()["skipped_samples"]
+    np.testing.assert_array_equal(b, a)
+    np.testing.assert_array_equal(nb, na)
+    assert skipped > 0.05 * na.sum(), (skipped, na.sum())
+    for mode in ("mop", "mip"):
+        pm = dict(params, composite=mode)
+        a2, na2, b2, nb2 = both(vol, cams, tfd, pm)
+        np.testing.assert_array_equal(b2, a2)
+        np.testing.assert_array_equal(nb2, na2)
+    ovol = orc.Volume(store_levels(orc, raw, src, store, 3), store, brick)
+    ref = orc.render(ovol, cams[0], tf, params, amb=AMB)
+    n0 = cams[0]["w"] * cams[0]["h"]
+    err, bad, _ = compare(b[:n0], ref, 2e-3 if store in ("u16", "f16") else TOL_FP32)
+    assert len(bad) == 0, err
+    assert np.all((nb[:n0] == ref["n"]) | (ref["amb"] & (nb[:n0] == ref["alt_n"])))
+
+
+def test_skip_counts_add_up(P):
+    """Composited plus jumped-over samples: every sample a ray passes, with and without skipping."""
+    D = (128, 128, 128)
+    raw = synth.noise_spheres(D, 5, octaves=4, period0=32.0, nspheres=10, radius=(4.0, 20.0), value=(0.3, 1.0))
+    vol = P.Volume(D, "u16", 32, 1)
+    vol.upload_level(0, raw, "u16")
+    tf = synth.tf_peaks(5)
+    tfd = torch.from_numpy(tf).cuda()
+    cam = synth.seeded_orbit(D, 128, 128, 5)
+    # MIP visits samples to the exit (or to the largest coordinate): many fall in cells below
+    # the kept coordinate
+    _, n_all = vol.render(cam, tfd, {"composite": "mip"}, nsamples=True)
+    _, n_skip = vol.render(cam, tfd, {"composite": "mip", "flags": SKIP}, nsamples=True)
+    torch.cuda.synchronize()
+    st = vol.stats()
+    np.testing.assert_array_equal(n_all.cpu().numpy(), n_skip.cpu().numpy())
+    assert 0 < st["skipped_samples"] < int(n_all.sum().item())
