@@ -107,6 +107,13 @@ typedef struct {
  * recomputing it forward within a 32-sample segment.  The gradients equal the checkpointed ones
  * up to the order of the atomic additions; it exists to test that recompute. */
 #define VOL_RENDER_CKPT_ALL 64u
+/* With VOL_RENDER_GRAD: the render keeps every sample's interpolated value (4 bytes per sample,
+ * room for the longest ray's samples for every ray), and vol_render_backward() recomputes the
+ * transmittance of a segment from its checkpoint and these values instead of interpolating
+ * them again from the bricks; the gradients are the same.  This flag turns the value tape off
+ * (the adjoint then interpolates again; it is also off when its memory cannot be allocated, and
+ * with VOL_RENDER_CKPT_ALL). */
+#define VOL_RENDER_GRAD_RECOMPUTE 128u
 
 /* Compositing (vol_params.composite).
  * VOL_COMPOSITE_DVR: front-to-back emission/absorption with early termination (Sec. IV-A).

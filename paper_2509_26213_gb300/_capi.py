@@ -33,6 +33,7 @@ VOL_RENDER_PREVIEW = 8
 VOL_RENDER_LEVEL_STEP = 16
 VOL_RENDER_NO_PREFETCH = 32
 VOL_RENDER_CKPT_ALL = 64
+VOL_RENDER_GRAD_RECOMPUTE = 128
 VOL_COMPOSITE_DVR, VOL_COMPOSITE_MOP, VOL_COMPOSITE_MIP = 0, 1, 2
 COMPOSITES = {"dvr": VOL_COMPOSITE_DVR, "mop": VOL_COMPOSITE_MOP, "mip": VOL_COMPOSITE_MIP}
 VOL_LAYOUT_COMPACT = 1

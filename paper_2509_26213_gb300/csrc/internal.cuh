@@ -130,6 +130,9 @@ struct RenderDev {
     long long nrays;
     int ckpt_shift;
     int* ray_n;
+    // value tape (NULL: none): the interpolated value of sample k of a ray at
+    // [(k / 32) * nrays + ray] * 32 + k % 32, for the adjoint's transmittance recompute
+    float* tape;
     // scheduling: work item i of a fresh pass renders tile tile_order[i] (NULL: tile i);
     // every finished ray raises tile_cost[its tile] to its sample count: the tile's longest ray
     // (NULL: not recorded)
@@ -141,7 +144,7 @@ struct BackwardDev {
     VolDev vol;
     const ViewDev* views;
     int nviews;
-    int nwork;
+    int nwork;          // work items: 32-ray parts of the tiles
     int tile_w, tile_h;
     const float4* tf;
     float step;
@@ -154,6 +157,7 @@ struct BackwardDev {
     unsigned* counters;
     const float* ckpt;
     int ckpt_shift;         // checkpoint spacing 2^ckpt_shift samples (0..kCkptShift)
+    const float* tape;      // the forward's sample values (RenderDev::tape layout), or NULL
     long long nrays;
     const int* ray_n;
     const int* tile_order;  // longest-ray-first order of the tiles (NULL: tile i)
@@ -191,7 +195,7 @@ const void* pick_render_skip_projection(int dtype, int brick, bool quad, bool lo
 // order[] = tiles sorted by descending log2 bucket of cost[] (longest ray first); zeroes cost[].
 // buckets: 64 ints of device scratch.
 cudaError_t launch_tile_order(int* cost, int* order, int ntiles, int* buckets, cudaStream_t s);
-int backward_blocks_per_sm(int dtype, bool lod);
+int backward_blocks_per_sm(int dtype, bool lod, bool tape);
 
 // ---- launchers (kernels_volume.cu) ----
 // Write every brick of a dense level (src of src_dtype) into atlas slots.

@@ -69,16 +69,20 @@ constexpr int kBwdBatch = VOLRC_BWD_BATCH;
 constexpr int kBwdThreads = VOLRC_BWD_THREADS;
 constexpr int kBwdMinBlocks = VOLRC_BWD_MINB;
 
-// Adjoint, warp-synchronous by checkpoint segment: in each round every lane holding a ray
-// processes one segment of it (samples 32 s .. 32 s + 31, the last one partial), first
-// forward -- transmittance from the segment's checkpoint and the sample values into shared
-// memory, kBwdBatch samples at a time -- then in reverse, accumulating dL/dtf and dL/dvoxel.
+// Adjoint, warp-synchronous by checkpoint segment: a warp takes 32 rays (a ray tile, or a
+// 32-pixel part of it) and, round by round, processes segment s of every one of them that has
+// it (samples 32 s .. 32 s + 31, the last one partial), s descending from the longest ray's last
+// segment: first forward -- transmittance from the segment's checkpoint and the sample values
+// into shared memory, kBwdBatch samples at a time -- then in reverse, accumulating dL/dtf and
+// dL/dvoxel.  Neighbouring rays then sample neighbouring depths in each round, as in the forward
+// march, which keeps the gathers and the dL/dvoxel reductions of a round together in the cache.
 // (With checkpoints before every sample -- the store-all debug mode -- a segment is one sample
 // and its transmittance is read, not recomputed.)
-// Lanes take a new ray between rounds, so a warp waits only on segments, not on whole rays.
 // LOD: samples on footprint levels; the gradient of a level-l voxel goes to P.dlev[l], which
 // the host then carries down to level 0 through the box filter's adjoint.
-template <int DT, bool LOD>
+// TAPE: the segment's sample values are read from the forward's value tape instead of being
+// interpolated again from the bricks (the transmittance is recomputed from the checkpoint either way).
+template <int DT, bool LOD, bool TAPE>
 __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const __grid_constant__ BackwardDev P) {
     __shared__ float4 s_tf[256];
     __shared__ float s_dtf[1024];
@@ -93,7 +97,6 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
     using VT = typename Voxel<DT>::T;
     const VT* __restrict__ atlas = (const VT*)P.vol.atlas;
     const unsigned lane = threadIdx.x & 31;
-    const unsigned ltmask = (1u << lane) - 1;
     const int tid = threadIdx.x;
     const int bshift = P.vol.bshift, bmask = P.vol.bmask, B1 = P.vol.B1;
     const bool quad = P.vol.quad != 0;
@@ -114,71 +117,85 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
     int cell_mask = 0, cell_lvl = 0;
     float cacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 
-    // warp-uniform tile pool
-    int pool_next = 0, pool_cnt = 0, pool_view = 0, pool_x0 = 0, pool_y0 = 0;
-    bool queue_done = false;
-    // lane state
+    // lane state: the lane's ray, its sample count n and segment count nseg
     bool has = false;
     long long ray = 0;
     float o0 = 0, o1 = 0, o2 = 0, d0 = 0, d1 = 0, d2 = 0, t0 = 0, lodscale = 0;
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     float R0 = 0, R1 = 0, R2 = 0, R3 = 0;
-    int n = 0, s = 0;
+    int n = 0, nseg = 0;
+    // warp-uniform: the segment index every lane processes in this round, descending; each
+    // lane's rays sample the same depths as its neighbours' (adjacent pixels), so the gathers
+    // and the dL/dvoxel reductions of a round stay close together in the volume
+    int s = -1;
+    const int tile_px = P.tile_w * P.tile_h;
+    const int chunks = (tile_px + 31) >> 5;  // work items per tile: 32 rays each
 
     for (;;) {
-        // ---- give lanes without a ray the next rays of the tile queue
-        while (!queue_done) {
-            const unsigned need = __ballot_sync(kFull, !has);
-            if (!need) break;
-            if (pool_next >= pool_cnt) {
-                int item = 0;
-                if (lane == 0) item = (int)atomicAdd(&P.counters[kWork], 1u);
-                item = __shfl_sync(kFull, item, 0);
-                if (item >= P.nwork) {
-                    queue_done = true;
-                    break;
+        if (s < 0) {
+            // ---- the next 32 rays: one tile, or a 32-pixel part of a larger one
+            int item = 0;
+            if (lane == 0) item = (int)atomicAdd(&P.counters[kWork], 1u);
+            item = __shfl_sync(kFull, item, 0);
+            if (item >= P.nwork) break;
+            const int ti = item / chunks, part = item - ti * chunks;
+            const int tile = P.tile_order ? P.tile_order[ti] : ti;
+            const int v = find_view_tile(P.views, P.nviews, tile);
+            const ViewDev& V = P.views[v];
+            const int tl = tile - V.tile_off;
+            const int idx = part * 32 + (int)lane;
+            const int px = (tl % V.tiles_x) * P.tile_w + idx % P.tile_w;
+            const int py = (tl / V.tiles_x) * P.tile_h + idx / P.tile_w;
+            has = false;
+            nseg = 0;
+            if (idx < tile_px && px < V.w && py < V.h) {
+                ray = V.ray_off + (long long)py * V.w + px;
+                n = P.ray_n[ray];
+                if (n > 0) {
+                    Ray R;
+                    make_ray(V, P.vol.D0f, px, py, R);
+                    o0 = R.o[0]; o1 = R.o[1]; o2 = R.o[2];
+                    d0 = R.d[0]; d1 = R.d[1]; d2 = R.d[2];
+                    t0 = R.t0;
+                    lodscale = V.lodscale;
+                    g = P.drgba[ray];
+                    R0 = P.bg.x; R1 = P.bg.y; R2 = P.bg.z; R3 = P.bg.w;
+                    nseg = ((n - 1) >> P.ckpt_shift) + 1;
+                    has = true;
                 }
-                const int tile = P.tile_order ? P.tile_order[item] : item;
-                const int v = find_view_tile(P.views, P.nviews, tile);
-                const int tl = tile - P.views[v].tile_off;
-                pool_view = v;
-                pool_x0 = (tl % P.views[v].tiles_x) * P.tile_w;
-                pool_y0 = (tl / P.views[v].tiles_x) * P.tile_h;
-                pool_cnt = P.tile_w * P.tile_h;
-                pool_next = 0;
             }
-            const int idx = pool_next + __popc(need & ltmask);
-            pool_next = min(pool_cnt, pool_next + __popc(need));
-            if (!has && idx < pool_cnt) {
-                const ViewDev& V = P.views[pool_view];
-                const int px = pool_x0 + idx % P.tile_w, py = pool_y0 + idx / P.tile_w;
-                if (px < V.w && py < V.h) {
-                    ray = V.ray_off + (long long)py * V.w + px;
-                    n = P.ray_n[ray];
-                    if (n > 0) {
-                        Ray R;
-                        make_ray(V, P.vol.D0f, px, py, R);
-                        o0 = R.o[0]; o1 = R.o[1]; o2 = R.o[2];
-                        d0 = R.d[0]; d1 = R.d[1]; d2 = R.d[2];
-                        t0 = R.t0;
-                        lodscale = V.lodscale;
-                        g = P.drgba[ray];
-                        R0 = P.bg.x; R1 = P.bg.y; R2 = P.bg.z; R3 = P.bg.w;
-                        s = (n - 1) >> P.ckpt_shift;
-                        has = true;
+            s = __reduce_max_sync(kFull, nseg) - 1;
+            if (s < 0) continue;
+        }
+
+        // ---- one round: segment s (2^ckpt_shift <= kCkptEvery samples) of every lane's ray that has it
+        const bool seg = has && s < nseg;
+        const int k0 = s << P.ckpt_shift;
+        const int len = seg ? min(1 << P.ckpt_shift, n - k0) : 0;
+        float T = (seg && s > 0) ? P.ckpt[(long long)(s - 1) * P.nrays + ray] : 1.0f;
+        const int maxlen = __reduce_max_sync(kFull, len);
+        if (TAPE) {
+            // forward from the tape: 4 values per load (a segment's 32 values are 128 contiguous bytes)
+            const float* tp = P.tape + ((long long)s * P.nrays + (seg ? ray : 0)) * kCkptEvery;
+            for (int jb = 0; jb < maxlen; jb += 4) {
+                const float4 v4 = jb < len ? __ldg(reinterpret_cast<const float4*>(tp + jb)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (jb + u < len) {
+                        const float x = tf_coord<DT>(vv[u]);
+                        const int i = min((int)x, 254);
+                        const float wt = x - (float)i;
+                        const float al = fmaf(wt, s_tf[i + 1].w - s_tf[i].w, s_tf[i].w);
+                        s_T[jb + u][tid] = T;
+                        s_V[jb + u][tid] = vv[u];
+                        T = T * (1.0f - al);
                     }
                 }
             }
         }
-        if (!__ballot_sync(kFull, has)) break;
-
-        // ---- one round: segment s of every lane's ray (2^ckpt_shift <= kCkptEvery samples)
-        const int k0 = s << P.ckpt_shift;
-        const int len = has ? min(1 << P.ckpt_shift, n - k0) : 0;
-        float T = (has && s > 0) ? P.ckpt[(long long)(s - 1) * P.nrays + ray] : 1.0f;
-        const int maxlen = __reduce_max_sync(kFull, len);
         // forward: decisions, then the page-table lookups, then the gathers of kBwdBatch samples
-        for (int jb = 0; jb < maxlen; jb += kBwdBatch) {
+        for (int jb = 0; !TAPE && jb < maxlen; jb += kBwdBatch) {
             uint32_t pti[kBwdBatch], loc[kBwdBatch];
             float wv[kBwdBatch][3];
             const float kf = (float)(k0 + jb);  // + u stays exact: indices are below 2^24
@@ -230,18 +247,20 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
         float kf = (float)(k0 + maxlen - 1);  // (float)(k0 + j), stepped down exactly
         for (int j = maxlen - 1; j >= 0; --j, kf = __fsub_rn(kf, 1.0f)) {
             if (j < len) {
-                const float t = __fadd_rn(t0, __fmul_rn(kf, step));
-                const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
-                                    __fadd_rn(o2, __fmul_rn(t, d2))};
-                if (LOD) {
-                    const int l = lod_level(t, lodscale, P.lod_bias, nlev);
-                    if (l != cur_l) {
-                        cur_l = l;
-                        L0 = load_lv(s_lv[l]);
+                Resolved Q;  // the sample's voxel and weights: only dL/dvoxel needs them
+                if (P.dvox) {
+                    const float t = __fadd_rn(t0, __fmul_rn(kf, step));
+                    const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
+                                        __fadd_rn(o2, __fmul_rn(t, d2))};
+                    if (LOD) {
+                        const int l = lod_level(t, lodscale, P.lod_bias, nlev);
+                        if (l != cur_l) {
+                            cur_l = l;
+                            L0 = load_lv(s_lv[l]);
+                        }
                     }
+                    resolve_reg(L0, bshift, bmask, row, p, Q);
                 }
-                Resolved Q;
-                resolve_reg(L0, bshift, bmask, row, p, Q);
                 const float val = s_V[j][tid];
                 const float Tk = s_T[j][tid];
                 const float x = tf_coord<DT>(val);
@@ -316,7 +335,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                 R3 = fmaf(al, 1.0f - R3, R3);
             }
         }
-        if (has && --s < 0) has = false;
+        --s;
     }
     if (P.dtf) flush_dtf(s_dtf, acc_i, acc);
     if (P.dvox) flush_vox(P.dlev[cell_lvl], cell_cur, cell_mask, dim_x(cell_lvl), dim_y(cell_lvl), cacc);
@@ -442,18 +461,21 @@ const void* pick_render(int dtype, int brick, bool quad, bool lod, bool grad) {
     return nullptr;
 }
 
-template <bool LOD>
+template <bool LOD, bool TAPE>
 const void* pick_backward_l(int dtype) {
     switch (dtype) {
-    case VOL_U8: return (const void*)k_backward<VOL_U8, LOD>;
-    case VOL_U16: return (const void*)k_backward<VOL_U16, LOD>;
-    case VOL_F16: return (const void*)k_backward<VOL_F16, LOD>;
-    case VOL_F32: return (const void*)k_backward<VOL_F32, LOD>;
+    case VOL_U8: return (const void*)k_backward<VOL_U8, LOD, TAPE>;
+    case VOL_U16: return (const void*)k_backward<VOL_U16, LOD, TAPE>;
+    case VOL_F16: return (const void*)k_backward<VOL_F16, LOD, TAPE>;
+    case VOL_F32: return (const void*)k_backward<VOL_F32, LOD, TAPE>;
     }
     return nullptr;
 }
 
-const void* pick_backward(int dtype, bool lod) { return lod ? pick_backward_l<true>(dtype) : pick_backward_l<false>(dtype); }
+const void* pick_backward(int dtype, bool lod, bool tape) {
+    if (tape) return lod ? pick_backward_l<true, true>(dtype) : pick_backward_l<false, true>(dtype);
+    return lod ? pick_backward_l<true, false>(dtype) : pick_backward_l<false, false>(dtype);
+}
 
 }  // namespace
 
@@ -483,7 +505,7 @@ cudaError_t launch_render(int dtype, int mode, const RenderDev& p, int grid, cud
 }
 
 cudaError_t launch_backward(int dtype, const BackwardDev& p, int grid, cudaStream_t s) {
-    const void* fn = pick_backward(dtype, p.lod_mode != 0);
+    const void* fn = pick_backward(dtype, p.lod_mode != 0, p.tape != nullptr);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&p};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kBwdThreads), args, 0, s);
@@ -512,9 +534,9 @@ int render_blocks_per_sm(int dtype, bool grad) {
     return n > 0 ? n : 1;
 }
 
-int backward_blocks_per_sm(int dtype, bool lod) {
+int backward_blocks_per_sm(int dtype, bool lod, bool tape) {
     int n = 0;
-    const void* fn = pick_backward(dtype, lod);
+    const void* fn = pick_backward(dtype, lod, tape);
     if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBwdThreads, 0) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }

@@ -1,6 +1,6 @@
 // kernels_skip.cu -- variants of the forward kernel with empty-space skipping (the paper's
 // empty-space skipping, Sec. III-H "const chunk table" and the ES column of Sec. IV-A) for
-// emission/absorption compositing, with and without gradient checkpoints.  A sample in a
+// emission/absorption compositing.  A sample in a
 // brick or 8^3-cell block whose value range the transfer function maps to zero opacity jumps
 // to the end of the run of such blocks; the image does not change.
 #include "render_common.cuh"
@@ -36,8 +36,8 @@ const void* pick_m(int dtype, int brick, bool quad, bool lod) {
 }  // namespace
 
 const void* pick_render_skip(int dtype, int brick, bool quad, bool lod, int mode) {
+    // (gradient mode renders without skipping: the adjoint reads a value for every sample)
     if (mode == kDvr) return pick_m<kDvr>(dtype, brick, quad, lod);
-    if (mode == kDvrGrad) return pick_m<kDvrGrad>(dtype, brick, quad, lod);
     return nullptr;
 }
 

@@ -659,6 +659,20 @@ __device__ __forceinline__ void suspend_ray(const RenderDev& P, long long ray, i
     }
 }
 
+// Value tape (gradient mode): sample k of a ray at [(k / 32) * nrays + ray] * 32 + k % 32.
+__device__ __forceinline__ long long tape_at(long long nrays, long long ray, int k) {
+    return ((long long)(k >> kCkptShift) * nrays + ray) * kCkptEvery + (k & (kCkptEvery - 1));
+}
+
+// Writes the values of samples kfrom .. k-1 still held in the lane's staging group tb (tb.w the
+// value of sample k-1, tb.z of k-2, tb.y of k-3; samples before kfrom are not the lane's).
+__device__ __forceinline__ void tape_flush(float* tape, long long nrays, long long ray, int k, int kfrom, float4 tb) {
+    const int q = k & 3;
+    if (q >= 1 && k - 1 >= kfrom) tape[tape_at(nrays, ray, k - 1)] = tb.w;
+    if (q >= 2 && k - 2 >= kfrom) tape[tape_at(nrays, ray, k - 2)] = tb.z;
+    if (q >= 3 && k - 3 >= kfrom) tape[tape_at(nrays, ray, k - 3)] = tb.y;
+}
+
 // Samples per lane per loop iteration: their page-table lookups and gathers are issued together,
 // then composited in order (memory-level parallelism along one ray).
 #ifndef VOLRC_BATCH
@@ -832,6 +846,10 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
     int k = 0;
     float C0 = 0, C1 = 0, C2 = 0, T = kT0;
     float tcur = 0.0f;  // LS: depth of sample k
+    // GRAD with a value tape: the values of the current group of 4 aligned samples, and the first
+    // sample this lane composited of the ray (since its start or resumption)
+    float4 tb = make_float4(0.f, 0.f, 0.f, 0.f);
+    int tb_from = 0;
     uint32_t cur_pti = kInvalidSlot;
     // ES: the brick of cur_pti cannot change the lane's state; the macro-cell last tested and
     // whether it cannot
@@ -913,6 +931,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         t0 = R.t0; t1 = R.t1;
                         lodscale = P.views[view].lodscale;
                         k = k0; C0 = c0; C1 = c1; C2 = c2; T = tt;
+                        tb_from = k0;
                         if (LS) tcur = P.resume ? tk0 : R.t0;
                         cur_pti = kInvalidSlot;
                         sk = false;
@@ -1113,6 +1132,20 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         if (j < stop && !fin) {
                             if (GRAD && k > 0 && (k & ((1 << P.ckpt_shift) - 1)) == 0)
                                 P.ckpt[(long long)((k >> P.ckpt_shift) - 1) * P.nrays + ray] = T;
+                            if (GRAD && P.tape) {
+                                // the sample's value, for the adjoint's recompute of T: staged in groups
+                                // of 4 aligned samples, written 16 bytes at a time
+                                tb = make_float4(tb.y, tb.z, tb.w, val[j]);
+                                if ((k & 3) == 3) {
+                                    if (k - 3 >= tb_from) {
+                                        *reinterpret_cast<float4*>(P.tape + tape_at(P.nrays, ray, k - 3)) = tb;
+                                    } else {  // the group began before this lane took the ray over
+                                        if (k - 2 >= tb_from) P.tape[tape_at(P.nrays, ray, k - 2)] = tb.y;
+                                        if (k - 1 >= tb_from) P.tape[tape_at(P.nrays, ray, k - 1)] = tb.z;
+                                        P.tape[tape_at(P.nrays, ray, k)] = tb.w;
+                                    }
+                                }
+                            }
                             fin = composite_row<MODE, LS>(tw[j], a, dab, amax_tf, et, T, C0, C1, C2,
                                                           LS ? lv[j] : 0);
                             ++k;
@@ -1190,7 +1223,10 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                                                  fmaf(T, bg.w, 1.0f - T));
                     }
                     if (P.nsamp) P.nsamp[ray] = k;
-                    if (GRAD) P.ray_n[ray] = k;
+                    if (GRAD) {
+                        P.ray_n[ray] = k;
+                        if (P.tape) tape_flush(P.tape, P.nrays, ray, k, tb_from, tb);
+                    }
                     if (P.tile_cost && my_tile >= 0) atomicMax(&P.tile_cost[my_tile], k);
                     active = false;
                 } else if (!fell && miss_at < kBatch) {
@@ -1205,6 +1241,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         if (!LS && P.prefetch)
                             prefetch_next_brick<LOD>(P, k, miss_pti, o0, o1, o2, d0, d1, d2, t0, t1, lodscale, s_lv,
                                                      bshift, bmask, row, B1 - 1);
+                        if (GRAD && P.tape) tape_flush(P.tape, P.nrays, ray, k, tb_from, tb);
                         suspend_ray(P, ray, k, C0, C1, C2, T, LS ? tcur : 0.0f);
                     } else {
                         atomicAdd(&P.counters[kDevError], 1u);

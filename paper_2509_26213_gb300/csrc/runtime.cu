@@ -191,6 +191,9 @@ struct vol_s {
     float* ckpt = nullptr;
     size_t ckpt_cap = 0;
     int ckpt_shift = kCkptShift;  // checkpoints every 2^ckpt_shift samples (0: VOL_RENDER_CKPT_ALL)
+    float* tape = nullptr;        // sample values of the last gradient render (RenderDev::tape layout)
+    size_t tape_cap = 0;
+    bool taped = false;           // the last gradient render wrote the tape
     int* ray_n = nullptr;
     size_t ray_n_cap = 0;
     float* dlev_buf = nullptr;  // adjoint with LOD: gradients of levels 1..L-1
@@ -625,6 +628,7 @@ RenderDev render_args(vol_t v) {
         p.ckpt = v->ckpt;
         p.ckpt_shift = v->ckpt_shift;
         p.ray_n = v->ray_n;
+        p.tape = v->taped ? v->tape : nullptr;
     }
     return p;
 }
@@ -1270,7 +1274,7 @@ void vol_destroy(vol_t v) {
     if (v->stream) cudaStreamSynchronize(v->stream);
     else cudaDeviceSynchronize();
     void* bufs[] = {v->atlas, v->pt, v->last_used, v->counters, v->aux, v->upd_dev, v->views_dev, v->req_table,
-                    v->req_list, v->susp[0], v->susp[1], v->ckpt, v->ray_n, v->stage_dev, v->stage_slots_dev,
+                    v->req_list, v->susp[0], v->susp[1], v->ckpt, v->tape, v->ray_n, v->stage_dev, v->stage_slots_dev,
                     v->tile_cost, v->tile_order, v->order_buckets, v->range, v->cells, v->dlev_buf, v->req_table64,
                     v->req_list64};
     for (void* b : bufs)
@@ -1638,6 +1642,18 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         const int64_t segs = (max_n + every - 1) / every;
         if (int rc = ensure(v, v->ckpt, v->ckpt_cap, (size_t)std::max<int64_t>(1, segs - 1) * (size_t)rays, "checkpoints")) return rc;
         if (int rc = ensure(v, v->ray_n, v->ray_n_cap, (size_t)rays, "ray sample counts")) return rc;
+        // value tape: 32 values per checkpoint segment of every ray; when it cannot be had the
+        // adjoint interpolates the values again from the bricks
+        v->taped = false;
+        if (v->ckpt_shift == kCkptShift && !(p.flags & VOL_RENDER_GRAD_RECOMPUTE)) {
+            const size_t need = (size_t)((max_n + kCkptEvery - 1) / kCkptEvery) * (size_t)rays * kCkptEvery;
+            if (ensure(v, v->tape, v->tape_cap, need, "value tape") == VOL_OK) {
+                v->taped = true;
+            } else {
+                cudaGetLastError();  // (the failed allocation; gradients are still exact)
+                v->err.clear();
+            }
+        }
     }
     // scheduling state: the previous frame's longest-ray-first order is reused while the tile
     // partition (tile shape, number of views, image sizes) is unchanged; cameras may move.
@@ -1732,7 +1748,7 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
     b.vol = vol_dev(v);
     b.views = v->views_dev;
     b.nviews = v->nviews;
-    b.nwork = v->ntiles;
+    b.nwork = v->ntiles * ((v->params.tile_w * v->params.tile_h + 31) / 32);  // 32 rays per work item
     b.tile_w = v->params.tile_w;
     b.tile_h = v->params.tile_h;
     b.tf = (const float4*)v->tf;
@@ -1760,6 +1776,7 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
     b.counters = v->counters;
     b.ckpt = v->ckpt;
     b.ckpt_shift = v->ckpt_shift;
+    b.tape = v->taped ? v->tape : nullptr;
     b.nrays = v->nrays;
     b.ray_n = v->ray_n;
     // the order built from this forward's per-tile longest rays: those tiles first
@@ -1767,7 +1784,7 @@ int vol_render_backward(vol_t v, const float* drgba_dev, float* dtf_dev, float* 
     CK(v, cudaMemsetAsync(v->counters, 0, sizeof(unsigned) * kNumCounters, v->stream));
     v->counters_collected = false;  // vol_get_stats adds the adjoint's device-side check count
     v->last_counters = v->counters;
-    const int grid = backward_blocks_per_sm(v->dtype, lod) * v->nsm;
+    const int grid = backward_blocks_per_sm(v->dtype, lod, b.tape != nullptr) * v->nsm;
     CK(v, launch_backward(v->dtype, b, grid, v->stream));
     v->stats.launches += 1;
     if (lod && dvoxel_dev) {

@@ -222,3 +222,70 @@ def test_checkpoint_recompute_equals_store_all(P, orc):
         off += n
     grad_close(b[2], odtf, "dtf (store-all)")
     grad_close(b[3], odvox, "dvoxel (store-all)")
+
+
+def test_value_tape_equals_recompute(P):
+    """The adjoint reading the forward's value tape against the adjoint interpolating every value
+    again from the bricks: the same images bit for bit, the same gradients up to the order of the
+    atomic additions, with and without footprint LOD."""
+    D, raw, cams, tf, params = small_case()
+    for lod in (0, 1):
+        vol = P.Volume(D, "f32", 16, 3 if lod else 1)
+        vol.upload_level(0, raw, "f32")
+        if lod:
+            vol.build_lod(0)
+        tfd = torch.from_numpy(tf).cuda()
+        npx = sum(c["w"] * c["h"] for c in cams)
+        dI = torch.from_numpy(np.random.default_rng(12).standard_normal((npx, 4)).astype(np.float32) * np.float32(0.1)).cuda()
+        res = []
+        for flags in (0, P.C.VOL_RENDER_GRAD_RECOMPUTE):
+            pr = dict(params, flags=flags, lod_mode=lod, lod_bias=1 if lod else 0)
+            img = vol.render(cams, tfd, pr, grad=True)
+            dtf = torch.zeros((256, 4), dtype=torch.float32, device="cuda")
+            dvox = torch.zeros(raw.shape, dtype=torch.float32, device="cuda")
+            vol.render_backward(dI, dtf, dvox)
+            torch.cuda.synchronize()
+            assert vol.stats()["device_error"] == 0
+            res.append((img.cpu().numpy(), dtf.cpu().numpy(), dvox.cpu().numpy()))
+        np.testing.assert_array_equal(res[0][0], res[1][0])
+        # (float32 sums of many atomic additions in another order: a few ulps of the largest entry)
+        for i in (1, 2):
+            scale = float(np.abs(res[1][i]).max())
+            assert scale > 0 and float(np.abs(res[0][i] - res[1][i]).max()) <= 1e-5 * scale
+
+
+def test_value_tape_across_suspended_rays(P):
+    """Bricks arriving during a gradient render (rays suspend at missing bricks and resume): the
+    value tape holds every sample's value across the resumption, so the gradients equal those of
+    a volume that was resident from the start."""
+    D, raw, cams, tf, params = small_case()
+    B = 16
+    tfd = torch.from_numpy(tf).cuda()
+    npx = sum(c["w"] * c["h"] for c in cams)
+    dI = torch.from_numpy(np.random.default_rng(13).standard_normal((npx, 4)).astype(np.float32) * np.float32(0.1)).cuda()
+
+    def brick(level, b):
+        idx = [np.minimum(np.arange(b[a] * B, b[a] * B + B + 1), D[a] - 1) for a in range(3)]
+        return np.ascontiguousarray(raw[idx[2]][:, idx[1]][:, :, idx[0]])
+
+    res = []
+    for lazy in (False, True):
+        vol = P.Volume(D, "f32", B, 1)
+        if lazy:
+            vol.set_provider(brick, "f32")
+        else:
+            vol.upload_level(0, raw, "f32")
+        img = vol.render(cams, tfd, dict(params, max_passes=1000), grad=True)
+        if lazy:
+            assert vol.stats()["passes"] > 1  # rays waited for bricks
+        dtf = torch.zeros((256, 4), dtype=torch.float32, device="cuda")
+        dvox = torch.zeros(raw.shape, dtype=torch.float32, device="cuda")
+        vol.render_backward(dI, dtf, dvox)
+        torch.cuda.synchronize()
+        assert vol.stats()["device_error"] == 0
+        res.append((img.cpu().numpy(), dtf.cpu().numpy(), dvox.cpu().numpy()))
+        vol.close()
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    for i in (1, 2):
+        scale = float(np.abs(res[0][i]).max())
+        assert float(np.abs(res[0][i] - res[1][i]).max()) <= 1e-5 * scale
