@@ -10,7 +10,10 @@ namespace {
 // ------------------------------------------------------------------ adjoint
 
 // dL/dtf accumulates in shared memory channel-major (s_dtf[c * 256 + i]), so that lanes
-// flushing different entries of one channel fall into different banks.
+// flushing different entries of one channel fall into different banks.  The table is kept in
+// DtfTable::kCopies copies, lane l adding to copy l % kCopies, each copy shifted by 32 / kCopies
+// banks: neighbouring rays often flush the same entry at once, and additions to one address in
+// one instruction are serialised.  The copies are summed at the end.
 __device__ __forceinline__ void flush_dtf(float* s_dtf, int idx, float acc[8]) {
     if (idx >= 0) {
 #pragma unroll
@@ -52,6 +55,17 @@ __device__ __forceinline__ void flush_dtf4(float* s_dtf, int idx, const float* a
         if (acc[c] != 0.0f) atomicAdd(&s_dtf[c * 256 + idx], acc[c]);
 }
 
+// Copies of the dL/dtf table: with the value tape the segment's values are not kept in shared
+// memory, which leaves room for 4 copies at the same occupancy.
+#ifndef VOLRC_BWD_COPIES
+#define VOLRC_BWD_COPIES 4
+#endif
+template <bool TAPE>
+struct DtfTable {
+    static constexpr int kCopies = TAPE ? VOLRC_BWD_COPIES : 1;
+    static constexpr int kStride = 1024 + (kCopies > 1 ? 32 / kCopies : 0);  // words between copies
+};
+
 // Samples per lane whose page-table lookups and gathers the adjoint's forward recompute issues
 // together.
 #ifndef VOLRC_BWD_BATCH
@@ -59,7 +73,7 @@ __device__ __forceinline__ void flush_dtf4(float* s_dtf, int idx, const float* a
 #endif
 constexpr int kBwdBatch = VOLRC_BWD_BATCH;
 // Adjoint CTA size and the resident CTAs per SM its register allocation must allow (shared
-// memory per CTA: 8 KiB + 256 B per thread).
+// memory per CTA: 4 KiB + 4 KiB per dL/dtf copy + 256 B per thread).
 #ifndef VOLRC_BWD_THREADS
 #define VOLRC_BWD_THREADS 192
 #endif
@@ -85,12 +99,14 @@ constexpr int kBwdMinBlocks = VOLRC_BWD_MINB;
 template <int DT, bool LOD, bool TAPE>
 __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const __grid_constant__ BackwardDev P) {
     __shared__ float4 s_tf[256];
-    __shared__ float s_dtf[1024];
+    constexpr int kDtfCopies = DtfTable<TAPE>::kCopies, kDtfStride = DtfTable<TAPE>::kStride;
+    __shared__ float s_dtf_all[kDtfCopies * kDtfStride];
     __shared__ float s_T[kCkptEvery][kBwdThreads];
-    __shared__ float s_V[kCkptEvery][kBwdThreads];
+    __shared__ float s_V[TAPE ? 1 : kCkptEvery][kBwdThreads];  // (with the tape: read from it again)
     __shared__ LevelDev s_lv[LOD ? kMaxLevels : 1];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = P.tf[i];
-    for (int i = threadIdx.x; i < 1024; i += blockDim.x) s_dtf[i] = 0.0f;
+    for (int i = threadIdx.x; i < kDtfCopies * kDtfStride; i += blockDim.x) s_dtf_all[i] = 0.0f;
+    float* s_dtf = s_dtf_all + (threadIdx.x & 31) % kDtfCopies * kDtfStride;  // this lane's copy
     if (LOD && threadIdx.x < P.vol.nlevels) s_lv[threadIdx.x] = P.vol.lv[threadIdx.x];
     __syncthreads();
 
@@ -174,9 +190,10 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
         const int len = seg ? min(1 << P.ckpt_shift, n - k0) : 0;
         float T = (seg && s > 0) ? P.ckpt[(long long)(s - 1) * P.nrays + ray] : 1.0f;
         const int maxlen = __reduce_max_sync(kFull, len);
+        // the lane's segment on the tape: 32 values in 128 contiguous bytes
+        const float* tp = TAPE ? P.tape + ((long long)s * P.nrays + (seg ? ray : 0)) * kCkptEvery : nullptr;
         if (TAPE) {
-            // forward from the tape: 4 values per load (a segment's 32 values are 128 contiguous bytes)
-            const float* tp = P.tape + ((long long)s * P.nrays + (seg ? ray : 0)) * kCkptEvery;
+            // forward from the tape, 4 values per load
             for (int jb = 0; jb < maxlen; jb += 4) {
                 const float4 v4 = jb < len ? __ldg(reinterpret_cast<const float4*>(tp + jb)) : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
@@ -188,7 +205,6 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                         const float wt = x - (float)i;
                         const float al = fmaf(wt, s_tf[i + 1].w - s_tf[i].w, s_tf[i].w);
                         s_T[jb + u][tid] = T;
-                        s_V[jb + u][tid] = vv[u];
                         T = T * (1.0f - al);
                     }
                 }
@@ -239,7 +255,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                     const float wt = x - (float)i;
                     const float al = fmaf(wt, s_tf[i + 1].w - s_tf[i].w, s_tf[i].w);
                     s_T[jb + u][tid] = T;
-                    s_V[jb + u][tid] = val[u];
+                    if (!TAPE) s_V[jb + u][tid] = val[u];
                     T = T * (1.0f - al);
                 }
             }
@@ -261,7 +277,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
                     }
                     resolve_reg(L0, bshift, bmask, row, p, Q);
                 }
-                const float val = s_V[j][tid];
+                const float val = TAPE ? __ldg(tp + j) : s_V[j][tid];
                 const float Tk = s_T[j][tid];
                 const float x = tf_coord<DT>(val);
                 const int i = min((int)x, 254);
@@ -342,7 +358,9 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_backward(const _
     __syncthreads();
     if (P.dtf)
         for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
-            const float v = s_dtf[(i & 3) * 256 + (i >> 2)];
+            float v = 0.0f;
+#pragma unroll
+            for (int r = 0; r < kDtfCopies; ++r) v += s_dtf_all[r * kDtfStride + (i & 3) * 256 + (i >> 2)];
             if (v != 0.0f) atomicAdd(&P.dtf[i], v);
         }
 }
