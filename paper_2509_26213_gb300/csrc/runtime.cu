@@ -165,6 +165,12 @@ struct vol_s {
     ViewDev* views_dev = nullptr;
     int views_cap = 0;
     std::vector<ViewDev> views_host;
+    // the view table the device copy holds, and the page-locked staging buffer it was copied from
+    // (reused once the event says the last copy out of it is done)
+    std::vector<ViewDev> views_sent;
+    ViewDev* views_pinned = nullptr;
+    int views_pinned_cap = 0;
+    cudaEvent_t ev_views = nullptr;
     int nviews = 0;
     int ntiles = 0;
     int64_t nrays = 0;
@@ -1279,7 +1285,8 @@ void vol_destroy(vol_t v) {
                     v->req_list64};
     for (void* b : bufs)
         if (b) cudaFree(b);
-    void* hbufs[] = {v->stage_host, v->ring.host, v->ring.slots, v->ring.ptis, v->poll_host};
+    void* hbufs[] = {v->stage_host, v->ring.host, v->ring.slots, v->ring.ptis, v->poll_host, v->views_pinned};
+    if (v->ev_views) cudaEventDestroy(v->ev_views);
     for (void* b : hbufs)
         if (b) cudaFreeHost(b);
     for (auto& r : v->ring.inflight) cudaEventDestroy(r.ev);
@@ -1592,6 +1599,7 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         if (!(c.tan_half_fov > 0.0f) || !std::isfinite(c.tan_half_fov))
             return fail(v, VOL_ERR_INVALID_ARG, "tan_half_fov must be > 0");
         ViewDev& V = v->views_host[i];
+        V = ViewDev{};  // (padding too: tables are compared bytewise)
         for (int a = 0; a < 3; ++a) {
             V.eye[a] = c.eye[a];
             V.right[a] = c.right[a];
@@ -1614,10 +1622,31 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         if (v->views_dev) cudaFree(v->views_dev);
         v->views_dev = nullptr;
         v->views_cap = 0;
+        v->views_sent.clear();
         CK(v, dev_alloc(v, (void**)&v->views_dev, sizeof(ViewDev) * nviews));
         v->views_cap = nviews;
     }
-    CK(v, cudaMemcpyAsync(v->views_dev, v->views_host.data(), sizeof(ViewDev) * nviews, cudaMemcpyHostToDevice, v->stream));
+    // the device table is copied only when the views changed, from page-locked memory (an
+    // asynchronous copy; a copy from pageable memory would wait for the staging)
+    if (v->views_sent.size() != (size_t)nviews ||
+        memcmp(v->views_sent.data(), v->views_host.data(), sizeof(ViewDev) * nviews) != 0) {
+        if (v->views_pinned_cap < nviews) {
+            if (v->views_pinned) {
+                CK(v, cudaEventSynchronize(v->ev_views));
+                cudaFreeHost(v->views_pinned);
+            }
+            v->views_pinned = nullptr;
+            v->views_pinned_cap = 0;
+            CK(v, host_alloc(v, (void**)&v->views_pinned, sizeof(ViewDev) * nviews, cudaHostAllocDefault));
+            v->views_pinned_cap = nviews;
+        }
+        if (!v->ev_views) CK(v, cudaEventCreateWithFlags(&v->ev_views, cudaEventDisableTiming));
+        else CK(v, cudaEventSynchronize(v->ev_views));  // the last copy out of the buffer is done
+        memcpy(v->views_pinned, v->views_host.data(), sizeof(ViewDev) * nviews);
+        CK(v, cudaMemcpyAsync(v->views_dev, v->views_pinned, sizeof(ViewDev) * nviews, cudaMemcpyHostToDevice, v->stream));
+        CK(v, cudaEventRecord(v->ev_views, v->stream));
+        v->views_sent = v->views_host;
+    }
     v->nviews = nviews;
     v->ntiles = (int)tiles;
     v->nrays = rays;

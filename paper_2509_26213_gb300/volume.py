@@ -20,11 +20,11 @@ _NP_DT = {"u8": np.uint8, "u16": np.uint16, "f16": np.float16, "f32": np.float32
 
 
 def camera_struct(cam: dict) -> C.vol_camera:
+    # (a ctypes float field rounds the value it is given to binary32 to nearest, as numpy does)
     s = C.vol_camera()
-    for k in ("eye", "right", "up", "fwd"):
-        getattr(s, k)[:] = [float(np.float32(x)) for x in cam[k]]
-    s.tan_half_fov = float(np.float32(cam["tan_half_fov"]))
-    s.aspect = float(np.float32(cam["aspect"]))
+    s.eye[:], s.right[:], s.up[:], s.fwd[:] = cam["eye"], cam["right"], cam["up"], cam["fwd"]
+    s.tan_half_fov = cam["tan_half_fov"]
+    s.aspect = cam["aspect"]
     s.w, s.h = int(cam["w"]), int(cam["h"])
     return s
 
@@ -32,8 +32,8 @@ def camera_struct(cam: dict) -> C.vol_camera:
 def params_struct(step=0.5, et=0.99, bg=(0.0, 0.0, 0.0, 0.0), lod_mode=0, lod_bias=0, tile_w=0, tile_h=0,
                   max_passes=0, flags=0, refill=0, ctas_per_sm=0, composite="dvr", grad=False) -> C.vol_params:
     p = C.vol_params()
-    p.step, p.et_threshold = float(np.float32(step)), float(np.float32(et))
-    p.bg[:] = [float(np.float32(b)) for b in bg]
+    p.step, p.et_threshold = step, et
+    p.bg[:] = bg
     p.lod_mode, p.lod_bias = int(lod_mode), int(lod_bias)
     p.tile_w, p.tile_h, p.max_passes = int(tile_w), int(tile_h), int(max_passes)
     p.flags = int(flags) | (C.VOL_RENDER_GRAD if grad else 0)
@@ -98,7 +98,10 @@ class Volume:
             pass
 
     def _sync_stream(self):
-        C.check(self.lib.vol_set_stream(self.h, _stream_ptr()), self.h)
+        st = torch.cuda.current_stream().cuda_stream
+        if st != getattr(self, "_stream", None):
+            C.check(self.lib.vol_set_stream(self.h, ctypes.c_void_p(st)), self.h)
+            self._stream = st
 
     # ------------------------------------------------------------ bricks
     def upload_level(self, level: int, src, src_dtype: str | None = None):
