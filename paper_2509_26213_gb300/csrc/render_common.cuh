@@ -27,6 +27,8 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+__host__ __device__ constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
+
 template <int DT>
 struct Voxel;
 template <>
@@ -360,6 +362,21 @@ __device__ __forceinline__ uint32_t cell_of(const int i0[3], int bmask, int cs, 
            (uint32_t)((i0[0] & bmask) >> cs);
 }
 
+// Quad layout with a brick edge BS >= 8 known at compile time: a sample's local entry offset is
+// (z BS + y) BS + x, so its macro-cell (8 per axis, cells of BS / 8 voxels) is a fixed set of bits
+// of it: key() keeps those bits (equal keys: the same cell of the brick), index() packs them into
+// the cell's table index cz 64 + cy 8 + cx.
+template <int BS>
+struct CellBits {
+    static constexpr int bs = BS >= 8 ? log2i(BS) : 3, cs = bs - 3;  // (only used for BS >= 8)
+    static constexpr uint32_t field = ((1u << bs) - 1u) & ~((1u << cs) - 1u);
+    static constexpr uint32_t mask = field | (field << bs) | (field << (2 * bs));
+    static __device__ __forceinline__ uint32_t key(uint32_t loc) { return loc & mask; }
+    static __device__ __forceinline__ uint32_t index(uint32_t key) {
+        return ((key >> cs) & 7u) | ((key >> (bs + cs - 3)) & 0x38u) | ((key >> (2 * bs + cs - 6)) & 0x1C0u);
+    }
+};
+
 // A macro-cell whose TF-entry span is [span & 255, span >> 8] holds no sample that changes the
 // lane's state (the per-cell form of brick_empty / brick_below_alpha / brick_below_coord; the
 // span already carries the one-entry margins).  MIP: every coordinate in the cell is below the
@@ -689,7 +706,6 @@ constexpr int kBatchLevelStep = VOLRC_BATCH_LS;
 #define VOLRC_MIN_CTAS 5
 #endif
 
-__host__ __device__ constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
 
 // The TF row of one sample: weight wt, entry a = tf[i] and dab = tf[i+1] - tf[i] at the TF
 // coordinate of the interpolated value (i = min(floor(x), 254)).
@@ -790,7 +806,10 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
     static_assert(!LS || MODE == kDvr, "level-scaled sampling is for emission/absorption without gradients");
     static_assert(!SP || (MODE == kDvr && !LS), "the sparse page table variant is for emission/absorption");
     static_assert(!ES || (!LS && !SP), "empty-space skipping assumes uniform steps and the flat page table");
-    constexpr int kBatch = (LS || ES) ? kBatchLevelStep : kBatchDefault;
+    // ES: the macro-cell of a quad-layout sample is read from its local offset; otherwise it is
+    // computed from the voxel and kept in bits 22..30 of the offset (offsets stay below 2^22)
+    constexpr bool kFastCell = ES && Q && BS >= 8;
+    constexpr int kBatch = LS || ES ? kBatchLevelStep : kBatchDefault;  // (6 spills with ES)
     constexpr bool GRAD = MODE == kDvrGrad;
     constexpr float kT0 = MODE == kMop ? 0.0f : (MODE == kMip ? -1.0f : 1.0f);
     __shared__ float4 s_tf[256];
@@ -1013,8 +1032,8 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                             pti[j] = sparse_top(L, h0, h1, h2);
                             sub[j] = sparse_sub(h0, h1, h2);
                         }
-                        // ES: the sample's macro-cell in bits 22..30 (local offsets stay below 2^22)
-                        loc[j] = ES ? (R.local | (cell_of(R.i0, bmask, P.vol.cshift, P.vol.cbits) << 22)) : R.local;
+                        loc[j] = ES && !kFastCell ? (R.local | (cell_of(R.i0, bmask, P.vol.cshift, P.vol.cbits) << 22))
+                                                  : R.local;
                         wgt[j][0] = R.w[0];
                         wgt[j][1] = R.w[1];
                         wgt[j][2] = R.w[2];
@@ -1084,14 +1103,16 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                             }
                         }
                         // (a skipping lane's leading samples in the block it jumped into are passed over)
-                        const bool lead = in_skip && pti[j] == pti[0] && (sk_brick || (loc[j] >> 22) == (loc[0] >> 22));
+                        const uint32_t c = kFastCell ? CellBits<BS>::key(loc[j]) : loc[j] >> 22;
+                        const bool lead = in_skip && pti[j] == pti[0] &&
+                                          (sk_brick || c == (kFastCell ? CellBits<BS>::key(loc[0]) : loc[0] >> 22));
                         if (ES && empty_at == kBatch && !lead) {
                             bool e = cur_bskip;
                             if (!e) {
-                                const uint32_t c = loc[j] >> 22;
                                 if (c != cur_cell) {
                                     cur_cell = c;
-                                    cur_cskip = span_skippable<MODE>(__ldg(P.vol.cells + slot[j] * ncells + c), s_apre,
+                                    const uint32_t ci = kFastCell ? CellBits<BS>::index(c) : c;
+                                    cur_cskip = span_skippable<MODE>(__ldg(P.vol.cells + slot[j] * ncells + ci), s_apre,
                                                                      s_amx, T);
                                 }
                                 e = cur_cskip;
@@ -1109,7 +1130,8 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 for (int j = 0; j < kBatch; ++j) {
                     const bool use = j < nvalid && j < miss_at;
                     const unsigned long long base =
-                        use ? (unsigned long long)slot[j] * slot_stride + (ES ? (loc[j] & 0x3FFFFFu) : loc[j]) : 0ull;
+                        use ? (unsigned long long)slot[j] * slot_stride + (ES && !kFastCell ? (loc[j] & 0x3FFFFFu) : loc[j])
+                            : 0ull;
                     val[j] = sample_value<DT, BS, Q>(P.vol.atlas, base, B1, wgt[j]);
                 }
                 const int stop = min(min(nvalid, miss_at), empty_at);
