@@ -198,6 +198,7 @@ def workload_config(wl, ws):
     """The keys that define the workload (printed identically by both arms)."""
     p = wl["params"]
     return {"workload": wl["name"], "store": wl["store"], "brick": wl["brick"], "levels": wl["levels"],
+            "layout": wl.get("layout", "quad"),
             "views": len(wl["cams"]), "pixels": sum(c["w"] * c["h"] for c in wl["cams"]),
             "lod": "footprint" if p.get("lod_mode") else "level 0", "step": p["step"], "et": p["et"],
             "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
@@ -288,8 +289,8 @@ def run_reference(args, dist, rank, ws):
 
 # ------------------------------------------------------------------ our arm
 
-def build_volume(P, wl, store, raw, layout="quad"):
-    vol = P.Volume(wl["D"], store, wl["brick"], wl["levels"], layout=layout)
+def build_volume(P, wl, store, raw, layout=None):
+    vol = P.Volume(wl["D"], store, wl["brick"], wl["levels"], layout=layout or wl.get("layout", "quad"))
     vol.upload_level(0, raw, wl["src"])
     if wl["levels"] > 1:
         vol.build_lod(0)
@@ -340,7 +341,7 @@ def forward_bytes(touched, brick, bpv, npx):
     return touched * (brick + 1) ** 3 * bpv + npx * 16 + 4096 + touched * 4
 
 
-def measure_variants(torch, P, vol, wl, raw, cams, tf, params, samples, args, flush, img_host, dev):
+def measure_variants(torch, P, vol, wl, raw, cams, tf, params, samples, args, flush):
     """The primary frame from other storage types, with empty-space skipping, level-scaled
     sampling and as projections."""
     variants = {}
@@ -405,10 +406,10 @@ def storage_variants(torch, P, wl, raw, cams, tf, params, args, flush, img_u16):
     return out
 
 
-def fwd_bwd(torch, P, args, flush, dev, do_err):
+def fwd_bwd(torch, P, args, flush, dev, do_err, key="c4"):
     """Differentiable workload: forward in gradient mode + adjoint of L = 1/2 sum (I - I*)^2, I*
     rendered with the seeded perturbed TF."""
-    w4 = workloads.c4()
+    w4 = getattr(workloads, key)()
     raw4 = w4["make"]()
     v4 = build_volume(P, w4, "f32", raw4)
     tf4 = torch.from_numpy(w4["tf"]).to(dev)
@@ -424,7 +425,7 @@ def fwd_bwd(torch, P, args, flush, dev, do_err):
     drgba = (o4 - target).contiguous()  # dL/dI of the L2 loss (the forward is deterministic)
     loss = 0.5 * float((drgba.double() ** 2).sum().item())
     dtf = torch.zeros((256, 4), dtype=torch.float32, device=dev)
-    dvox = torch.zeros((256, 256, 256), dtype=torch.float32, device=dev)
+    dvox = torch.zeros(tuple(w4["D"][::-1]), dtype=torch.float32, device=dev)
     v4.render_backward(drgba, dtf, dvox)
     torch.cuda.synchronize()
     dvox_touched = int(torch.count_nonzero(dvox).item())
@@ -600,6 +601,7 @@ def run_ours(args, dist, rank, ws, local):
     dev = torch.device("cuda", local)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     wl = load_workload(args.workload, rank, ws)
+    wl["layout"] = args.layout
     raw = wl["make"]()
     cams, params = wl["cams"], dict(wl["params"])
     tf = torch.from_numpy(wl["tf"]).to(dev)
@@ -693,7 +695,7 @@ def run_ours(args, dist, rank, ws, local):
     imgh = img.cpu().numpy() if rank == 0 else None
     del img
     if extras:
-        variants = measure_variants(torch, P, vol, wl, raw, cams, tf, params, samples, args, flush, img_host, dev)
+        variants = measure_variants(torch, P, vol, wl, raw, cams, tf, params, samples, args, flush)
     vol.close()
     torch.cuda.empty_cache()
     stores = {}
@@ -701,8 +703,8 @@ def run_ours(args, dist, rank, ws, local):
         stores = storage_variants(torch, P, wl, raw, cams, tf, params, args, flush, imgh)
         for k, (rec, _) in stores.items():
             variants[k] = rec
-    if extras and args.workload in ("c2", "c4"):
-        fb = fwd_bwd(torch, P, args, flush, dev, do_err=not args.no_cpu)
+    if extras and args.workload in ("c2", "c4", "c4s"):
+        fb = fwd_bwd(torch, P, args, flush, dev, do_err=not args.no_cpu, key="c4s" if args.workload == "c4s" else "c4")
     if extras and args.workload == "c2" and not args.only_primary:
         others["c1"] = single_workload(torch, P, "c1", args, flush, dev, do_err=not args.no_cpu)
         others["c3"] = single_workload(torch, P, "c3", args, flush, dev, do_err=not args.no_cpu, autotune=True)
@@ -887,7 +889,9 @@ def main():
                     help="variants and fwd+bwd, but not the plain, batched and out-of-core workloads")
     ap.add_argument("--no-cpu", action="store_true", help="no oracle: no cpu_baseline and no error statements")
     ap.add_argument("--autotune", action="store_true", help="autotune tile, refill and brick size first")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s", "c3", "c4", "c4s", "c5"])
+    ap.add_argument("--layout", default="quad", choices=["quad", "compact"],
+                    help="atlas slot layout of the primary line's volume")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-frac", type=float, default=0.25, help="reference arm: fraction of pixels per step")
     args = ap.parse_args()

@@ -96,3 +96,12 @@ def c2s(seed: int = 2) -> dict:
         "params": {"step": 0.5, "et": 0.99, "lod_mode": 1, "lod_bias": 0},
         "name": "reduced-precision single view, 512^3 u16 noise+spheres, 64^3 bricks, 4 levels, 1920x1080",
     }
+
+
+def c4s(seed: int = 4) -> dict:
+    """c4 with 2 of its 16 views (same volume, TF and target): the case the adjoint is profiled in
+    detail on, a few GB on the device at most."""
+    wl = c4(seed)
+    wl.update(key="c4s", cams=wl["cams"][:2],
+              name="differentiable, 256^3 f32 blobs, 2 views 512x512, forward + adjoint")
+    return wl
