@@ -512,6 +512,7 @@ def single_workload(torch, P, key, args, flush, dev, do_err, autotune=False):
     cams, params = wl["cams"], dict(wl["params"])
     tf = torch.from_numpy(wl["tf"]).to(dev)
     store = wl["store"]
+    plain_brick, plain_params = wl["brick"], dict(wl["params"])  # the config's own, before autotuning
     tuned = None
     if autotune:
         tuned = run_autotune(P, wl, store, raw, cams, tf, params)
@@ -547,12 +548,13 @@ def single_workload(torch, P, key, args, flush, dev, do_err, autotune=False):
         v32.close()
     if key == "c3":
         # the plain form at matched rays: the same views rendered one launch each from a float32
-        # store of the same volume (converted on the GPU; compact slots keep it to ~41 GB)
-        wl32 = dict(wl)
+        # store of the same volume (converted on the GPU; compact slots keep it to ~41 GB), with
+        # the configuration's own brick size and the default ray tiles
+        wl32 = dict(wl, brick=plain_brick)
         v32 = build_volume(P, wl32, "f32", raw, layout="compact")
         s32 = 0
         for cam in cams:
-            _, nsv = v32.render(cam, tf, params, nsamples=True)
+            _, nsv = v32.render(cam, tf, plain_params, nsamples=True)
             s32 += int(nsv.sum().item())
         torch.cuda.synchronize()
         per_view = []
@@ -561,14 +563,15 @@ def single_workload(torch, P, key, args, flush, dev, do_err, autotune=False):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             for cam in cams:
-                v32.render(cam, tf, params)
+                v32.render(cam, tf, plain_params)
             b.record()
             torch.cuda.synchronize()
             per_view.append(a.elapsed_time(b))
         ms32 = mean(per_view)
         rec["plain_f32_one_view_per_launch"] = {"ms_per_frame": ms32, "samples_per_frame": s32,
                                                 "samples_per_s": s32 / (ms32 * 1e-3), "launches": len(cams),
-                                                "store": "f32 compact", "speedup_of_batched": ms32 / ms}
+                                                "store": "f32 compact", "brick": plain_brick,
+                                                "tile": "default (4 x 8)", "speedup_of_batched": ms32 / ms}
         v32.close()
     torch.cuda.empty_cache()
     if do_err:
