@@ -159,8 +159,8 @@ void orc_u16_to_f32(int64_t n, const uint16_t *src, float *dst)
 /* ------------------------------------------------------ downsample */
 
 /*
- * Sec. III-D: level l+1 from level l by a 2x2x2 box filter ("smoothing and
- * downsampling").  Coarse voxel i averages children 2i and 2i+1 per axis;
+ * Sec. III-D: level l+1 from level l by a 2x2x2 box filter (the paper
+ * smooths, then halves the resolution).  Coarse voxel i averages children 2i and 2i+1 per axis;
  * a child index beyond the fine edge is replaced by the last fine voxel.
  *   u8/u16: integer mean rounded half up, (sum + 4) >> 3
  *   f16/f32: binary32 sum of the eight children in the order

@@ -1,5 +1,5 @@
 // kernels_skip.cu -- variants of the forward kernel with empty-space skipping (the paper's
-// empty-space skipping, Sec. III-H "const chunk table" and the ES column of Sec. IV-A) for
+// empty-space skipping: the table of uniform chunks of Sec. III-H and the ES column of Sec. IV-A) for
 // emission/absorption compositing.  A sample in a
 // brick or 8^3-cell block whose value range the transfer function maps to zero opacity jumps
 // to the end of the run of such blocks; the image does not change.
