@@ -363,17 +363,19 @@ __device__ __forceinline__ uint32_t cell_of(const int i0[3], int bmask, int cs, 
 }
 
 // Quad layout with a brick edge BS >= 8 known at compile time: a sample's local entry offset is
-// (z BS + y) BS + x, so its macro-cell (8 per axis, cells of BS / 8 voxels) is a fixed set of bits
-// of it: key() keeps those bits (equal keys: the same cell of the brick), index() packs them into
-// the cell's table index cz 64 + cy 8 + cx.
+// (z BS + y) BS + x, so its macro-cell (2^cb per axis, cells of BS >> cb voxels) is a fixed set
+// of bits of it: key() keeps those bits (equal keys: the same cell of the brick), index() packs
+// them into the cell's table index (cz CB + cy) CB + cx, CB = 2^cb.
 template <int BS>
 struct CellBits {
-    static constexpr int bs = BS >= 8 ? log2i(BS) : 3, cs = bs - 3;  // (only used for BS >= 8)
+    static constexpr int bs = BS >= 8 ? log2i(BS) : 3;  // (only used for BS >= 8)
+    static constexpr int cb = cell_bits_for(bs), cs = bs - cb;
+    static constexpr uint32_t cm = (1u << cb) - 1u;
     static constexpr uint32_t field = ((1u << bs) - 1u) & ~((1u << cs) - 1u);
     static constexpr uint32_t mask = field | (field << bs) | (field << (2 * bs));
     static __device__ __forceinline__ uint32_t key(uint32_t loc) { return loc & mask; }
     static __device__ __forceinline__ uint32_t index(uint32_t key) {
-        return ((key >> cs) & 7u) | ((key >> (bs + cs - 3)) & 0x38u) | ((key >> (2 * bs + cs - 6)) & 0x1C0u);
+        return ((key >> cs) & cm) | ((key >> (bs + cs - cb)) & (cm << cb)) | ((key >> (2 * bs + cs - 2 * cb)) & (cm << (2 * cb)));
     }
 };
 
@@ -699,8 +701,13 @@ __device__ __forceinline__ void tape_flush(float* tape, long long nrays, long lo
 #ifndef VOLRC_BATCH_LS
 #define VOLRC_BATCH_LS 5
 #endif
+// Empty-space skipping keeps the tested block's value range and span through the batch.
+#ifndef VOLRC_BATCH_ES
+#define VOLRC_BATCH_ES 6
+#endif
 constexpr int kBatchDefault = VOLRC_BATCH;
 constexpr int kBatchLevelStep = VOLRC_BATCH_LS;
+constexpr int kBatchSkip = VOLRC_BATCH_ES;
 // Minimum resident CTAs per SM the register allocation must allow.
 #ifndef VOLRC_MIN_CTAS
 #define VOLRC_MIN_CTAS 5
@@ -796,20 +803,23 @@ __device__ __forceinline__ float next_t_level_step(float t, float step, int l) {
 // on level l, whose opacity is corrected to that longer step; t of the lane's next sample is
 // kept in tcur (and in a suspended ray's record).
 // SP: three-level sparse page table (emission/absorption, uniform steps, no empty-space jumps).
-// ES: empty-space skipping: when a batch meets a sample in a brick or macro-cell that cannot change
-// the lane's state (zero TF opacity over its value range; for MOP/MIP no opacity / coordinate
-// above the kept one), the lane's next batch starts at that block's estimated last sample instead;
-// the batch's first decision verifies the estimate exactly (same level and block), so a lane
-// crosses a whole block per iteration in step with the other lanes of its warp.
+// ES: empty-space skipping: when the last sample of a batch lies in a brick or macro-cell that
+// cannot change the lane's state (zero TF opacity over its value range; for MOP/MIP no opacity /
+// coordinate above the kept one), the lane's next batch starts near that block's estimated last
+// sample instead of the next one; the batch's first decision verifies the estimate exactly (same
+// level and block), so a lane crosses a whole block per iteration in step with the other lanes of
+// its warp.  One block is tested per batch, and its value range and span are loaded together with
+// the gathers: a sample that enters an empty block earlier in the batch is composited (it adds
+// nothing), which costs less than testing every sample.
 template <int DT, bool LOD, int MODE, int BS, bool Q, bool LS = false, bool SP = false, bool ES = false>
 __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const __grid_constant__ RenderDev P) {
     static_assert(!LS || MODE == kDvr, "level-scaled sampling is for emission/absorption without gradients");
     static_assert(!SP || (MODE == kDvr && !LS), "the sparse page table variant is for emission/absorption");
     static_assert(!ES || (!LS && !SP), "empty-space skipping assumes uniform steps and the flat page table");
     // ES: the macro-cell of a quad-layout sample is read from its local offset; otherwise it is
-    // computed from the voxel and kept in bits 22..30 of the offset (offsets stay below 2^22)
+    // computed from the voxel
     constexpr bool kFastCell = ES && Q && BS >= 8;
-    constexpr int kBatch = LS || ES ? kBatchLevelStep : kBatchDefault;  // (6 spills with ES)
+    constexpr int kBatch = LS ? kBatchLevelStep : (ES ? kBatchSkip : kBatchDefault);
     constexpr bool GRAD = MODE == kDvrGrad;
     constexpr float kT0 = MODE == kMop ? 0.0f : (MODE == kMip ? -1.0f : 1.0f);
     __shared__ float4 s_tf[256];
@@ -824,13 +834,24 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
         const float4 a = s_tf[i], b = s_tf[i + 1];
         s_tfd[i] = make_float4(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y), __fsub_rn(b.z, a.z), __fsub_rn(b.w, a.w));
     }
-    if (threadIdx.x == 0) {
-        int c = 0;
-        for (int i = 0; i < 256; ++i) {
-            s_apre[i] = c;
-            c += s_tf[i].w != 0.0f;
+    if (ES && threadIdx.x < 32) {
+        // (only the skip tests read it) lane l counts entries 8 l .. 8 l + 7, then a scan over lanes
+        const int l8 = 8 * (int)threadIdx.x;
+        int c[8], tot = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            c[u] = tot;
+            tot += s_tf[l8 + u].w != 0.0f;
         }
-        s_apre[256] = c;
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if ((int)threadIdx.x >= o) incl += y;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s_apre[l8 + u] = incl - tot + c[u];
+        if (threadIdx.x == 31) s_apre[256] = incl;
     }
     if (MODE == kMop) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) s_amx[i] = s_tf[i].w;
@@ -870,13 +891,9 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
     float4 tb = make_float4(0.f, 0.f, 0.f, 0.f);
     int tb_from = 0;
     uint32_t cur_pti = kInvalidSlot;
-    // ES: the brick of cur_pti cannot change the lane's state; the macro-cell last tested and
-    // whether it cannot
-    bool cur_bskip = false, cur_cskip = false;
-    uint32_t cur_cell = kInvalidSlot;
     const unsigned long long ncells = ES ? 1ull << (3 * P.vol.cbits) : 0ull;
-    // ES: sample k lies in a block (brick when sk_brick, else macro-cell) that cannot change the
-    // lane's state
+    // ES: sample k - 1 lies in a block (brick when sk_brick, else macro-cell) that cannot change
+    // the lane's state
     bool sk = false, sk_brick = false;
     const int nlev = P.vol.nlevels;
     int cur_l = 0;
@@ -977,13 +994,13 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 int lv[kBatch];        // LS: their levels
                 uint32_t sub[kBatch];  // SP: brick position inside the middle and leaf pages
                 tv[0] = tcur;
-                // ES: a lane whose sample k lies in a block that cannot change its state starts the
-                // batch at the block's estimated last sample kb (verified below by sample kb)
+                // ES: a lane whose sample k - 1 lies in a block that cannot change its state starts
+                // the batch at the block's estimated last sample kb (verified below by sample kb)
                 int kb = k;
-                int key_l = 0, key_g[3] = {0, 0, 0}, key_shift = 0;  // ES: the block of sample k
+                int key_l = 0, key_g[3] = {0, 0, 0}, key_shift = 0;  // ES: the block of sample k - 1
                 if (ES && sk) {
                     const float o3[3] = {o0, o1, o2}, d3[3] = {d0, d1, d2};
-                    const SampleKey K = sample_key<LOD>(k, o3, d3, t0, t1, step, lodscale, P.lod_bias, nlev, s_lv,
+                    const SampleKey K = sample_key<LOD>(k - 1, o3, d3, t0, t1, step, lodscale, P.lod_bias, nlev, s_lv,
                                                         bshift, bmask, row);
                     key_shift = sk_brick ? bshift : P.vol.cshift;
                     key_l = K.l;
@@ -992,12 +1009,13 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     key_g[2] = K.R.i0[2] >> key_shift;
                     // one sample short of the estimate: the batch then lands inside the block, and the
                     // block's samples at its start are passed over below
-                    kb = max(k, block_end_estimate<LOD>(k, K, key_shift, o3, d3, t0, t1, step, lodscale, P.lod_bias,
-                                                        nlev, s_lv) - 1);
+                    kb = max(k, block_end_estimate<LOD>(k - 1, K, key_shift, o3, d3, t0, t1, step, lodscale,
+                                                        P.lod_bias, nlev, s_lv) - 1);
                 }
-                // ES: sample kb must lie in the block of sample k; then every sample in between does
-                // (a block's samples are contiguous along the ray) and composites nothing.  When it
-                // does not (the estimate overshot), the decisions are taken again from k.
+                // ES: sample kb must lie in the block of sample k - 1; then every sample in between
+                // does (a block's samples are contiguous along the ray) and composites nothing.  When
+                // it does not (the estimate overshot), the decisions are taken again from k.
+                uint32_t cell_last = 0u;  // ES: macro-cell (table index) of the batch's last sample
                 for (;;) {
                     nvalid = kBatch;
                     bool in_block = true;  // ES: sample kb lies in the block of sample k
@@ -1032,8 +1050,10 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                             pti[j] = sparse_top(L, h0, h1, h2);
                             sub[j] = sparse_sub(h0, h1, h2);
                         }
-                        loc[j] = ES && !kFastCell ? (R.local | (cell_of(R.i0, bmask, P.vol.cshift, P.vol.cbits) << 22))
-                                                  : R.local;
+                        loc[j] = R.local;
+                        if (ES && j == kBatch - 1)
+                            cell_last = kFastCell ? CellBits<BS>::index(CellBits<BS>::key(R.local))
+                                                  : cell_of(R.i0, bmask, P.vol.cshift, P.vol.cbits);
                         wgt[j][0] = R.w[0];
                         wgt[j][1] = R.w[1];
                         wgt[j][2] = R.w[2];
@@ -1041,8 +1061,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     if (!(ES && sk && kb > k) || (nvalid > 0 && in_block)) break;
                     kb = k;
                 }
-                const bool in_skip = ES && sk;
-                if (ES && in_skip && kb > k) {
+                if (ES && sk && kb > k) {
                     if (GRAD) {
                         const int cs = P.ckpt_shift;
                         for (int kk = ((k + (1 << cs) - 1) >> cs) << cs; kk < kb; kk += 1 << cs)
@@ -1077,8 +1096,8 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
 #pragma unroll
                     for (int j = 0; j < kBatch; ++j) slot[j] = __ldg(P.vol.pt + (j < nvalid ? pti[j] : 0u));
                 }
-                // (the entries at miss_at and empty_at are selected in these loops: indexing the
-                // arrays with a run-time index would move them to local memory)
+                // (the entry at miss_at is selected in this loop: indexing the arrays with a run-time
+                // index would move them to local memory)
                 int miss_at = kBatch;
                 uint32_t miss_pti = 0u;
 #pragma unroll
@@ -1087,54 +1106,32 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         miss_at = j;
                         miss_pti = pti[j];
                     }
-                // usage stamps (one store per brick change); ES: the first sample in a brick or
-                // macro-cell that cannot change the lane's state
-                int empty_at = kBatch;
-                bool empty_brick = false;
+                // usage stamps (one store per brick change)
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
-                    if (j < nvalid && j < miss_at) {
-                        if (pti[j] != cur_pti) {
-                            cur_pti = pti[j];
-                            if (P.last_used) P.last_used[slot[j]] = P.frame;
-                            if (ES) {
-                                cur_bskip = brick_skippable<DT, MODE>(__ldg(P.vol.range + slot[j]), s_apre, s_amx, T);
-                                cur_cell = kInvalidSlot;
-                            }
-                        }
-                        // (a skipping lane's leading samples in the block it jumped into are passed over)
-                        const uint32_t c = kFastCell ? CellBits<BS>::key(loc[j]) : loc[j] >> 22;
-                        const bool lead = in_skip && pti[j] == pti[0] &&
-                                          (sk_brick || c == (kFastCell ? CellBits<BS>::key(loc[0]) : loc[0] >> 22));
-                        if (ES && empty_at == kBatch && !lead) {
-                            bool e = cur_bskip;
-                            if (!e) {
-                                if (c != cur_cell) {
-                                    cur_cell = c;
-                                    const uint32_t ci = kFastCell ? CellBits<BS>::index(c) : c;
-                                    cur_cskip = span_skippable<MODE>(__ldg(P.vol.cells + slot[j] * ncells + ci), s_apre,
-                                                                     s_amx, T);
-                                }
-                                e = cur_cskip;
-                            }
-                            if (e) {
-                                empty_at = j;
-                                empty_brick = cur_bskip;
-                            }
-                        }
+                    if (j < nvalid && j < miss_at && pti[j] != cur_pti) {
+                        cur_pti = pti[j];
+                        if (P.last_used) P.last_used[slot[j]] = P.frame;
                     }
+                }
+                // ES: the value range and macro-cell span of the batch's last sample, loaded beside
+                // the gathers and tested after compositing
+                const bool test_last = ES && nvalid == kBatch && miss_at == kBatch;
+                float2 rng_last = make_float2(0.f, 0.f);
+                uint32_t span_last = 0u;
+                if (test_last) {
+                    rng_last = __ldg(P.vol.range + slot[kBatch - 1]);
+                    span_last = __ldg(P.vol.cells + slot[kBatch - 1] * ncells + cell_last);
                 }
                 // (c) gathers, all issued together (unused samples read slot 0, element 0)
                 float val[kBatch];
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
                     const bool use = j < nvalid && j < miss_at;
-                    const unsigned long long base =
-                        use ? (unsigned long long)slot[j] * slot_stride + (ES && !kFastCell ? (loc[j] & 0x3FFFFFu) : loc[j])
-                            : 0ull;
+                    const unsigned long long base = use ? (unsigned long long)slot[j] * slot_stride + loc[j] : 0ull;
                     val[j] = sample_value<DT, BS, Q>(P.vol.atlas, base, B1, wgt[j]);
                 }
-                const int stop = min(min(nvalid, miss_at), empty_at);
+                const int stop = min(nvalid, miss_at);
                 bool fin = false;
                 if constexpr (MODE != kMip) {
                     // TF rows: indices and weights of the batch first, then each sample's row is
@@ -1184,7 +1181,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     }
                 }
                 bool fell = false;
-                if (!GRAD && P.preview && !fin && miss_at < kBatch && miss_at < empty_at) {
+                if (!GRAD && P.preview && !fin && miss_at < kBatch) {
                     // preview (Sec. III-H): sample k lies in a brick that is not resident.  Request the
                     // brick for the refinement and take the sample on the finest coarser resident
                     // level (left out when none is).
@@ -1197,8 +1194,6 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                         request_brick(P, miss_pti + 1u);
                     }
                     cur_pti = SP ? kInvalidSlot : miss_pti;
-                    cur_bskip = false;
-                    cur_cell = kInvalidSlot;
                     const float tk = LS ? tcur : __fadd_rn(t0, __fmul_rn((float)k, step));
                     const int lk = LOD ? lod_level(tk, lodscale, P.lod_bias, nlev) : 0;
                     const Fallback F = preview_fallback<LOD, SP>(P.vol.pt, tk, o0, o1, o2, d0, d1, d2, lodscale,
@@ -1215,12 +1210,12 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                     const unsigned m = __activemask();
                     if ((int)lane == __ffs(m) - 1) atomicAdd(&P.counters[kPreview], (unsigned)__popc(m));
                 }
-                if (!fin && !fell && nvalid < kBatch && nvalid <= miss_at && nvalid <= empty_at) fin = true;  // left the volume
-                if (ES && !fin && !fell && empty_at < kBatch && empty_at < miss_at && empty_at < nvalid) {
-                    // sample k lies in a brick or macro-cell that cannot change the state: the next
-                    // batch starts at the block's end
-                    sk = true;
-                    sk_brick = empty_brick;
+                if (!fin && !fell && nvalid < kBatch && nvalid <= miss_at) fin = true;  // left the volume
+                if (test_last && !fin) {
+                    // sample k - 1 (the batch's last) lies in a brick or macro-cell that cannot change
+                    // the state: the next batch starts at the block's end
+                    sk_brick = brick_skippable<DT, MODE>(rng_last, s_apre, s_amx, T);
+                    sk = sk_brick || span_skippable<MODE>(span_last, s_apre, s_amx, T);
                 } else if (fin) {
                     const float4 bg = P.bg;
                     if (MODE == kMop || MODE == kMip) {

@@ -1235,7 +1235,7 @@ int vol_create(const int64_t dims[3], int dtype, int brick, int levels, uint64_t
     if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->order_buckets, sizeof(int) * 64);
     if (e == cudaSuccess) e = dev_alloc(v, (void**)&v->range, sizeof(float2) * (size_t)lay.nslots);
     // macro-cells for empty-space skipping: 8 per brick axis (B per axis for B < 8), 2 bytes each
-    v->cbits = std::min(v->bshift, 3);
+    v->cbits = cell_bits_for(v->bshift);
     v->cshift = v->bshift - v->cbits;
     if (e == cudaSuccess)
         e = dev_alloc(v, (void**)&v->cells, sizeof(uint16_t) * ((size_t)1 << (3 * v->cbits)) * (size_t)lay.nslots);
