@@ -298,10 +298,12 @@ def build_volume(P, wl, store, raw, layout=None):
 
 
 def time_frames(torch, vol, cams, tf, params, steps, warmup, flush, grad=False, drgba=None, dtf=None, dvox=None):
-    """Per-step CUDA-event times (ms) of one frame; L2 flushed before every step (not timed)."""
+    """Per-step CUDA-event times (ms) of one frame; L2 flushed before every step (not timed).
+    grad: the forward in gradient mode, followed by the adjoint when drgba is given."""
+    back = grad and drgba is not None
     for _ in range(warmup):
         vol.render(cams, tf, params, grad=grad)
-        if grad:
+        if back:
             vol.render_backward(drgba, dtf, dvox)
     torch.cuda.synchronize()
     evs = []
@@ -310,7 +312,7 @@ def time_frames(torch, vol, cams, tf, params, steps, warmup, flush, grad=False, 
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         vol.render(cams, tf, params, grad=grad)
-        if grad:
+        if back:
             vol.render_backward(drgba, dtf, dvox)
         b.record()
         evs.append((a, b))
