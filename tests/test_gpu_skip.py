@@ -101,11 +101,12 @@ def test_skip_with_bricks_on_demand(P):
 
 
 @pytest.mark.parametrize("store,brick,layout", [("u16", 64, "quad"), ("f16", 32, "compact"), ("u8", 32, "quad"),
-                                               ("f32", 64, "compact")])
+                                               ("f32", 64, "compact"), ("u8", 8, "compact"), ("u16", 16, "compact")])
 def test_macro_cell_skip_is_exact(P, orc, store, brick, layout):
-    """Noise + spheres under a TF of narrow opacity peaks: no brick is empty, but many 8^3-cell
-    blocks are.  Images and sample counts are bit-identical with the skipping, which jumps over
-    a measured share of the samples; MOP and MIP likewise; and the image is the oracle's."""
+    """Noise + spheres under a TF of narrow opacity peaks: no large brick is empty, but many
+    8^3-voxel cells are (8, 4 or 2 per brick axis; an 8^3 brick is one cell).  Images and sample
+    counts are bit-identical with the skipping, which jumps over a measured share of the samples;
+    MOP and MIP likewise; and the image is the oracle's."""
     D = (200, 176, 160)
     raw16 = synth.noise_spheres(D, 21, octaves=5, period0=48.0, nspheres=30, radius=(4.0, 30.0), value=(0.3, 1.0))
     src = "u16" if store in ("u16", "f16", "f32") else "u8"
