@@ -71,10 +71,14 @@ typedef struct {
 } vol_camera;
 
 #define VOL_RENDER_GRAD 1u /* keep transmittance checkpoints for vol_render_backward */
-/* Empty-space skipping (the paper's empty-brick skipping, Sec. III-H and Sec. IV-A): a ray that
- * enters a brick whose stored value range the transfer function maps to zero opacity jumps
- * to the brick's last sample.  Those samples would composite nothing (alpha exactly 0), so
- * the image and the per-pixel sample counts are identical with or without it. */
+/* Empty-space skipping (the paper's skipping of uniform chunks, Sec. III-H and Sec. IV-A):
+ * after each batch of samples a ray tests the brick, and the macro-cell of 8^3 voxels inside
+ * it, of its last sample; when the transfer function maps the block's stored value range to
+ * zero opacity, the ray jumps to the block's last sample.  Those samples would composite
+ * nothing (alpha exactly 0), so the image and the per-pixel sample counts are identical with
+ * or without it; vol_stats.skipped_samples counts them.  (Emission/absorption, MOP and MIP on
+ * the flat page table with uniform steps; other renders ignore the flag, and so does a quad
+ * layout with bricks other than 32^3 or 64^3.) */
 #define VOL_RENDER_SKIP_EMPTY 2u
 /* With a batch provider, vol_render overlaps brick loading with rendering: while a pass
  * runs, the requests it appends are read and a library thread runs the provider on chunks
@@ -127,8 +131,9 @@ typedef struct {
  * Both projections composite the kept (rgb, a) once over the background:
  *   out_rgb = a rgb + (1 - a) bg_rgb,  out_a = a + (1 - a) bg_a,
  * and give bg for a ray that misses the box.  With VOL_RENDER_SKIP_EMPTY, a ray skips a
- * brick whose stored value range bounds every sample's opacity (MOP) or coordinate (MIP)
- * at or below the kept one; the image does not change.  Neither has an adjoint. */
+ * brick or macro-cell whose stored value range bounds every sample's opacity (MOP) or
+ * coordinate (MIP) at or below the kept one; the image does not change.  Neither has an
+ * adjoint. */
 #define VOL_COMPOSITE_DVR 0
 #define VOL_COMPOSITE_MOP 1
 #define VOL_COMPOSITE_MIP 2
