@@ -1,7 +1,9 @@
 """Full-size parity in the benchmark's launch configuration, checked on sampled outputs the
 oracle computes one by one: every pixel is rendered on the GPU, the oracle renders a seeded
 subset; page-table resolve and LOD selection are compared record by record on a seeded subset
-of pixels of one view of each image size (C2: 256 pixels; C3: 32 pixels in each of the 4 sizes)."""
+of pixels of one view of each image size (C2: 4096 pixels, and 256 more with a LOD bias of +2 so
+that the coarser levels of its pyramid (2 and 3) are traced and rendered at full size too; C3: 32 pixels in each of
+the 4 sizes)."""
 import numpy as np
 import pytest
 import torch
@@ -33,12 +35,13 @@ def c2_data(orc):
     return wl, raw, lev_u16, lev_f16
 
 
-def check_sampled(P, orc, wl, raw, store, levels, npix, tol, ntrace=24, maxs=4096):
+def check_sampled(P, orc, wl, raw, store, levels, npix, tol, ntrace=24, maxs=4096, params=None):
+    params = dict(wl["params"] if params is None else params)
     vol = P.Volume(wl["D"], store, wl["brick"], wl["levels"])
     vol.upload_level(0, raw, wl["src"])
     vol.build_lod(0)
     tf = torch.from_numpy(wl["tf"]).cuda()
-    out, ns = vol.render(wl["cams"], tf, wl["params"], nsamples=True)
+    out, ns = vol.render(wl["cams"], tf, params, nsamples=True)
     torch.cuda.synchronize()
     gpu, ngpu = out.cpu().numpy(), ns.cpu().numpy()
     assert vol.stats()["device_error"] == 0
@@ -49,7 +52,7 @@ def check_sampled(P, orc, wl, raw, store, levels, npix, tol, ntrace=24, maxs=409
         k = max(1, npix // len(wl["cams"]))
         pix = synth.pixel_subset(cam["w"], cam["h"], k, 100 + v)
         idx = off + pix[:, 1].astype(np.int64) * cam["w"] + pix[:, 0]
-        ref = orc.render(ovol, cam, wl["tf"], wl["params"], pixels=pix, amb=AMB)
+        ref = orc.render(ovol, cam, wl["tf"], params, pixels=pix, amb=AMB)
         err, bad, alt = compare(gpu[idx], ref, tol)
         assert len(bad) == 0, f"view {v}: {len(bad)} pixels above {tol}, max {err}"
         agree = (ngpu[idx] == ref["n"]) | (alt & (ngpu[idx] == ref["alt_n"]))
@@ -64,9 +67,9 @@ def check_sampled(P, orc, wl, raw, store, levels, npix, tol, ntrace=24, maxs=409
     for v in sorted(sizes.values()):
         cam = wl["cams"][v]
         pix = synth.pixel_subset(cam["w"], cam["h"], ntrace, 999 + v)
-        recs, counts = vol.trace(cam, wl["params"], pix, maxs)
+        recs, counts = vol.trace(cam, params, pix, maxs)
         for i, (px, py) in enumerate(pix):
-            want, n = orc.trace(ovol, cam, wl["params"], int(px), int(py), maxs)
+            want, n = orc.trace(ovol, cam, params, int(px), int(py), maxs)
             assert counts[i] == n
             got = recs[i, :min(n, maxs)]
             for f in ("k", "t_bits", "level", "i0", "local", "brick_id"):
@@ -79,11 +82,24 @@ def check_sampled(P, orc, wl, raw, store, levels, npix, tol, ntrace=24, maxs=409
 @pytest.mark.parametrize("store", ["u16", "f16"])
 def test_c2_reduced_precision_sampled(P, orc, c2_data, store):
     wl, raw, lev_u16, lev_f16 = c2_data
+    # (each trace is compared over its first 2048 samples: the frame's longest rays have about 1,700)
     worst, seen = check_sampled(P, orc, wl, raw, store, lev_u16 if store == "u16" else lev_f16, 4096, TOL_REDUCED,
-                                ntrace=256)
+                                ntrace=4096 if store == "u16" else 256, maxs=2048)
     print(f"C2 {store}: max abs err {worst:.3g} on 4096 sampled pixels; levels traced {sorted(seen)}")
     assert worst <= TOL_FP32  # decoded alike on both sides: only float32 arithmetic differs
     assert len(seen) >= 2
+
+
+def test_c2_coarse_levels_sampled(P, orc, c2_data):
+    """The same frame with a LOD bias of +2: its samples fall on levels 2 and 3 of the 1024^3
+    pyramid, which the benchmark's view does not reach."""
+    wl, raw, lev_u16, _ = c2_data
+    params = dict(wl["params"], lod_bias=2)
+    worst, seen = check_sampled(P, orc, wl, raw, "u16", lev_u16, 2048, TOL_REDUCED, ntrace=256, maxs=2048,
+                                params=params)
+    print(f"C2 lod_bias +2: max abs err {worst:.3g} on 2048 sampled pixels; levels traced {sorted(seen)}")
+    assert worst <= TOL_FP32
+    assert max(seen) >= 3 and len(seen) >= 2
 
 
 def test_c2_bench_variants_sampled(P, orc, c2_data):
