@@ -795,6 +795,150 @@ __device__ __forceinline__ float next_t_level_step(float t, float step, int l) {
     return __fadd_rn(t, __fmul_rn(step, (float)(1 << l)));
 }
 
+// Tail of the persistent launch: once the work queue is empty and at most kAssistLanes rays are
+// left in a warp, the warp's lanes split among those rays -- G lanes per ray, G = 2, 4 or 8 --
+// and lane q of a group decides, looks up and interpolates samples k + 6 q .. k + 6 q + 5 of its
+// group's ray; the group's first lane composites all 6 G of them in order, taking each one's TF
+// index and weight from its lane by shuffle.  The decisions, values and compositing are the
+// per-sample arithmetic of the main loop, in the same order, so the image and the sample counts
+// are bit for bit the same; the longest rays of a frame (often ~30 times the mean) then end in
+// about 1/G of the iterations instead of running on alone while their SM idles.  Emission /
+// absorption on a resident volume only (no requests, preview, level-scaled steps, sparse table,
+// skipping or gradients); called by all 32 lanes of the warp.
+#ifndef VOLRC_ASSIST_LANES
+#define VOLRC_ASSIST_LANES 16
+#endif
+constexpr int kAssistLanes = VOLRC_ASSIST_LANES;
+constexpr int kAssistBatch = 6;
+
+template <int DT, bool LOD, int BS, bool Q>
+__device__ __noinline__ void assist_finish(const RenderDev& P, bool live, long long ray, int tile, float o0, float o1,
+                                           float o2, float d0, float d1, float d2, float t0, float t1, float lodscale,
+                                           int k, float C0, float C1, float C2, float T, const float4* s_tf,
+                                           const float4* s_tfd, const LevelDev* s_lv) {
+    constexpr int kB = kAssistBatch;
+    const int lane = (int)(threadIdx.x & 31);
+    const int bshift = BS ? log2i(BS) : P.vol.bshift;
+    const int bmask = BS ? BS - 1 : P.vol.bmask;
+    const int B1 = BS ? BS + 1 : P.vol.B1;
+    const int row = Q ? B1 - 1 : B1;
+    const unsigned long long slot_stride = Q ? P.vol.slot_entries : P.vol.slot_elems;
+    const float step = P.step, et = P.et;
+    const int nlev = P.vol.nlevels;
+    int cur_l = 0;
+    LvReg L = load_lv(s_lv[0]);
+    for (;;) {
+        // ---- groups: the r-th ray (r-th lane with one) goes to lanes r G .. r G + G - 1
+        const unsigned own = __ballot_sync(kFull, live);
+        if (!own) return;
+        const int nr = __popc(own);
+        const int G = nr <= 4 ? 8 : (nr <= 8 ? 4 : 2);
+        const int r = lane / G, q = lane - r * G, gl = r * G;
+        unsigned m = own;
+        for (int i = 0; i < r && m; ++i) m &= m - 1u;
+        const int src = m ? __ffs(m) - 1 : 0;
+        const bool in = r < nr;
+        o0 = __shfl_sync(kFull, o0, src); o1 = __shfl_sync(kFull, o1, src); o2 = __shfl_sync(kFull, o2, src);
+        d0 = __shfl_sync(kFull, d0, src); d1 = __shfl_sync(kFull, d1, src); d2 = __shfl_sync(kFull, d2, src);
+        t0 = __shfl_sync(kFull, t0, src); t1 = __shfl_sync(kFull, t1, src);
+        lodscale = __shfl_sync(kFull, lodscale, src);
+        k = __shfl_sync(kFull, k, src);
+        C0 = __shfl_sync(kFull, C0, src); C1 = __shfl_sync(kFull, C1, src); C2 = __shfl_sync(kFull, C2, src);
+        T = __shfl_sync(kFull, T, src);
+        ray = __shfl_sync(kFull, ray, src);
+        tile = __shfl_sync(kFull, tile, src);
+        live = in;
+        // ---- march until a group's ray ends (then the rays are regrouped)
+        bool ended = false;
+        while (!__any_sync(kFull, ended)) {
+            uint32_t pti[kB], loc[kB], slot[kB];
+            float wgt[kB][3];
+            int nvalid = live ? kB : 0;
+            const float kf = (float)(k + kB * q);  // exact: indices stay below 2^24
+#pragma unroll
+            for (int j = 0; j < kB; ++j) {
+                const float t = __fadd_rn(t0, __fmul_rn(__fadd_rn(kf, (float)j), step));
+                if (!(t < t1) && nvalid == kB) nvalid = j;
+                const float p[3] = {__fadd_rn(o0, __fmul_rn(t, d0)), __fadd_rn(o1, __fmul_rn(t, d1)),
+                                    __fadd_rn(o2, __fmul_rn(t, d2))};
+                if (LOD) {
+                    const int l = lod_level(t, lodscale, P.lod_bias, nlev);
+                    if (l != cur_l) {
+                        cur_l = l;
+                        L = load_lv(s_lv[l]);
+                    }
+                }
+                Resolved R;
+                resolve_reg(L, bshift, bmask, row, p, R);
+                pti[j] = R.pti;
+                loc[j] = R.local;
+                wgt[j][0] = R.w[0];
+                wgt[j][1] = R.w[1];
+                wgt[j][2] = R.w[2];
+            }
+#pragma unroll
+            for (int j = 0; j < kB; ++j) slot[j] = __ldg(P.vol.pt + (j < nvalid ? pti[j] : 0u));
+            int miss_at = kB;
+#pragma unroll
+            for (int j = kB - 1; j >= 0; --j)
+                if (j < nvalid && slot[j] == kInvalidSlot) miss_at = j;
+            // usage stamps (idempotent: every lane stamps the bricks of its own samples)
+#pragma unroll
+            for (int j = 0; j < kB; ++j)
+                if (P.last_used && j < nvalid && j < miss_at && (j == 0 || pti[j] != pti[j - 1]))
+                    P.last_used[slot[j]] = P.frame;
+            int ti[kB];
+            float tw[kB];
+#pragma unroll
+            for (int j = 0; j < kB; ++j) {
+                const bool use = j < nvalid && j < miss_at;
+                const unsigned long long base = use ? (unsigned long long)slot[j] * slot_stride + loc[j] : 0ull;
+                tf_index<DT>(sample_value<DT, BS, Q>(P.vol.atlas, base, B1, wgt[j]), ti[j], tw[j]);
+            }
+            // ---- the group's first lane composites the group's 6 G samples in order
+            bool fin = false, out = false, err = false;  // early termination, left the volume, missing brick
+            int kk = k;
+            for (int qq = 0; qq < G; ++qq) {
+                const int from = gl + qq;  // (lanes of groups past the last ray shuffle among themselves)
+                const int nv = __shfl_sync(kFull, nvalid, from), ms = __shfl_sync(kFull, miss_at, from);
+#pragma unroll
+                for (int j = 0; j < kB; ++j) {
+                    const int tij = __shfl_sync(kFull, ti[j], from);
+                    const float twj = __shfl_sync(kFull, tw[j], from);
+                    if (q == 0 && live && !fin && !out && !err) {
+                        if (j >= nv && nv <= ms) {
+                            out = true;
+                        } else if (j >= ms) {
+                            err = true;
+                        } else {
+                            fin = composite_row<kDvr, false>(twj, s_tf[tij], s_tfd[tij], 0.0f, et, T, C0, C1, C2);
+                            ++kk;
+                        }
+                    }
+                }
+            }
+            k = __shfl_sync(kFull, kk, gl);
+            const bool stop = __shfl_sync(kFull, (fin || out || err) ? 1 : 0, gl) != 0;
+            if (live && stop) {
+                if (q == 0) {
+                    if (err) {
+                        atomicAdd(&P.counters[kDevError], 1u);
+                    } else {
+                        const float4 bg = P.bg;
+                        P.out[ray] = make_float4(fmaf(T, bg.x, C0), fmaf(T, bg.y, C1), fmaf(T, bg.z, C2),
+                                                 fmaf(T, bg.w, 1.0f - T));
+                        if (P.nsamp) P.nsamp[ray] = k;
+                        if (P.tile_cost && tile >= 0) atomicMax(&P.tile_cost[tile], k);
+                    }
+                }
+                live = false;
+                ended = true;
+            }
+        }
+        if (q != 0) live = false;  // only a group's first lane keeps the ray for the regrouping
+    }
+}
+
 // BS: brick edge known at compile time (32 or 64), or 0 for any power of two read at run time.
 // MODE: kDvr, kDvrGrad, kMop or kMip.  Lane state (C0, C1, C2, T): emission/absorption keeps
 // the partial colour and the transmittance; MOP the kept sample's colour and opacity (T,
@@ -821,6 +965,9 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
     constexpr bool kFastCell = ES && Q && BS >= 8;
     constexpr int kBatch = LS ? kBatchLevelStep : (ES ? kBatchSkip : kBatchDefault);
     constexpr bool GRAD = MODE == kDvrGrad;
+    // the tail's lane assist (assist_finish): plain emission/absorption on a resident volume
+    constexpr bool kAssistOk = MODE == kDvr && !LS && !SP && !ES && kAssistLanes > 0;
+    const bool kAssist = kAssistOk && !P.preview && !P.req_table;
     constexpr float kT0 = MODE == kMop ? 0.0f : (MODE == kMip ? -1.0f : 1.0f);
     __shared__ float4 s_tf[256];
     __shared__ float4 s_tfd[255];  // tf[i+1] - tf[i], each difference rounded once
@@ -981,9 +1128,17 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
         }
         unsigned act = __ballot_sync(kFull, active);
         if (!act) break;
+        if constexpr (kAssistOk) {
+            if (kAssist && queue_done && __popc(act) <= kAssistLanes) {
+                // the tail: the warp's lanes split among its last rays (assist_finish)
+                assist_finish<DT, LOD, BS, Q>(P, active, ray, my_tile, o0, o1, o2, d0, d1, d2, t0, t1, lodscale, k, C0,
+                                              C1, C2, T, s_tf, s_tfd, s_lv);
+                break;
+            }
+        }
 
         // ---- march: per iteration up to kBatch samples of each active ray
-        const int thresh = queue_done ? 1 : P.refill_thresh;
+        const int thresh = queue_done ? (kAssist ? kAssistLanes + 1 : 1) : P.refill_thresh;
         do {
             if (active) {
                 // (a) decisions for the batch (ALU only)
