@@ -802,20 +802,20 @@ __device__ __forceinline__ float next_t_level_step(float t, float step, int l) {
 // index and weight from its lane by shuffle.  The decisions, values and compositing are the
 // per-sample arithmetic of the main loop, in the same order, so the image and the sample counts
 // are bit for bit the same; the longest rays of a frame (often ~30 times the mean) then end in
-// about 1/G of the iterations instead of running on alone while their SM idles.  Emission /
-// absorption on a resident volume only (no requests, preview, level-scaled steps, sparse table,
-// skipping or gradients); called by all 32 lanes of the warp.
+// about 1/G of the iterations instead of running on alone while their SM idles.  Any compositing
+// mode but the gradient one, on a resident volume (no requests, preview, level-scaled steps,
+// sparse table or skipping); called by all 32 lanes of the warp.
 #ifndef VOLRC_ASSIST_LANES
 #define VOLRC_ASSIST_LANES 16
 #endif
 constexpr int kAssistLanes = VOLRC_ASSIST_LANES;
 constexpr int kAssistBatch = 6;
 
-template <int DT, bool LOD, int BS, bool Q>
+template <int DT, bool LOD, int MODE, int BS, bool Q>
 __device__ __noinline__ void assist_finish(const RenderDev& P, bool live, long long ray, int tile, float o0, float o1,
                                            float o2, float d0, float d1, float d2, float t0, float t1, float lodscale,
                                            int k, float C0, float C1, float C2, float T, const float4* s_tf,
-                                           const float4* s_tfd, const LevelDev* s_lv) {
+                                           const float4* s_tfd, const LevelDev* s_lv, float amax_tf) {
     constexpr int kB = kAssistBatch;
     const int lane = (int)(threadIdx.x & 31);
     const int bshift = BS ? log2i(BS) : P.vol.bshift;
@@ -887,13 +887,19 @@ __device__ __noinline__ void assist_finish(const RenderDev& P, bool live, long l
             for (int j = 0; j < kB; ++j)
                 if (P.last_used && j < nvalid && j < miss_at && (j == 0 || pti[j] != pti[j - 1]))
                     P.last_used[slot[j]] = P.frame;
-            int ti[kB];
-            float tw[kB];
+            int ti[kB];    // TF row (MIP: unused)
+            float tw[kB];  // its weight (MIP: the TF coordinate)
 #pragma unroll
             for (int j = 0; j < kB; ++j) {
                 const bool use = j < nvalid && j < miss_at;
                 const unsigned long long base = use ? (unsigned long long)slot[j] * slot_stride + loc[j] : 0ull;
-                tf_index<DT>(sample_value<DT, BS, Q>(P.vol.atlas, base, B1, wgt[j]), ti[j], tw[j]);
+                const float v = sample_value<DT, BS, Q>(P.vol.atlas, base, B1, wgt[j]);
+                if (MODE == kMip) {
+                    ti[j] = 0;
+                    tw[j] = tf_coord<DT>(v);
+                } else {
+                    tf_index<DT>(v, ti[j], tw[j]);
+                }
             }
             // ---- the group's first lane composites the group's 6 G samples in order
             bool fin = false, out = false, err = false;  // early termination, left the volume, missing brick
@@ -911,7 +917,12 @@ __device__ __noinline__ void assist_finish(const RenderDev& P, bool live, long l
                         } else if (j >= ms) {
                             err = true;
                         } else {
-                            fin = composite_row<kDvr, false>(twj, s_tf[tij], s_tfd[tij], 0.0f, et, T, C0, C1, C2);
+                            if constexpr (MODE == kMip) {
+                                if (twj > T) T = twj;
+                                fin = T >= 255.0f;  // no coordinate lies above 255
+                            } else {
+                                fin = composite_row<MODE, false>(twj, s_tf[tij], s_tfd[tij], amax_tf, et, T, C0, C1, C2);
+                            }
                             ++kk;
                         }
                     }
@@ -925,8 +936,27 @@ __device__ __noinline__ void assist_finish(const RenderDev& P, bool live, long l
                         atomicAdd(&P.counters[kDevError], 1u);
                     } else {
                         const float4 bg = P.bg;
-                        P.out[ray] = make_float4(fmaf(T, bg.x, C0), fmaf(T, bg.y, C1), fmaf(T, bg.z, C2),
-                                                 fmaf(T, bg.w, 1.0f - T));
+                        if (MODE == kMop || MODE == kMip) {
+                            // the kept sample composited once over the background, as in k_render
+                            float al = 0.0f;
+                            if (MODE == kMop) {
+                                al = T;
+                            } else if (T >= 0.0f) {  // the TF at the largest coordinate
+                                const int i = min((int)T, 254);
+                                const float wt = T - (float)i;
+                                const float4 a = s_tf[i], dab = s_tfd[i];
+                                al = fmaf(wt, dab.w, a.w);
+                                C0 = fmaf(wt, dab.x, a.x);
+                                C1 = fmaf(wt, dab.y, a.y);
+                                C2 = fmaf(wt, dab.z, a.z);
+                            }
+                            const float tb = 1.0f - al;
+                            P.out[ray] = make_float4(fmaf(al, C0, tb * bg.x), fmaf(al, C1, tb * bg.y),
+                                                     fmaf(al, C2, tb * bg.z), fmaf(tb, bg.w, al));
+                        } else {
+                            P.out[ray] = make_float4(fmaf(T, bg.x, C0), fmaf(T, bg.y, C1), fmaf(T, bg.z, C2),
+                                                     fmaf(T, bg.w, 1.0f - T));
+                        }
                         if (P.nsamp) P.nsamp[ray] = k;
                         if (P.tile_cost && tile >= 0) atomicMax(&P.tile_cost[tile], k);
                     }
@@ -966,7 +996,7 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
     constexpr int kBatch = LS ? kBatchLevelStep : (ES ? kBatchSkip : kBatchDefault);
     constexpr bool GRAD = MODE == kDvrGrad;
     // the tail's lane assist (assist_finish): plain emission/absorption on a resident volume
-    constexpr bool kAssistOk = MODE == kDvr && !LS && !SP && !ES && kAssistLanes > 0;
+    constexpr bool kAssistOk = MODE != kDvrGrad && !LS && !SP && !ES && kAssistLanes > 0;
     const bool kAssist = kAssistOk && !P.preview && !P.req_table;
     constexpr float kT0 = MODE == kMop ? 0.0f : (MODE == kMip ? -1.0f : 1.0f);
     __shared__ float4 s_tf[256];
@@ -1131,8 +1161,8 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
         if constexpr (kAssistOk) {
             if (kAssist && queue_done && __popc(act) <= kAssistLanes) {
                 // the tail: the warp's lanes split among its last rays (assist_finish)
-                assist_finish<DT, LOD, BS, Q>(P, active, ray, my_tile, o0, o1, o2, d0, d1, d2, t0, t1, lodscale, k, C0,
-                                              C1, C2, T, s_tf, s_tfd, s_lv);
+                assist_finish<DT, LOD, MODE, BS, Q>(P, active, ray, my_tile, o0, o1, o2, d0, d1, d2, t0, t1, lodscale,
+                                                    k, C0, C1, C2, T, s_tf, s_tfd, s_lv, amax_tf);
                 break;
             }
         }
