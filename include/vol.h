@@ -431,8 +431,7 @@ int vol_trace(vol_t v, const vol_camera *cam, const vol_params *params, const in
  * VOL_NOALLOC_MAX_VIEWS views per call.  The caller passes inputs and outputs
  * exactly as for vol_render().
  *   - The first call on each device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with the device current.
  *   - All calls share the array, and each call overwrites it: calls that
  *     overlap on the GPU (different streams, or different volumes on streams
  *     that are not ordered) race.  Calls on one stream are ordered and safe.
