@@ -76,6 +76,9 @@ struct ViewDev {
     int tiles_x;
     int tile_off;     // first work item of this view
     long long ray_off;// first ray (pixel) of this view in the packed image
+    // pixels outside [cx0, cx1] x [cy0, cy1] miss the volume (a conservative bound of its
+    // projection, with a margin; the whole image when no bound applies)
+    int cx0, cx1, cy0, cy1;
 };
 
 struct SuspRec {       // a ray waiting for a brick

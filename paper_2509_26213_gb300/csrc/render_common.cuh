@@ -810,6 +810,26 @@ __device__ __forceinline__ float next_t_level_step(float t, float step, int l) {
 #endif
 constexpr int kAssistLanes = VOLRC_ASSIST_LANES;
 constexpr int kAssistBatch = 6;
+// Tiles wholly outside a view's bound of the volume's projection are written as misses without
+// setting up their rays.
+#ifndef VOLRC_CULL_TILES
+#define VOLRC_CULL_TILES 1
+#endif
+constexpr bool kCullTiles = VOLRC_CULL_TILES != 0;
+
+// The misses of a ray tile that cannot meet the volume, written by the lanes of a warp (not
+// inlined: it keeps the render loop's code as it is).
+__device__ __noinline__ void write_missed_tile(const RenderDev& P, const ViewDev& V, int x0, int y0, int cnt, int lane) {
+    for (int q = lane; q < cnt; q += 32) {
+        const int px = x0 + q % P.tile_w, py = y0 + q / P.tile_w;
+        if (px < V.w && py < V.h) {
+            const long long r = V.ray_off + (long long)py * V.w + px;
+            P.out[r] = P.bg;
+            if (P.nsamp) P.nsamp[r] = 0;
+            if (P.ray_n) P.ray_n[r] = 0;
+        }
+    }
+}
 
 template <int DT, bool LOD, int MODE, int BS, bool Q>
 __device__ __noinline__ void assist_finish(const RenderDev& P, bool live, long long ray, int tile, float o0, float o1,
@@ -1092,13 +1112,22 @@ __global__ void __launch_bounds__(kRenderThreads, VOLRC_MIN_CTAS) k_render(const
                 if (!P.resume) {
                     const int tile = P.tile_order ? P.tile_order[item] : item;
                     const int v = find_view_tile(P.views, P.nviews, tile);
-                    const int tl = tile - P.views[v].tile_off;
-                    const int tx = P.views[v].tiles_x;
+                    const ViewDev& V = P.views[v];
+                    const int tl = tile - V.tile_off;
+                    const int tx = V.tiles_x;
                     pool_tile = tile;
                     pool_a = v;
                     pool_x0 = (tl % tx) * P.tile_w;
                     pool_y0 = (tl / tx) * P.tile_h;
                     pool_cnt = P.tile_w * P.tile_h;
+                    if (kCullTiles &&
+                        (pool_x0 > V.cx1 || pool_x0 + P.tile_w <= V.cx0 || pool_y0 > V.cy1 || pool_y0 + P.tile_h <= V.cy0)) {
+                        // no ray of the tile can meet the volume (outside the view's bound of its
+                        // projection): the warp writes the tile's misses at once
+                        write_missed_tile(P, V, pool_x0, pool_y0, pool_cnt, (int)lane);
+                        pool_next = pool_cnt;
+                        continue;
+                    }
                 } else {
                     pool_tile = -1;
                     pool_a = item * 32;

@@ -639,6 +639,52 @@ RenderDev render_args(vol_t v) {
     return p;
 }
 
+// Pixel box outside of which no ray of view c meets the volume [0, D0): the 8 corners of the box
+// are expressed in the camera basis (fwd, right, up; any non-singular basis, solved in double),
+// projected to pixel-centre coordinates, and their bounding box widened by 2 pixels.  A ray's
+// direction is rounded to binary32 only, so a pixel 2 pixels outside that box cannot reach the
+// volume.  When a corner is not in front of the eye (the eye near or inside the volume) or the
+// basis is singular, the box is the whole image.
+void view_cull_box(const vol_camera& c, const float D0f[3], ViewDev& V) {
+    V.cx0 = 0;
+    V.cx1 = c.w - 1;
+    V.cy0 = 0;
+    V.cy1 = c.h - 1;
+    const double F[3] = {c.fwd[0], c.fwd[1], c.fwd[2]}, R[3] = {c.right[0], c.right[1], c.right[2]},
+                 U[3] = {c.up[0], c.up[1], c.up[2]};
+    // inverse of the matrix with columns F, R, U (rows of the inverse: cross products / det)
+    const double cRU[3] = {R[1] * U[2] - R[2] * U[1], R[2] * U[0] - R[0] * U[2], R[0] * U[1] - R[1] * U[0]};
+    const double cUF[3] = {U[1] * F[2] - U[2] * F[1], U[2] * F[0] - U[0] * F[2], U[0] * F[1] - U[1] * F[0]};
+    const double cFR[3] = {F[1] * R[2] - F[2] * R[1], F[2] * R[0] - F[0] * R[2], F[0] * R[1] - F[1] * R[0]};
+    const double det = F[0] * cRU[0] + F[1] * cRU[1] + F[2] * cRU[2];
+    const double ta = (double)c.tan_half_fov * (double)c.aspect, tv = (double)c.tan_half_fov;
+    if (!(std::fabs(det) > 1e-12) || !(ta > 0.0) || !(tv > 0.0)) return;
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int k = 0; k < 8; ++k) {
+        const double p[3] = {(k & 1) ? (double)D0f[0] : 0.0, (k & 2) ? (double)D0f[1] : 0.0,
+                             (k & 4) ? (double)D0f[2] : 0.0};
+        const double r[3] = {p[0] - c.eye[0], p[1] - c.eye[1], p[2] - c.eye[2]};
+        const double len = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        // r = lam (F + a R + b U): lam, lam a, lam b
+        const double lam = (r[0] * cRU[0] + r[1] * cRU[1] + r[2] * cRU[2]) / det;
+        const double la = (r[0] * cUF[0] + r[1] * cUF[1] + r[2] * cUF[2]) / det;
+        const double lb = (r[0] * cFR[0] + r[1] * cFR[1] + r[2] * cFR[2]) / det;
+        if (!(lam > 1e-6 * (len + 1.0))) return;  // not clearly in front of the eye
+        const double u = la / lam / ta, vv = lb / lam / tv;
+        const double px = (u + 1.0) * 0.5 * c.w - 0.5, py = (1.0 - vv) * 0.5 * c.h - 0.5;
+        if (!std::isfinite(px) || !std::isfinite(py)) return;
+        x0 = std::min(x0, px);
+        x1 = std::max(x1, px);
+        y0 = std::min(y0, py);
+        y1 = std::max(y1, py);
+    }
+    const double m = 2.0;
+    V.cx0 = (int)std::max(0.0, std::min((double)c.w, std::floor(x0 - m)));
+    V.cx1 = (int)std::max(-1.0, std::min((double)c.w - 1.0, std::ceil(x1 + m)));
+    V.cy0 = (int)std::max(0.0, std::min((double)c.h, std::floor(y0 - m)));
+    V.cy1 = (int)std::max(-1.0, std::min((double)c.h - 1.0, std::ceil(y1 + m)));
+}
+
 // One kernel pass.  resume = false: all tiles; true: the rays suspended in susp[susp_cur].
 int run_pass(vol_t v, bool resume, bool may_miss) {
     RenderDev p = render_args(v);
@@ -1614,6 +1660,8 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
         V.tiles_x = (c.w + p.tile_w - 1) / p.tile_w;
         V.tile_off = (int)tiles;
         V.ray_off = rays;
+        const float D0f[3] = {(float)v->lay.dims[0], (float)v->lay.dims[1], (float)v->lay.dims[2]};
+        view_cull_box(c, D0f, V);
         tiles += (int64_t)V.tiles_x * ((c.h + p.tile_h - 1) / p.tile_h);
         rays += (int64_t)c.w * c.h;
     }
@@ -1984,6 +2032,8 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
         V.tiles_x = (c.w + p.tile_w - 1) / p.tile_w;
         V.tile_off = (int)tiles;
         V.ray_off = rays;
+        const float D0f[3] = {(float)v->lay.dims[0], (float)v->lay.dims[1], (float)v->lay.dims[2]};
+        view_cull_box(c, D0f, V);
         tiles += (int64_t)V.tiles_x * ((c.h + p.tile_h - 1) / p.tile_h);
         rays += (int64_t)c.w * c.h;
     }

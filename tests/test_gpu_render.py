@@ -372,3 +372,31 @@ def test_compact_layout_miss_path(P, orc):
     vol.set_provider(provider, "u8")
     got = vol.render(cam, tf_dev(tf), dict(params, max_passes=300)).cpu().numpy()
     np.testing.assert_array_equal(got, want)
+
+
+def test_tile_culling_is_conservative(P, orc):
+    """Ray tiles outside a view's bound of the volume's projection are written as misses without
+    their rays being set up.  Against the oracle on every pixel, the hit/miss pattern, the sample
+    counts and the image are the same, for a volume seen small in a corner of the image, a camera
+    whose basis is neither orthogonal nor unit-length, a volume partly behind the eye and one
+    that projects outside the image."""
+    D = (48, 40, 36)
+    raw = np.full(D[::-1], 140, dtype=np.uint8)
+    vol = gpu_volume(P, raw, "u8", "u8", 16, 1)
+    ovol = orc.Volume(store_levels(orc, raw, "u8", "u8", 1), "u8", 16)
+    tf = synth.tf_ramp(alpha_start=0.0, alpha_max=0.05)
+    corner = synth.look_at((150.0, 130.0, 110.0), (30.0, 10.0, 5.0), 96, 72, fov_deg=40.0)
+    skew = dict(synth.look_at((-60.0, 20.0, 18.0), (24.0, 20.0, 18.0), 80, 64, fov_deg=50.0))
+    skew["right"] = np.float32(skew["right"] * 1.3 + 0.2 * skew["up"])
+    skew["up"] = np.float32(skew["up"] * 0.8 - 0.1 * skew["fwd"])
+    behind = synth.look_at((24.0, 20.0, 40.0), (24.0, 60.0, 40.0), 64, 48, fov_deg=90.0)
+    away = synth.look_at((-100.0, -80.0, 18.0), (200.0, -80.0, 18.0), 64, 48, fov_deg=30.0)
+    for cam in (corner, skew, behind, away):
+        out, ns = vol.render(cam, tf_dev(tf), {}, nsamples=True)
+        torch.cuda.synchronize()
+        ref = orc.render(ovol, cam, tf, {}, amb=AMB)
+        n = ns.cpu().numpy()
+        assert np.array_equal(n > 0, ref["n"] > 0)
+        assert np.all((n == ref["n"]) | (ref["amb"] & (n == ref["alt_n"])))
+        err, bad, _ = compare(out.cpu().numpy(), ref, TOL_FP32)
+        assert len(bad) == 0, err
