@@ -150,7 +150,8 @@ typedef struct {
     int32_t max_passes;  /* miss/refill passes per render when a provider is set; 0 = 256 */
     uint32_t flags;      /* VOL_RENDER_* bits */
     int32_t refill;      /* a warp fetches new rays once fewer lanes than this are busy
-                            (1..32; 0 = default 20); performance only, never the image */
+                            (1..32; 0 = default: 20 for emission/absorption, 28 for MOP and
+                            MIP); performance only, never the image */
     int32_t ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
     int32_t composite;   /* VOL_COMPOSITE_* (0 = emission/absorption) */
 } vol_params;

@@ -685,6 +685,11 @@ void view_cull_box(const vol_camera& c, const float D0f[3], ViewDev& V) {
     V.cy1 = (int)std::max(-1.0, std::min((double)c.h - 1.0, std::ceil(y1 + m)));
 }
 
+// Default lane-refill threshold: projections keep every ray to its exit, and fetch new rays later
+// (measured on the 1024^3 frame: MOP 3.62 -> 3.38 ms, MIP 3.17 -> 2.95 ms at 28 instead of 20;
+// emission/absorption is fastest at 20).
+int default_refill(int composite) { return composite == VOL_COMPOSITE_DVR ? 20 : 28; }
+
 // One kernel pass.  resume = false: all tiles; true: the rays suspended in susp[susp_cur].
 int run_pass(vol_t v, bool resume, bool may_miss) {
     RenderDev p = render_args(v);
@@ -1618,7 +1623,7 @@ int vol_render(vol_t v, const vol_camera* cams, int nviews, const float* tf_dev,
     if (p.tile_h <= 0) p.tile_h = 8;
     if (p.tile_w > 4096 || p.tile_h > 4096 || p.tile_w * p.tile_h > 4096)
         return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be at most 4096");
-    if (p.refill <= 0 || p.refill > 32) p.refill = 20;
+    if (p.refill <= 0 || p.refill > 32) p.refill = default_refill(p.composite);
     if (p.lod_mode != 0 && p.lod_mode != 1) return fail(v, VOL_ERR_INVALID_ARG, "lod_mode must be 0 or 1");
     if (p.composite < VOL_COMPOSITE_DVR || p.composite > VOL_COMPOSITE_MIP)
         return fail(v, VOL_ERR_INVALID_ARG, "composite must be VOL_COMPOSITE_DVR, _MOP or _MIP");
@@ -1993,7 +1998,7 @@ extern "C" int vol_render_noalloc(vol_t v, const vol_camera* cams, int nviews, c
     if (p.tile_h <= 0) p.tile_h = 8;
     if (p.tile_w > 4096 || p.tile_h > 4096 || p.tile_w * p.tile_h > 4096)
         return fail(v, VOL_ERR_INVALID_ARG, "tile_w * tile_h must be at most 4096");
-    if (p.refill <= 0 || p.refill > 32) p.refill = 20;
+    if (p.refill <= 0 || p.refill > 32) p.refill = default_refill(p.composite);
     if (p.lod_mode != 0 && p.lod_mode != 1) return fail(v, VOL_ERR_INVALID_ARG, "lod_mode must be 0 or 1");
     if (p.composite < VOL_COMPOSITE_DVR || p.composite > VOL_COMPOSITE_MIP)
         return fail(v, VOL_ERR_INVALID_ARG, "composite must be VOL_COMPOSITE_DVR, _MOP or _MIP");
