@@ -614,6 +614,8 @@ def run_ours(args, dist, rank, ws, local):
     wl["layout"] = args.layout
     raw = wl["make"]()
     cams, params = wl["cams"], dict(wl["params"])
+    if args.skip_empty:  # (profiling aid: the primary frame rendered by the skip variant)
+        params["flags"] = params.get("flags", 0) | P.C.VOL_RENDER_SKIP_EMPTY
     tf = torch.from_numpy(wl["tf"]).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     store = wl["store"]
@@ -902,6 +904,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s", "c3", "c4", "c4s", "c5"])
     ap.add_argument("--layout", default="quad", choices=["quad", "compact"],
                     help="atlas slot layout of the primary line's volume")
+    ap.add_argument("--skip-empty", action="store_true",
+                    help="render the primary frame with empty-space skipping (for profiling the skip variant)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-frac", type=float, default=0.25, help="reference arm: fraction of pixels per step")
     args = ap.parse_args()
